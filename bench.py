@@ -1,0 +1,295 @@
+#!/usr/bin/env python
+"""Benchmark of the coupled Maxwell-Schroedinger step on GB300.
+
+Workload (default): the split-ring-resonator array, a 128x128x192 Yee grid
+(2 nm cells, silver Drude rings on glass, CPML in z, TF/SF pulse) driving
+50,000 molecules (128-point radial grid, J <= 4, two surfaces) -- one step
+is one coupled time step of the whole path (H update, molecular
+split-operator step with gather of the local field, polarization scatter,
+E update with the Drude current).
+
+Prints ONE JSON line.  value = molecule-steps/s of the whole coupled step
+(all ranks); the Yee cell-updates/s of the same steps ride along.
+N > 1 ranks (torchrun) run independent replicas (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Yee cell-updates/s + molecule-steps/s, mixed vs plain FP32 at stated error"
+UNIT = "molecule-steps/s"
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--molecules", type=int, default=50000)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (of measured)"
+    return 6800.0, "recipe fallback 6.8 TB/s (of fallback)"
+
+
+def _kernel_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, valid only while
+    the kernel's source is unchanged (sha256 of the .cu file)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_2209_04487_gb300", "csrc", d["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    return d["bytes_per_launch"] if sha == d["sha256"] else None
+
+
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(device_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _workload(nmol):
+    import workloads as W
+    return W.config1(n_molecules=nmol)
+
+
+# ---------------------------------------------------------------------------
+# the oracle, timed on the host cores (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def _oracle_sample(wl, field_steps=2, mol_sub=500, mol_steps=3):
+    """Bounded sample of the same workload through the FP64 oracle: field
+    steps on the full grid and molecule steps on a subset; returns the
+    whole-step molecule-steps/s extrapolated linearly in molecules."""
+    import numpy as np
+
+    from oracle.fdtd import YeeOracle
+    from oracle.molecule import SpeciesEnsemble, dtau_au
+    f = YeeOracle(wl.nx, wl.ny, wl.nz, wl.nsim, wl.dx, wl.dt, wl.mat_id, wl.materials, pml=wl.pml,
+                  bc_z=wl.bc_z, src_k=wl.src_k, src=wl.src, aux_len=4096)
+    t0 = time.perf_counter()
+    for _ in range(field_steps):
+        f.step()
+    t_field = (time.perf_counter() - t0) / field_steps
+    ens = SpeciesEnsemble(wl.species[0], wl.quat[:mol_sub], dtau_au(wl.dt))
+    E = np.random.default_rng(0).standard_normal((mol_sub, 3)) * 1e9
+    t0 = time.perf_counter()
+    for _ in range(mol_steps):
+        ens.step(E)
+    t_mol = (time.perf_counter() - t0) / mol_steps * (wl.n_molecules / mol_sub)
+    t_step = t_field + t_mol
+    return wl.n_molecules / t_step, t_step, t_field, t_mol
+
+
+def _cpu_desc():
+    return os.cpu_count() or 1
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = _workload(a.molecules)
+    for _ in range(a.warmup):
+        _oracle_sample(wl, field_steps=1, mol_sub=100, mol_steps=1)
+    vals, tsteps = [], []
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        v, ts, _, _ = _oracle_sample(wl, field_steps=1, mol_sub=200, mol_steps=1)
+        vals.append(v)
+        tsteps.append(ts)
+    wall = time.perf_counter() - t0
+    value = wl.n_molecules * len(tsteps) / sum(tsteps)
+    sample = (f"per step: 1 FP64 field step on the full {wl.nx}x{wl.ny}x{wl.nz} grid + 200 of "
+              f"{wl.n_molecules} molecules, molecule time scaled x{wl.n_molecules // 200}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(tsteps) / len(tsteps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(wl),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cpu_desc(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": wall}
+    print(json.dumps(line), flush=True)
+
+
+def _config(wl):
+    sp = wl.species[0]
+    return {"workload": "split-ring array 128x128x192 (2 nm, Ag Drude rings on glass, CPML z, TF/SF "
+                        f"pulse) + {wl.n_molecules} molecules (Nr {sp.nr}, J<={sp.jmax}, 2 surfaces)",
+            "cells": wl.cells, "molecules": wl.n_molecules, "nr": sp.nr, "jmax": sp.jmax,
+            "form": "plain FP32 (FP64 accumulators)", "l2": "inputs larger than L2 "
+            f"(wavepacket state {2 * sp.nrot * sp.nr * 8 * wl.n_molecules / 1e9:.2f} GB per step)",
+            "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    a = _args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import numpy as np
+    import torch
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2209_04487_gb300 import build
+    if rank == 0:
+        build.build()
+    if dist:
+        dist.barrier()
+    from paper_2209_04487_gb300 import binding as B
+
+    wl = _workload(a.molecules)
+    sim = B.Simulation(wl)
+    sim.step(a.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = Clocks(local)
+    stream = sim.stream          # the stream the library launches on
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    sim.timing_begin()
+    ev0.record(stream)
+    sim.step(a.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    phases, nsteps, launches = sim.timing_end()
+    cl = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    P = sim.populations()
+    norm_err = float(np.abs(P.sum(axis=1) + sim.dissociation()[0].sum(axis=1) - 1.0).max())
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    sec = ms / 1e3
+    value = world * wl.n_molecules * a.steps / sec
+    cells_rate = world * wl.cells * a.steps / sec
+    sp = wl.species[0]
+    mol_bytes = 2 * 2 * sp.nrot * sp.nr * 8 + 12 + 80   # state read+write + field + records
+    bytes_launch = mol_bytes * wl.n_molecules
+    mol_ms = phases[1] / max(nsteps, 1)
+    achieved = bytes_launch / (mol_ms / 1e3) / 1e9
+    peak, peak_src = _peaks()
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": _kernel_traffic("mol_step_kernel"), "kernel": f"mol_step_kernel<{sp.nr}>",
+            "bytes_per_launch": bytes_launch, "peak_source": peak_src,
+            "note": "algorithmic bytes = FP32 wavepacket state read + written once per molecule-step"}
+
+    e2e = None
+    if not a.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = B.Simulation(wl)
+        host_in = (wl.mat_id.nbytes + wl.pos.nbytes + wl.quat.nbytes + wl.species_id.nbytes
+                   + wl.sim_id.nbytes)
+        for _ in range(a.steps):
+            s2.step(1)
+            s2.populations()
+        t1 = time.perf_counter()
+        s2.close()
+        e2e = {"value": world * wl.n_molecules * a.steps / (t1 - t0), "unit": UNIT,
+               "h2d_bytes_per_step": host_in / a.steps, "d2h_bytes_per_step": 16 * wl.n_molecules,
+               "note": "ms_create from host inputs + per step ms_step(1) and a D2H read of all "
+                       "populations, host wall clock"}
+
+    cpu = None
+    if rank == 0 and not a.no_cpu_baseline:
+        v, ts, tf, tm = _oracle_sample(wl)
+        cpu = {"value": v, "unit": UNIT, "cores": _cpu_desc(), "kind": "oracle",
+               "sample": f"FP64 numpy oracle: 2 field steps on the full grid ({tf:.2f} s/step) + 3 steps "
+                         f"of 500 of {wl.n_molecules} molecules ({tm:.2f} s/step scaled); numpy "
+                         "element-wise ops single-threaded, BLAS matmuls on up to all cores"}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": _config(wl), "cell_updates_per_s": cells_rate,
+                "phases_ms_per_step": {"h": phases[0] / nsteps, "molecules": phases[1] / nsteps,
+                                       "e": phases[2] / nsteps},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
+                "clocks": cl, "norm_bookkeeping_max_err": norm_err,
+                "forms": {"plain_fp32": value, "mixed_bf16x3": None}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * ms.h -- C ABI of the GB300 coupled Maxwell-Schroedinger time step.
+ *
+ * The library advances, on one GPU, the coupled system of arXiv 2209.04487:
+ *   - Maxwell's curl equations on a 3D Yee grid (Eq. 1), leap-frog, with a
+ *     Drude current in metal cells (Eq. 2), periodic x/y, convolutional PML
+ *     along z and a total-field/scattered-field plane-wave source
+ *     (section "The domain decomposition methodology for FDTD");
+ *   - an ensemble of diatomic molecules, each carrying ro-vibrational
+ *     wavepackets xi^{g,e}_{jm}(R) on a ground and an excited surface
+ *     (Eq. 3), advanced by split-operator steps of Eq. 4 with the effective
+ *     Hamiltonians of Eq. 5 (Morse ground surface Eq. 6, repulsive excited
+ *     surface of the Eq. 7 family, constant transition dipole) under the
+ *     local field E^n at the molecule's cell;
+ *   - the induced dipoles, multiplied by the molecular number density
+ *     (one molecule per molecule: 1/dx^3 per cell), enter Ampere's law as
+ *     the polarization current dP/dt (section "Efficient numerical
+ *     implementation of quantum dynamics ...").
+ *
+ * Conventions (all calls):
+ *   - Every input pointer is host memory owned by the caller; ms_create
+ *     copies what it needs, so the caller may free its buffers afterwards.
+ *   - Every output pointer is host memory allocated by the caller.
+ *   - Calls return an ms_status and never throw or abort.  A device-side
+ *     condition (non-finite field, coupling series that does not converge)
+ *     is latched in a device word and reported by the next ms_step or
+ *     ms_read_* call as MS_ENUMERIC.
+ *   - ms_step is asynchronous on the handle's stream; ms_read_* synchronise
+ *     that stream.  One handle must not be used from two threads at once.
+ *   - There is no CPU fallback: without a compute-capability-10.3 device
+ *     ms_create returns MS_EUNSUPPORTED.
+ *
+ * Array layouts:
+ *   grid arrays are [nsim][nz][ny][nx] with x fastest; cell (i,j,k) owns
+ *   Ex(i+1/2,j,k), Ey(i,j+1/2,k), Ez(i,j,k+1/2), Hx(i,j+1/2,k+1/2),
+ *   Hy(i+1/2,j,k+1/2), Hz(i+1/2,j+1/2,k).  E is in V/m at integer steps,
+ *   H in A/m at half steps.  Molecular quantities are in atomic units.
+ */
+#ifndef MS_H
+#define MS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ms_sim ms_sim; /* opaque; owned by the library */
+
+typedef enum {
+  MS_OK = 0,
+  MS_EINVAL = -1,       /* invalid descriptor or argument */
+  MS_ENOMEM = -2,       /* device allocation failed (nothing leaked) */
+  MS_ECUDA = -3,        /* a CUDA runtime call failed */
+  MS_ENUMERIC = -4,     /* latched device condition: non-finite value or
+                           a coupling exponential that did not converge */
+  MS_ETIMEOUT = -5,     /* reserved: bounded device wait gave up */
+  MS_EUNSUPPORTED = -6  /* no sm_103 device, or a configuration this build
+                           does not support */
+} ms_status;
+
+enum { MS_BC_PML = 0, MS_BC_PERIODIC = 1 };
+enum { MS_PREC_FP32 = 0, MS_PREC_MIXED_BF16X3 = 1 };
+enum { MS_DRIVE_FDTD = 0, MS_DRIVE_PRESCRIBED = 1 };
+enum { MS_FIELD_E = 0, MS_FIELD_H = 1 };
+
+/* Grid and source.  dt must satisfy dt <= dx/(sqrt(3) c) (checked).
+ * src_plane_z: absolute z index of the TF/SF plane (total field for
+ * k >= src_plane_z), -1 for no source; it must lie outside the z absorbers.
+ * src: nsim rows of 4 doubles: peak field E0 [V/m], carrier photon energy
+ * [eV], FWHM of the field envelope [s], time of the peak t0 [s]; the
+ * incident plane wave is x-polarised and travels towards +z with
+ * E(t) = E0 exp(-4 ln2 ((t-t0)/fwhm)^2) cos(w (t-t0)) at the plane. */
+typedef struct {
+  int32_t nx, ny, nz, nsim;
+  double dx_m, dt_s;
+  int32_t pml_cells;   /* CPML thickness at each z end (MS_BC_PML) */
+  int32_t bc_z;        /* MS_BC_PML or MS_BC_PERIODIC */
+  int32_t src_plane_z; /* -1 = no source */
+  const double* src;   /* [nsim][4], may be NULL when src_plane_z < 0 */
+} ms_grid_desc;
+
+/* Materials: n_materials entries of (eps_inf, plasma energy wp [eV],
+ * damping gamma [eV]); wp = 0 marks a non-dispersive dielectric with
+ * eps = eps_inf.  material_id: [nsim][nz][ny][nx] bytes, < n_materials. */
+typedef struct {
+  int32_t n_materials;
+  const double* eps_inf;
+  const double* wp_eV;
+  const double* gamma_eV;
+  const uint8_t* material_id;
+} ms_materials_desc;
+
+/* One molecular species (atomic units).  Radial grid r_i = rmin + i dR,
+ * dR = (rmax - rmin)/(nr - 1), nr in {64, 128, 256}; rotational channels
+ * j <= jmax, |m| <= j ((jmax+1)^2 per surface), jmax <= 8.
+ * Ground surface De (1 - exp(-a (r - re)))^2 - De (Eq. 6); excited surface
+ * A + B exp(-beta (r - rc)) (Eq. 7 is A = 0, B = 2 D_e); constant
+ * transition dipole d [e a0]; absorbing mask cos(pi/2 (r-ra)/(rmax-ra))^p
+ * for r > ra (ra >= rmax disables it). */
+typedef struct {
+  int32_t nr, jmax;
+  double rmin, rmax, mass_me;
+  double morse_De, morse_a, morse_re;
+  double exc_A, exc_B, exc_beta, exc_rc;
+  double dipole_ea0;
+  double absorber_r, absorber_power;
+} ms_species;
+
+/* Molecules: species_id, sim_id [n]; pos_m [n][3] absolute position in the
+ * sim's box (metres; cell = floor(pos/dx), a point on a face belongs to
+ * the upper cell); orient [n][4] unit quaternion (w,x,y,z) rotating the
+ * molecule frame into the lab frame.  Every molecule starts in the v=0,
+ * j=0, m=0 state of the ground surface. */
+typedef struct {
+  int32_t n_species;
+  const ms_species* species;
+  int64_t n_molecules;
+  const int32_t* species_id;
+  const int32_t* sim_id;
+  const double* pos_m;
+  const double* orient;
+} ms_molecules_desc;
+
+/* Options.  alloc/free: optional device allocator (e.g. a framework's
+ * caching allocator); when NULL the library uses cudaMalloc/cudaFree.
+ * stream: cudaStream_t to run on; NULL = a stream the library creates. */
+typedef struct {
+  int32_t precision;    /* MS_PREC_FP32 (MS_PREC_MIXED_BF16X3: see ms_create) */
+  int32_t mol_substeps; /* molecular step every mol_substeps field steps; 1 */
+  int32_t drive;        /* MS_DRIVE_FDTD or MS_DRIVE_PRESCRIBED */
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+  void* stream;
+} ms_options;
+
+/* Create a simulation: validates the descriptors, builds the species
+ * tables (potential and kinetic phases, angular coupling matrices, Fourier
+ * grid ground state), sorts molecules by cell, allocates and uploads.
+ * On failure *out is NULL and nothing is leaked. */
+ms_status ms_create(const ms_grid_desc* grid, const ms_materials_desc* materials,
+                    const ms_molecules_desc* molecules, const ms_options* opts,
+                    ms_sim** out);
+
+/* Advance n coupled steps (n >= 0) on the handle's stream, asynchronously.
+ * Step order: H update, molecular step under E^n, polarization change,
+ * E update (the paper's leap-frog with the molecular current). */
+ms_status ms_step(ms_sim* sim, int64_t n);
+
+/* Number of steps taken so far. */
+int64_t ms_step_count(const ms_sim* sim);
+
+/* Copy the E (which = MS_FIELD_E) or H field of one sim to host_dst,
+ * 3 * nz*ny*nx floats: all x components, then y, then z.  n is the
+ * capacity of host_dst in floats. */
+ms_status ms_read_fields(ms_sim* sim, int32_t which, int32_t sim_index, float* host_dst,
+                         size_t n);
+
+/* Overwrite the E or H field of one sim (same layout); for tests. */
+ms_status ms_write_fields(ms_sim* sim, int32_t which, int32_t sim_index, const float* src,
+                          size_t n);
+
+/* Per-molecule populations P_g, P_e (FP64) of molecules [first, first+count)
+ * in the caller's molecule order, at the current time.  Either output may
+ * be NULL. */
+ms_status ms_read_populations(ms_sim* sim, int64_t first, int64_t count, double* Pg,
+                              double* Pe);
+
+/* Per-molecule dissociation observables (FP64): norm removed by the
+ * absorber since t=0 on each surface, and the numerator <chi_e|R|chi_e>
+ * and denominator <chi_e|chi_e> of Eq. 8 at the current time.  Any output
+ * may be NULL. */
+ms_status ms_read_dissociation(ms_sim* sim, int64_t first, int64_t count, double* absorbed_g,
+                               double* absorbed_e, double* R_e_num, double* R_e_den);
+
+/* Per-molecule lab-frame induced dipole (a.u., FP64, [count][3]) at the
+ * current time. */
+ms_status ms_read_dipoles(ms_sim* sim, int64_t first, int64_t count, double* mu);
+
+/* Prescribed drive (MS_DRIVE_PRESCRIBED): molecule k sees the lab field
+ * amp[k][0..2] * wave[n] (V/m) during step n; the field grid is not
+ * advanced.  nsteps samples of wave; ms_step fails with MS_EINVAL beyond
+ * them. */
+ms_status ms_set_prescribed_field(ms_sim* sim, const float* amp, const float* wave,
+                                  int64_t nsteps);
+
+/* Phase timing with CUDA events on the handle's stream.  Between
+ * ms_timing_begin and ms_timing_end every ms_step records events around its
+ * three phases; ms_timing_end synchronises and writes the summed durations
+ * in milliseconds: out[0] H half step (H update and incident line),
+ * out[1] molecular step (all species), out[2] E half step (E update,
+ * incident line, step counter), out[3] their sum; *steps receives the
+ * number of steps timed and *launches the number of kernels launched. */
+ms_status ms_timing_begin(ms_sim* sim);
+ms_status ms_timing_end(ms_sim* sim, double out[4], int64_t* steps, int64_t* launches);
+
+/* Device memory held by the simulation, in bytes. */
+size_t ms_device_bytes(const ms_sim* sim);
+
+void ms_destroy(ms_sim* sim);
+const char* ms_status_string(ms_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MS_H */

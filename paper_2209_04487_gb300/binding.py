@@ -1,0 +1,268 @@
+"""ctypes binding of include/ms.h (argument marshalling only).
+
+Every step of the coupled time step runs in libms.so's CUDA kernels; this
+module converts NumPy arrays into the C descriptors, hands PyTorch's caching
+allocator and current stream to the library, and copies results back.  If the
+library cannot be loaded the import of this module fails: there is no
+Python or CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+MS_OK, MS_EINVAL, MS_ENOMEM, MS_ECUDA, MS_ENUMERIC, MS_ETIMEOUT, MS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+MS_BC_PML, MS_BC_PERIODIC = 0, 1
+MS_PREC_FP32, MS_PREC_MIXED_BF16X3 = 0, 1
+MS_DRIVE_FDTD, MS_DRIVE_PRESCRIBED = 0, 1
+MS_FIELD_E, MS_FIELD_H = 0, 1
+
+_ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+_FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class GridDesc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nsim", C.c_int32),
+                ("dx_m", C.c_double), ("dt_s", C.c_double), ("pml_cells", C.c_int32),
+                ("bc_z", C.c_int32), ("src_plane_z", C.c_int32), ("src", C.POINTER(C.c_double))]
+
+
+class MaterialsDesc(C.Structure):
+    _fields_ = [("n_materials", C.c_int32), ("eps_inf", C.POINTER(C.c_double)),
+                ("wp_eV", C.POINTER(C.c_double)), ("gamma_eV", C.POINTER(C.c_double)),
+                ("material_id", C.POINTER(C.c_uint8))]
+
+
+class SpeciesDesc(C.Structure):
+    _fields_ = [("nr", C.c_int32), ("jmax", C.c_int32), ("rmin", C.c_double), ("rmax", C.c_double),
+                ("mass_me", C.c_double), ("morse_De", C.c_double), ("morse_a", C.c_double),
+                ("morse_re", C.c_double), ("exc_A", C.c_double), ("exc_B", C.c_double),
+                ("exc_beta", C.c_double), ("exc_rc", C.c_double), ("dipole_ea0", C.c_double),
+                ("absorber_r", C.c_double), ("absorber_power", C.c_double)]
+
+
+class MoleculesDesc(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("species", C.POINTER(SpeciesDesc)),
+                ("n_molecules", C.c_int64), ("species_id", C.POINTER(C.c_int32)),
+                ("sim_id", C.POINTER(C.c_int32)), ("pos_m", C.POINTER(C.c_double)),
+                ("orient", C.POINTER(C.c_double))]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("mol_substeps", C.c_int32), ("drive", C.c_int32),
+                ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p)]
+
+
+def _load() -> C.CDLL:
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run paper_2209_04487_gb300.build.build() "
+                          "(or __graft_entry__.build()) first")
+    lib = C.CDLL(path)
+    P = C.POINTER
+    sig = {
+        "ms_create": (C.c_int, [P(GridDesc), P(MaterialsDesc), P(MoleculesDesc), P(Options), P(C.c_void_p)]),
+        "ms_step": (C.c_int, [C.c_void_p, C.c_int64]),
+        "ms_step_count": (C.c_int64, [C.c_void_p]),
+        "ms_read_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, P(C.c_float), C.c_size_t]),
+        "ms_write_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, P(C.c_float), C.c_size_t]),
+        "ms_read_populations": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, P(C.c_double), P(C.c_double)]),
+        "ms_read_dissociation": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, P(C.c_double),
+                                           P(C.c_double), P(C.c_double), P(C.c_double)]),
+        "ms_read_dipoles": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, P(C.c_double)]),
+        "ms_set_prescribed_field": (C.c_int, [C.c_void_p, P(C.c_float), P(C.c_float), C.c_int64]),
+        "ms_device_bytes": (C.c_size_t, [C.c_void_p]),
+        "ms_timing_begin": (C.c_int, [C.c_void_p]),
+        "ms_timing_end": (C.c_int, [C.c_void_p, P(C.c_double), P(C.c_int64), P(C.c_int64)]),
+        "ms_destroy": (None, [C.c_void_p]),
+        "ms_status_string": (C.c_char_p, [C.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+# every symbol include/ms.h declares
+EXPORTED = ("ms_create", "ms_step", "ms_step_count", "ms_read_fields", "ms_write_fields",
+            "ms_read_populations", "ms_read_dissociation", "ms_read_dipoles",
+            "ms_set_prescribed_field", "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
+            "ms_destroy", "ms_status_string")
+
+
+class MSError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {LIB.ms_status_string(code).decode()} ({code})")
+        self.code = code
+
+
+def _check(code: int, what: str):
+    if code != MS_OK:
+        raise MSError(code, what)
+
+
+def _ptr(a: Optional[np.ndarray], ct):
+    if a is None:
+        return None
+    return a.ctypes.data_as(C.POINTER(ct))
+
+
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator, kept alive by reference."""
+
+    def __init__(self):
+        import torch
+        self.torch = torch
+        self.live = {}
+        self.c_alloc = _ALLOC(self._alloc)
+        self.c_free = _FREE(self._free)
+
+    def _alloc(self, n, ctx):
+        try:
+            t = self.torch.empty(int(n), dtype=self.torch.uint8, device="cuda")
+        except Exception:
+            return None
+        p = t.data_ptr()
+        self.live[p] = t
+        return p
+
+    def _free(self, p, ctx):
+        self.live.pop(p, None)
+
+
+def species_desc(sp) -> SpeciesDesc:
+    return SpeciesDesc(sp.nr, sp.jmax, sp.rmin, sp.rmax, sp.mass, sp.De, sp.a, sp.re, sp.A, sp.B,
+                       sp.beta, sp.rc, sp.dipole, sp.absorber_r, sp.absorber_power)
+
+
+class Simulation:
+    """One coupled simulation on the current CUDA device (workload in the
+    layout of ``workloads.Workload``)."""
+
+    def __init__(self, wl, *, drive: int = MS_DRIVE_FDTD, precision: int = MS_PREC_FP32,
+                 with_molecules: bool = True, use_torch: bool = True, stream=None):
+        self.wl = wl
+        self._keep = []
+        src = np.ascontiguousarray(wl.src, np.float64) if wl.src_k >= 0 else None
+        self._keep.append(src)
+        g = GridDesc(wl.nx, wl.ny, wl.nz, wl.nsim, wl.dx, wl.dt, wl.pml,
+                     MS_BC_PML if wl.bc_z == "pml" else MS_BC_PERIODIC, wl.src_k, _ptr(src, C.c_double))
+        eps = np.array([m[0] for m in wl.materials], np.float64)
+        wp = np.array([m[1] for m in wl.materials], np.float64)
+        ga = np.array([m[2] for m in wl.materials], np.float64)
+        mid = np.ascontiguousarray(wl.mat_id, np.uint8)
+        self._keep += [eps, wp, ga, mid]
+        m = MaterialsDesc(len(wl.materials), _ptr(eps, C.c_double), _ptr(wp, C.c_double),
+                          _ptr(ga, C.c_double), _ptr(mid, C.c_uint8))
+        nmol = wl.n_molecules if with_molecules else 0
+        self.nmol = nmol
+        sp_arr = (SpeciesDesc * max(1, len(wl.species)))(*[species_desc(s) for s in wl.species])
+        sid = np.ascontiguousarray(wl.species_id[:nmol], np.int32)
+        simid = np.ascontiguousarray(wl.sim_id[:nmol], np.int32)
+        pos = np.ascontiguousarray(wl.pos[:nmol], np.float64)
+        quat = np.ascontiguousarray(wl.quat[:nmol], np.float64)
+        self._keep += [sp_arr, sid, simid, pos, quat]
+        d = MoleculesDesc(len(wl.species), sp_arr, nmol, _ptr(sid, C.c_int32), _ptr(simid, C.c_int32),
+                          _ptr(pos, C.c_double), _ptr(quat, C.c_double))
+        opts = Options()
+        opts.precision = precision
+        opts.mol_substeps = 1
+        opts.drive = drive
+        self.stream = None
+        if use_torch:
+            import torch
+            self._alloc = _TorchAllocator()
+            opts.alloc = self._alloc.c_alloc
+            opts.free = self._alloc.c_free
+            # a real (non-legacy-default) stream, so that torch events recorded
+            # on self.stream order with the library's launches
+            self.stream = stream if stream is not None else torch.cuda.Stream()
+            opts.stream = C.c_void_p(self.stream.cuda_stream)
+        else:
+            self._alloc = None
+            opts.alloc = _ALLOC()
+            opts.free = _FREE()
+            opts.stream = None
+        h = C.c_void_p()
+        _check(LIB.ms_create(C.byref(g), C.byref(m), C.byref(d), C.byref(opts), C.byref(h)), "ms_create")
+        self.h = h
+
+    # -- stepping ---------------------------------------------------------------
+    def step(self, n: int = 1):
+        _check(LIB.ms_step(self.h, int(n)), "ms_step")
+
+    @property
+    def steps(self) -> int:
+        return int(LIB.ms_step_count(self.h))
+
+    def set_prescribed(self, amp: np.ndarray, wave: np.ndarray):
+        a = np.ascontiguousarray(amp, np.float32)
+        w = np.ascontiguousarray(wave, np.float32)
+        _check(LIB.ms_set_prescribed_field(self.h, _ptr(a, C.c_float), _ptr(w, C.c_float), w.size),
+               "ms_set_prescribed_field")
+
+    # -- reads --------------------------------------------------------------------
+    def fields(self, which: int = MS_FIELD_E, sim: int = 0) -> np.ndarray:
+        n = self.wl.nx * self.wl.ny * self.wl.nz
+        out = np.empty(3 * n, np.float32)
+        _check(LIB.ms_read_fields(self.h, which, sim, _ptr(out, C.c_float), out.size), "ms_read_fields")
+        return out.reshape(3, self.wl.nz, self.wl.ny, self.wl.nx)
+
+    def write_fields(self, which: int, sim: int, arr: np.ndarray):
+        a = np.ascontiguousarray(arr, np.float32).ravel()
+        _check(LIB.ms_write_fields(self.h, which, sim, _ptr(a, C.c_float), a.size), "ms_write_fields")
+
+    def populations(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        count = self.nmol - first if count is None else count
+        pg = np.empty(count)
+        pe = np.empty(count)
+        _check(LIB.ms_read_populations(self.h, first, count, _ptr(pg, C.c_double), _ptr(pe, C.c_double)),
+               "ms_read_populations")
+        return np.stack([pg, pe], axis=1)
+
+    def dissociation(self, first: int = 0, count: Optional[int] = None):
+        count = self.nmol - first if count is None else count
+        ag, ae, rn, rd = (np.empty(count) for _ in range(4))
+        _check(LIB.ms_read_dissociation(self.h, first, count, _ptr(ag, C.c_double), _ptr(ae, C.c_double),
+                                        _ptr(rn, C.c_double), _ptr(rd, C.c_double)), "ms_read_dissociation")
+        return np.stack([ag, ae], axis=1), np.stack([rn, rd], axis=1)
+
+    def dipoles(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
+        count = self.nmol - first if count is None else count
+        mu = np.empty((count, 3))
+        _check(LIB.ms_read_dipoles(self.h, first, count, _ptr(mu, C.c_double)), "ms_read_dipoles")
+        return mu
+
+    def timing_begin(self):
+        _check(LIB.ms_timing_begin(self.h), "ms_timing_begin")
+
+    def timing_end(self):
+        """(ms per phase [H, molecules, E, total], steps timed, kernels launched)"""
+        out = (C.c_double * 4)()
+        st = C.c_int64()
+        ln = C.c_int64()
+        _check(LIB.ms_timing_end(self.h, out, C.byref(st), C.byref(ln)), "ms_timing_end")
+        return list(out), st.value, ln.value
+
+    @property
+    def device_bytes(self) -> int:
+        return int(LIB.ms_device_bytes(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            LIB.ms_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,795 @@
+// C ABI of the coupled Maxwell-Schroedinger library: validation, FP64 table
+// construction on the host, device allocation, the step sequence and reads.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ms.h"
+#include "ms_internal.cuh"
+
+namespace {
+
+using cplx = std::complex<double>;
+
+// CODATA 2018
+constexpr double kC0 = 299792458.0;
+constexpr double kMu0 = 1.25663706212e-6;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kHbarEVs = 6.582119569e-16;
+constexpr double kTau = 2.4188843265857e-17;  // atomic unit of time, s
+constexpr double kEA0 = 8.4783536255e-30;     // atomic unit of dipole, C m
+constexpr double kPi = 3.14159265358979323846;
+
+// CPML grading (Roden-Gedney form, kappa = 1)
+constexpr int kCpmlOrder = 3;
+constexpr double kCpmlAlphaMax = 0.05;  // S/m
+// incident line length (cells): exact for runs of up to ~4x this many steps
+constexpr int kAuxLen = 32768;
+
+// e^{i a} - 1 without cancellation
+cplx expm1i(double a) {
+  const double sh = std::sin(0.5 * a);
+  return cplx(-2.0 * sh * sh, std::sin(a));
+}
+
+float4 hilo(cplx z) {
+  const float ch = (float)z.real(), sh = (float)z.imag();
+  return make_float4(ch, sh, (float)(z.real() - (double)ch), (float)(z.imag() - (double)sh));
+}
+
+struct Alloc {
+  void* (*fn)(size_t, void*) = nullptr;
+  void (*fr)(void*, void*) = nullptr;
+  void* ctx = nullptr;
+};
+
+}  // namespace
+
+struct ms_sim {
+  Alloc al;
+  std::vector<void*> blocks;
+  size_t bytes = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int drive = MS_DRIVE_FDTD;
+  int nspecies = 0;
+  int64_t nmol = 0;
+  int64_t steps = 0;
+  int64_t nwave = 0;
+  ms::Grid g{};
+  ms::MolDev md{};
+  ms::SpeciesDev sp[ms::kMaxSpecies]{};
+  int* d_err = nullptr;
+  long long* d_step = nullptr;
+  // phase timing
+  bool timing = false;
+  std::vector<cudaEvent_t> events;   // 4 per timed step
+  int64_t timed_steps = 0, launches = 0;
+
+  void* alloc(size_t n) {
+    if (n == 0) n = 16;
+    void* p = nullptr;
+    if (al.fn) {
+      p = al.fn(n, al.ctx);
+    } else if (cudaMalloc(&p, n) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    if (p) {
+      blocks.push_back(p);
+      bytes += n;
+    }
+    return p;
+  }
+  void release() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+    events.clear();
+    for (void* p : blocks) {
+      if (al.fr) al.fr(p, al.ctx);
+      else cudaFree(p);
+    }
+    blocks.clear();
+    if (own_stream && stream) cudaStreamDestroy(stream);
+    stream = nullptr;
+  }
+};
+
+namespace {
+
+template <class T>
+ms_status upload(ms_sim* s, T** dst, const T* src, size_t n) {
+  void* p = s->alloc(n * sizeof(T));
+  if (!p) return MS_ENOMEM;
+  *dst = (T*)p;
+  if (src && n && cudaMemcpyAsync(p, src, n * sizeof(T), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+    return MS_ECUDA;
+  return MS_OK;
+}
+
+template <class T>
+ms_status zeros(ms_sim* s, T** dst, size_t n) {
+  void* p = s->alloc(n * sizeof(T));
+  if (!p) return MS_ENOMEM;
+  *dst = (T*)p;
+  if (cudaMemsetAsync(p, 0, n * sizeof(T), s->stream) != cudaSuccess) return MS_ECUDA;
+  return MS_OK;
+}
+
+#define MS_TRY(x)                      \
+  do {                                 \
+    const ms_status _st = (x);         \
+    if (_st != MS_OK) return _st;      \
+  } while (0)
+
+// ---- Fourier-grid Hamiltonian ground state (Marston-Balint-Kurti), by
+// inverse iteration with a Cholesky factorisation of H - sigma I, sigma
+// below the spectrum.
+bool fgh_ground_state(int n, double dR, double mass, const std::vector<double>& U,
+                      std::vector<double>& psi) {
+  std::vector<double> H((size_t)n * n, 0.0);
+  for (int a = 0; a < n; ++a)
+    for (int b = 0; b < n; ++b) {
+      double t = 0.0;
+      for (int p = -n / 2; p < n - n / 2; ++p) {
+        const double k = 2.0 * kPi * p / (n * dR);
+        t += k * k / (2.0 * mass) * std::cos(k * (a - b) * dR);
+      }
+      H[(size_t)a * n + b] = t / n;
+    }
+  double umin = U[0];
+  for (int a = 0; a < n; ++a) {
+    H[(size_t)a * n + a] += U[a];
+    umin = std::min(umin, U[a]);
+  }
+  const double sigma = umin - 1e-3 * std::max(1.0, std::fabs(umin));
+  for (int a = 0; a < n; ++a) H[(size_t)a * n + a] -= sigma;
+  // Cholesky H = L L^T (lower, in place)
+  for (int j = 0; j < n; ++j) {
+    double d = H[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= H[(size_t)j * n + k] * H[(size_t)j * n + k];
+    if (d <= 0.0) return false;
+    d = std::sqrt(d);
+    H[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double v = H[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) v -= H[(size_t)i * n + k] * H[(size_t)j * n + k];
+      H[(size_t)i * n + j] = v / d;
+    }
+  }
+  std::vector<double> x(n, 1.0), y(n);
+  for (int it = 0; it < 400; ++it) {
+    for (int i = 0; i < n; ++i) {  // L y = x
+      double v = x[i];
+      for (int k = 0; k < i; ++k) v -= H[(size_t)i * n + k] * y[k];
+      y[i] = v / H[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // L^T x = y
+      double v = y[i];
+      for (int k = i + 1; k < n; ++k) v -= H[(size_t)k * n + i] * x[k];
+      x[i] = v / H[(size_t)i * n + i];
+    }
+    double nn = 0.0;
+    for (double v : x) nn += v * v;
+    nn = std::sqrt(nn);
+    for (double& v : x) v /= nn;
+  }
+  int imax = 0;
+  for (int i = 1; i < n; ++i)
+    if (std::fabs(x[i]) > std::fabs(x[imax])) imax = i;
+  const double sgn = x[imax] < 0 ? -1.0 : 1.0;
+  double nrm = 0.0;
+  for (double v : x) nrm += v * v * dR;
+  nrm = std::sqrt(nrm);
+  psi.resize(n);
+  for (int i = 0; i < n; ++i) psi[i] = sgn * x[i] / nrm;
+  return true;
+}
+
+int channel(int j, int m) { return j * j + j + m; }
+
+ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const std::vector<int>& ids) {
+  ms::SpeciesDev& sp = s->sp[si];
+  const int nr = d.nr, J = d.jmax, nrot = (J + 1) * (J + 1);
+  sp.nr = nr;
+  sp.jmax = J;
+  sp.nrot = nrot;
+  sp.nmol = (int)ids.size();
+  const double dR = (d.rmax - d.rmin) / (nr - 1);
+  const double dtau = dt / kTau;
+  const double mu = d.mass_me;
+  sp.dR = (float)dR;
+  sp.theta = d.dipole_ea0 * dtau;
+  sp.dipole = d.dipole_ea0;
+  std::vector<double> r(nr), Ug(nr), Ue(nr);
+  for (int i = 0; i < nr; ++i) {
+    r[i] = d.rmin + i * dR;
+    const double e = 1.0 - std::exp(-d.morse_a * (r[i] - d.morse_re));
+    Ug[i] = d.morse_De * e * e - d.morse_De;
+    Ue[i] = d.exc_A + d.exc_B * std::exp(-d.exc_beta * (r[i] - d.exc_rc));
+  }
+  // potential phases per (surface, j, r)
+  std::vector<float4> vdelta((size_t)2 * (J + 1) * nr);
+  std::vector<float2> vhalf((size_t)2 * (J + 1) * nr);
+  for (int sf = 0; sf < 2; ++sf)
+    for (int j = 0; j <= J; ++j)
+      for (int i = 0; i < nr; ++i) {
+        const double V = (sf == 0 ? Ug[i] : Ue[i]) + j * (j + 1) / (2.0 * mu * r[i] * r[i]);
+        const size_t q = ((size_t)sf * (J + 1) + j) * nr + i;
+        vdelta[q] = hilo(expm1i(-V * dtau));
+        const cplx h = std::polar(1.0, -0.5 * V * dtau);
+        vhalf[q] = make_float2((float)h.real(), (float)h.imag());
+      }
+  // kinetic phases (natural DFT order) and four-step twiddles
+  std::vector<float4> kph(nr), kphi(nr), tw(nr);
+  for (int k = 0; k < nr; ++k) {
+    const int p = k < nr / 2 ? k : k - nr;
+    const double kk = 2.0 * kPi * p / (nr * dR);
+    kph[k] = hilo(expm1i(-kk * kk * dtau / (2.0 * mu)) / (double)nr);
+    kphi[k] = hilo(std::polar(1.0 / nr, +kk * kk * dtau / (4.0 * mu)));
+  }
+  const int N1 = nr == 64 ? 8 : 16, N2 = nr / N1;
+  for (int n1 = 0; n1 < N1; ++n1)
+    for (int k2 = 0; k2 < N2; ++k2) tw[n1 * N2 + k2] = hilo(std::polar(1.0, -2.0 * kPi * n1 * k2 / nr));
+  // absorber
+  std::vector<float2> mw(nr);
+  std::vector<float> rf(nr);
+  for (int i = 0; i < nr; ++i) {
+    double m = 1.0;
+    if (d.absorber_r < d.rmax && r[i] > d.absorber_r) {
+      const double x = (r[i] - d.absorber_r) / (d.rmax - d.absorber_r);
+      m = std::pow(std::max(std::cos(0.5 * kPi * x), 0.0), d.absorber_power);
+    }
+    mw[i] = make_float2((float)m, (float)(1.0 - m * m));
+    rf[i] = (float)r[i];
+  }
+  // coupling rows of R^hat = x X + y Y + z Z written with S+ = sin(t)e^{ip}:
+  // M = E+ S+ + E- S- + Ez Z, E+- = (E'x -+ i E'y)/2
+  auto a_c = [](int j, int m) { return std::sqrt(((j + 1.0) * (j + 1) - m * m) / ((2.0 * j + 1) * (2.0 * j + 3))); };
+  auto b_c = [](int j, int m) { return -std::sqrt((j + m + 1.0) * (j + m + 2) / ((2.0 * j + 1) * (2.0 * j + 3))); };
+  auto c_c = [](int j, int m) { return std::sqrt((j - m) * (j - m - 1.0) / ((2.0 * j - 1) * (2.0 * j + 1))); };
+  auto valid = [J](int j, int m) { return j >= 0 && j <= J && m >= -j && m <= j; };
+  std::vector<int4> cp((size_t)nrot * ms::kMaxCoupl, make_int4(-1, 0, 0, 0));
+  for (int j = 0; j <= J; ++j)
+    for (int m = -j; m <= j; ++m) {
+      int e = 0;
+      auto add = [&](int jn, int mn, int kind, double coef) {
+        if (!valid(jn, mn) || coef == 0.0) return;
+        float cf = (float)coef;
+        int bits;
+        std::memcpy(&bits, &cf, 4);
+        cp[(size_t)channel(j, m) * ms::kMaxCoupl + e++] = make_int4(channel(jn, mn), kind, bits, 0);
+      };
+      add(j - 1, m, 0, valid(j - 1, m) ? a_c(j - 1, m) : 0.0);  // Z
+      add(j + 1, m, 0, a_c(j, m));
+      add(j - 1, m - 1, 1, valid(j - 1, m - 1) ? b_c(j - 1, m - 1) : 0.0);  // S+ row
+      add(j + 1, m - 1, 1, valid(j + 1, m - 1) ? c_c(j + 1, m - 1) : 0.0);
+      add(j + 1, m + 1, 2, b_c(j, m));  // S- row
+      add(j - 1, m + 1, 2, j >= 1 ? c_c(j, m) : 0.0);
+    }
+  // initial state: v=0, j=0 Fourier-grid ground state, phi0 = T^{1/2} psi0
+  std::vector<double> psi0;
+  if (!fgh_ground_state(nr, dR, mu, Ug, psi0)) return MS_EINVAL;
+  std::vector<cplx> spec(nr), phi0(nr);
+  for (int p = -nr / 2; p < nr - nr / 2; ++p) {
+    const double k = 2.0 * kPi * p / (nr * dR);
+    cplx acc = 0.0;
+    for (int b = 0; b < nr; ++b) acc += psi0[b] * std::polar(1.0, -k * b * dR);
+    spec[p + nr / 2] = acc * std::polar(1.0, -k * k * dtau / (4.0 * mu));
+  }
+  for (int a = 0; a < nr; ++a) {
+    cplx acc = 0.0;
+    for (int p = -nr / 2; p < nr - nr / 2; ++p) {
+      const double k = 2.0 * kPi * p / (nr * dR);
+      acc += spec[p + nr / 2] * std::polar(1.0, k * a * dR);
+    }
+    phi0[a] = acc / (double)nr;
+  }
+  const size_t per = (size_t)2 * nrot * nr;
+  std::vector<float2> row0(nr);
+  for (int a = 0; a < nr; ++a) row0[a] = make_float2((float)phi0[a].real(), (float)phi0[a].imag());
+  MS_TRY(zeros(s, &sp.psi, per * ids.size()));
+  float2* d_row0 = nullptr;
+  MS_TRY(upload(s, &d_row0, row0.data(), row0.size()));
+  if (ms::launch_broadcast_row(sp.psi, d_row0, nr, per, (long long)ids.size(), s->stream) != cudaSuccess)
+    return MS_ECUDA;
+  MS_TRY(upload(s, (float4**)&sp.vdelta, vdelta.data(), vdelta.size()));
+  MS_TRY(upload(s, (float2**)&sp.vhalf, vhalf.data(), vhalf.size()));
+  MS_TRY(upload(s, (float4**)&sp.kdelta, kph.data(), kph.size()));
+  MS_TRY(upload(s, (float4**)&sp.kphase_inv, kphi.data(), kphi.size()));
+  MS_TRY(upload(s, (float4**)&sp.twiddle, tw.data(), tw.size()));
+  MS_TRY(upload(s, (float2**)&sp.maskw, mw.data(), mw.size()));
+  MS_TRY(upload(s, (float**)&sp.r, rf.data(), rf.size()));
+  MS_TRY(upload(s, (int4**)&sp.coupl, cp.data(), cp.size()));
+  MS_TRY(upload(s, (int**)&sp.mol, ids.data(), ids.size()));
+  // populations at t = 0
+  double n0 = 0.0;
+  for (double v : psi0) n0 += v * v * dR;
+  std::vector<double> pop(2 * ids.size());
+  for (size_t q = 0; q < ids.size(); ++q) {
+    pop[2 * q] = n0;
+    pop[2 * q + 1] = 0.0;
+  }
+  for (size_t q = 0; q < ids.size(); ++q)
+    if (cudaMemcpyAsync(s->md.pop + 2 * (size_t)ids[q], &pop[2 * q], 2 * sizeof(double),
+                        cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+      return MS_ECUDA;
+  return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
+}
+
+ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const ms_molecules_desc* D,
+                      const ms_options* O, ms_sim* s) {
+  const int nx = G->nx, ny = G->ny, nz = G->nz, nsim = G->nsim;
+  const long long ncs = (long long)nx * ny * nz;
+  const long long ncell = ncs * nsim;
+  const double dx = G->dx_m, dt = G->dt_s;
+  s->drive = O ? O->drive : MS_DRIVE_FDTD;
+  s->nmol = D ? D->n_molecules : 0;
+  s->nspecies = D ? D->n_species : 0;
+  ms::Grid& g = s->g;
+  g.nx = nx;
+  g.ny = ny;
+  g.nz = nz;
+  g.nsim = nsim;
+  g.ncell_sim = ncs;
+  g.ch = (float)(dt / (kMu0 * dx));
+  g.ce_vac = (float)(dt / (kEps0 * dx));
+  g.periodic_z = G->bc_z == MS_BC_PERIODIC;
+  g.dt = dt;
+  MS_TRY(zeros(s, &g.step, 1));
+  s->d_step = g.step;
+  MS_TRY(zeros(s, &s->d_err, 1));
+  // materials
+  ms::MaterialCoef* mc = g.mc;
+  for (int i = 0; i < M->n_materials; ++i) {
+    const double er = M->eps_inf[i];
+    mc[i].ce = (float)(dt / (kEps0 * er * dx));
+    mc[i].cj = (float)(dt / (kEps0 * er));
+    mc[i].cp = (float)(kEA0 / (dx * dx * dx * kEps0 * er));
+    mc[i].metal = M->wp_eV[i] > 0;
+    if (mc[i].metal) {
+      const double wp = M->wp_eV[i] / kHbarEVs, ga = M->gamma_eV[i] / kHbarEVs;
+      const double den = 1.0 + 0.5 * ga * dt;
+      mc[i].alpha = (float)((1.0 - 0.5 * ga * dt) / den);
+      mc[i].beta = (float)(kEps0 * wp * wp * dt / den);
+    } else {
+      mc[i].alpha = 1.f;
+      mc[i].beta = 0.f;
+    }
+  }
+  if (s->drive == MS_DRIVE_FDTD) {
+    for (int c = 0; c < 3; ++c) {
+      MS_TRY(zeros(s, &g.E[c], ncell));
+      MS_TRY(zeros(s, &g.H[c], ncell));
+    }
+    MS_TRY(upload(s, (uint8_t**)&g.mat, M->material_id, ncell));
+    // Drude slab: z range holding metal cells
+    int jk0 = nz, jk1 = 0;
+    for (long long c = 0; c < ncell; ++c)
+      if (M->wp_eV[M->material_id[c]] > 0) {
+        const int k = (int)((c / ((long long)nx * ny)) % nz);
+        jk0 = std::min(jk0, k);
+        jk1 = std::max(jk1, k + 1);
+      }
+    if (jk1 <= jk0) jk0 = jk1 = 0;
+    g.jk0 = jk0;
+    g.jk1 = jk1;
+    const long long nj = (long long)nsim * (jk1 - jk0) * nx * ny;
+    for (int c = 0; c < 3; ++c) MS_TRY(zeros(s, &g.J[c], nj > 0 ? nj : 1));
+    // CPML
+    g.pml = G->bc_z == MS_BC_PML ? G->pml_cells : 0;
+    std::vector<float4> cpml(nz, make_float4(1.f, 0.f, 1.f, 0.f));
+    if (g.pml > 0) {
+      const double L = g.pml * dx;
+      const double eta0 = std::sqrt(kMu0 / kEps0);
+      const double smax = 0.8 * (kCpmlOrder + 1) / (eta0 * dx);
+      auto prof = [&](double z, float* b, float* a) {
+        const double rho = std::max(L - z, 0.0) + std::max(z - (nz * dx - L), 0.0);
+        if (rho <= 0.0) {
+          *b = 1.f;
+          *a = 0.f;
+          return;
+        }
+        const double sg = smax * std::pow(rho / L, kCpmlOrder);
+        const double al = kCpmlAlphaMax * (1.0 - rho / L);
+        const double bb = std::exp(-(sg + al) * dt / kEps0);
+        *b = (float)bb;
+        *a = (float)(sg > 0 ? sg / (sg + al) * (bb - 1.0) : 0.0);
+      };
+      for (int k = 0; k < nz; ++k) {
+        prof(k * dx, &cpml[k].x, &cpml[k].y);
+        prof((k + 0.5) * dx, &cpml[k].z, &cpml[k].w);
+      }
+      const long long np = (long long)nsim * 2 * g.pml * nx * ny;
+      for (int c = 0; c < 2; ++c) {
+        MS_TRY(zeros(s, &g.psiE[c], np));
+        MS_TRY(zeros(s, &g.psiH[c], np));
+      }
+    }
+    MS_TRY(upload(s, (float4**)&g.cpml, cpml.data(), cpml.size()));
+    // TF/SF source
+    g.ks = G->src_plane_z;
+    g.aux_len = kAuxLen;
+    if (g.ks >= 0) {
+      std::vector<ms::SrcParam> sp(nsim);
+      for (int q = 0; q < nsim; ++q) {
+        sp[q].E0 = G->src[4 * q];
+        sp[q].w = G->src[4 * q + 1] / kHbarEVs;
+        sp[q].fwhm = G->src[4 * q + 2];
+        sp[q].t0 = G->src[4 * q + 3];
+      }
+      MS_TRY(upload(s, (ms::SrcParam**)&g.src, sp.data(), sp.size()));
+      std::vector<float> aE((size_t)nsim * (kAuxLen + 1), 0.f);
+      for (int q = 0; q < nsim; ++q) {
+        const double x = (0.0 - sp[q].t0) / sp[q].fwhm;
+        aE[(size_t)q * (kAuxLen + 1)] =
+            (float)(sp[q].E0 * std::exp(-4.0 * std::log(2.0) * x * x) * std::cos(sp[q].w * (0.0 - sp[q].t0)));
+      }
+      MS_TRY(upload(s, &g.auxE, aE.data(), aE.size()));
+      MS_TRY(zeros(s, &g.auxH, (size_t)nsim * kAuxLen));
+    }
+  } else {
+    g.ks = -1;
+  }
+  // molecules
+  const long long n = s->nmol;
+  ms::MolDev& md = s->md;
+  md.n = n;
+  std::vector<int> cell(n > 0 ? n : 1, -1);
+  std::vector<float> rot(9 * (n > 0 ? n : 1), 0.f);
+  int mk0 = nz, mk1 = 0;
+  for (long long q = 0; q < n; ++q) {
+    const int ci = (int)std::floor(D->pos_m[3 * q] / dx);
+    const int cj = (int)std::floor(D->pos_m[3 * q + 1] / dx);
+    const int ck = (int)std::floor(D->pos_m[3 * q + 2] / dx);
+    const int sm = D->sim_id ? D->sim_id[q] : 0;
+    cell[q] = (int)(((long long)sm * nz + ck) * ny * nx + (long long)cj * nx + ci);
+    mk0 = std::min(mk0, ck);
+    mk1 = std::max(mk1, ck + 1);
+    double w = D->orient[4 * q], x = D->orient[4 * q + 1], y = D->orient[4 * q + 2], z = D->orient[4 * q + 3];
+    const double nn = std::sqrt(w * w + x * x + y * y + z * z);
+    w /= nn; x /= nn; y /= nn; z /= nn;
+    const double R[9] = {1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+                         2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+                         2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)};
+    for (int e = 0; e < 9; ++e) rot[9 * q + e] = (float)R[e];
+  }
+  if (n == 0) mk0 = mk1 = 0;
+  g.mk0 = mk0;
+  g.mk1 = mk1;
+  MS_TRY(upload(s, (int**)&md.cell, cell.data(), cell.size()));
+  MS_TRY(upload(s, (float**)&md.rot, rot.data(), rot.size()));
+  const size_t nn1 = n > 0 ? n : 1;
+  MS_TRY(zeros(s, &md.mu, 3 * nn1));
+  MS_TRY(zeros(s, &md.dmu, 3 * nn1));
+  MS_TRY(zeros(s, &md.pop, 2 * nn1));
+  MS_TRY(zeros(s, &md.absorbed, 2 * nn1));
+  MS_TRY(zeros(s, &md.Rnum, nn1));
+  MS_TRY(zeros(s, &md.Rden, nn1));
+  g.dmu = md.dmu;
+  if (s->drive == MS_DRIVE_FDTD && n > 0) {
+    // CSR over the molecule slab: cells sorted, molecules of a cell in id order
+    const long long nsl = (long long)nsim * (mk1 - mk0) * ny * nx;
+    std::vector<int> off(nsl + 1, 0), lst(n);
+    std::vector<long long> sl(n);
+    for (long long q = 0; q < n; ++q) {
+      const long long c = cell[q];
+      const long long sm = c / ncs, rem = c % ncs;
+      const long long k = rem / ((long long)nx * ny), ij = rem % ((long long)nx * ny);
+      sl[q] = (sm * (mk1 - mk0) + (k - mk0)) * nx * ny + ij;
+      off[sl[q] + 1]++;
+    }
+    for (long long c = 0; c < nsl; ++c) off[c + 1] += off[c];
+    std::vector<int> fill(off.begin(), off.end() - 1);
+    for (long long q = 0; q < n; ++q) lst[fill[sl[q]]++] = (int)q;
+    MS_TRY(upload(s, (int**)&g.cell_off, off.data(), off.size()));
+    MS_TRY(upload(s, (int**)&g.cell_mol, lst.data(), lst.size()));
+  }
+  // species
+  for (int si = 0; si < s->nspecies; ++si) {
+    std::vector<int> ids;
+    for (long long q = 0; q < n; ++q)
+      if (D->species_id[q] == si) ids.push_back((int)q);
+    MS_TRY(build_species(s, si, D->species[si], dt, ids));
+  }
+  return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
+}
+
+ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_molecules_desc* D,
+                   const ms_options* O) {
+  if (!G || !M) return MS_EINVAL;
+  if (G->nx <= 0 || G->ny <= 0 || G->nz <= 2 || G->nsim <= 0) return MS_EINVAL;
+  if (!(G->dx_m > 0) || !(G->dt_s > 0)) return MS_EINVAL;
+  if (G->dt_s > G->dx_m / (std::sqrt(3.0) * kC0)) return MS_EINVAL;
+  const long long ncell = (long long)G->nx * G->ny * G->nz * G->nsim;
+  if (ncell >= (1LL << 31)) return MS_EUNSUPPORTED;
+  if (G->bc_z != MS_BC_PML && G->bc_z != MS_BC_PERIODIC) return MS_EINVAL;
+  if (G->bc_z == MS_BC_PML && (G->pml_cells < 0 || 2 * G->pml_cells >= G->nz)) return MS_EINVAL;
+  if (G->src_plane_z >= 0) {
+    if (!G->src || G->bc_z != MS_BC_PML) return MS_EINVAL;
+    if (G->src_plane_z < G->pml_cells + 2 || G->src_plane_z >= G->nz - G->pml_cells) return MS_EINVAL;
+    for (int q = 0; q < G->nsim; ++q)
+      if (!(G->src[4 * q + 2] > 0)) return MS_EINVAL;
+  }
+  if (M->n_materials <= 0 || M->n_materials > ms::kMaxMaterials || !M->eps_inf || !M->wp_eV ||
+      !M->gamma_eV || !M->material_id)
+    return MS_EINVAL;
+  for (int i = 0; i < M->n_materials; ++i)
+    if (!(M->eps_inf[i] > 0) || M->wp_eV[i] < 0 || M->gamma_eV[i] < 0) return MS_EINVAL;
+  for (long long c = 0; c < ncell; ++c)
+    if (M->material_id[c] >= M->n_materials) return MS_EINVAL;
+  const int drive = O ? O->drive : MS_DRIVE_FDTD;
+  if (drive != MS_DRIVE_FDTD && drive != MS_DRIVE_PRESCRIBED) return MS_EINVAL;
+  if (O && O->precision != MS_PREC_FP32) return MS_EUNSUPPORTED;
+  if (O && O->mol_substeps != 0 && O->mol_substeps != 1) return MS_EUNSUPPORTED;
+  if (O && ((O->alloc == nullptr) != (O->free == nullptr))) return MS_EINVAL;
+  if (D && D->n_molecules > 0) {
+    if (D->n_species <= 0 || D->n_species > ms::kMaxSpecies || !D->species || !D->species_id ||
+        !D->pos_m || !D->orient)
+      return MS_EINVAL;
+    if (D->n_molecules >= (1LL << 31)) return MS_EUNSUPPORTED;
+    for (int si = 0; si < D->n_species; ++si) {
+      const ms_species& sp = D->species[si];
+      if (sp.nr != 64 && sp.nr != 128 && sp.nr != 256) return MS_EUNSUPPORTED;
+      if (sp.jmax < 0 || sp.jmax > ms::kMaxJ) return MS_EUNSUPPORTED;
+      if (!(sp.rmax > sp.rmin) || !(sp.rmin > 0) || !(sp.mass_me > 0) || sp.absorber_power < 0)
+        return MS_EINVAL;
+      if (ms::mol_step_smem(sp.nr, (sp.jmax + 1) * (sp.jmax + 1)) > 227 * 1024) return MS_EUNSUPPORTED;
+    }
+    for (long long q = 0; q < D->n_molecules; ++q) {
+      const int si = D->species_id[q];
+      if (si < 0 || si >= D->n_species) return MS_EINVAL;
+      const int sm = D->sim_id ? D->sim_id[q] : 0;
+      if (sm < 0 || sm >= G->nsim) return MS_EINVAL;
+      const double* p = D->pos_m + 3 * q;
+      const int ext[3] = {G->nx, G->ny, G->nz};
+      for (int a = 0; a < 3; ++a) {
+        const double c = std::floor(p[a] / G->dx_m);
+        if (!(c >= 0) || c >= ext[a]) return MS_EINVAL;
+      }
+      const double* o = D->orient + 4 * q;
+      const double nn = o[0] * o[0] + o[1] * o[1] + o[2] * o[2] + o[3] * o[3];
+      if (!(nn > 1e-12) || !std::isfinite(nn)) return MS_EINVAL;
+    }
+  }
+  return MS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ms_status_string(ms_status s) {
+  switch (s) {
+    case MS_OK: return "ok";
+    case MS_EINVAL: return "invalid argument";
+    case MS_ENOMEM: return "device allocation failed";
+    case MS_ECUDA: return "CUDA runtime error";
+    case MS_ENUMERIC: return "non-finite value or coupling series out of range";
+    case MS_ETIMEOUT: return "device wait timed out";
+    case MS_EUNSUPPORTED: return "unsupported device or configuration";
+  }
+  return "unknown status";
+}
+
+ms_status ms_create(const ms_grid_desc* grid, const ms_materials_desc* materials,
+                    const ms_molecules_desc* molecules, const ms_options* opts, ms_sim** out) {
+  if (!out) return MS_EINVAL;
+  *out = nullptr;
+  const ms_status v = validate(grid, materials, molecules, opts);
+  if (v != MS_OK) return v;
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return MS_EUNSUPPORTED;
+  }
+  if (prop.major != 10 || prop.minor != 3) return MS_EUNSUPPORTED;
+  ms_sim* s = new (std::nothrow) ms_sim();
+  if (!s) return MS_ENOMEM;
+  if (opts && opts->alloc) {
+    s->al.fn = opts->alloc;
+    s->al.fr = opts->free;
+    s->al.ctx = opts->alloc_ctx;
+  }
+  if (opts && opts->stream) {
+    s->stream = (cudaStream_t)opts->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete s;
+      return MS_ECUDA;
+    }
+    s->own_stream = true;
+  }
+  const ms_status st = create_impl(grid, materials, molecules, opts, s);
+  if (st != MS_OK) {
+    cudaGetLastError();
+    s->release();
+    delete s;
+    return st;
+  }
+  *out = s;
+  return MS_OK;
+}
+
+static ms_status latched(ms_sim* s) {
+  int e = 0;
+  if (cudaMemcpyAsync(&e, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+    return MS_ECUDA;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
+  if (e & ms::kErrPrescribedRange) return MS_EINVAL;
+  return e ? MS_ENUMERIC : MS_OK;
+}
+
+static cudaEvent_t mark(ms_sim* s) {
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  cudaEventRecord(e, s->stream);
+  s->events.push_back(e);
+  return e;
+}
+
+ms_status ms_step(ms_sim* s, int64_t n) {
+  if (!s || n < 0) return MS_EINVAL;
+  if (s->drive == MS_DRIVE_PRESCRIBED && s->nmol > 0 && s->steps + n > s->nwave) return MS_EINVAL;
+  const bool fdtd = s->drive == MS_DRIVE_FDTD;
+  const bool src = fdtd && s->g.ks >= 0;
+  int per_step = 1;  // step counter
+  if (fdtd) per_step += 2 + (src ? 2 : 0);
+  for (int si = 0; si < s->nspecies; ++si) per_step += s->sp[si].nmol > 0;
+  for (int64_t q = 0; q < n; ++q) {
+    if (s->timing) mark(s);
+    if (fdtd) {
+      ms::launch_yee_h(s->g, s->stream);
+      ms::launch_aux_h(s->g, s->stream);
+    }
+    if (s->timing) mark(s);
+    for (int si = 0; si < s->nspecies; ++si)
+      ms::launch_mol_step(s->sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
+    if (s->timing) mark(s);
+    if (fdtd) {
+      ms::launch_yee_e(s->g, s->stream);
+      ms::launch_aux_e(s->g, s->stream);
+    }
+    ms::launch_step_counter(s->d_step, s->stream);
+    if (s->timing) {
+      mark(s);
+      s->timed_steps++;
+      s->launches += per_step;
+    }
+  }
+  s->steps += n;
+  return cudaGetLastError() == cudaSuccess ? MS_OK : MS_ECUDA;
+}
+
+ms_status ms_timing_begin(ms_sim* s) {
+  if (!s) return MS_EINVAL;
+  for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+  s->events.clear();
+  s->timed_steps = 0;
+  s->launches = 0;
+  s->timing = true;
+  return MS_OK;
+}
+
+ms_status ms_timing_end(ms_sim* s, double out[4], int64_t* steps, int64_t* launches) {
+  if (!s || !out) return MS_EINVAL;
+  s->timing = false;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
+  double acc[3] = {0, 0, 0};
+  for (size_t b = 0; b + 3 < s->events.size(); b += 4)
+    for (int p = 0; p < 3; ++p) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, s->events[b + p], s->events[b + p + 1]) != cudaSuccess) return MS_ECUDA;
+      acc[p] += ms;
+    }
+  out[0] = acc[0];
+  out[1] = acc[1];
+  out[2] = acc[2];
+  out[3] = acc[0] + acc[1] + acc[2];
+  if (steps) *steps = s->timed_steps;
+  if (launches) *launches = s->launches;
+  for (cudaEvent_t e : s->events) cudaEventDestroy(e);
+  s->events.clear();
+  return MS_OK;
+}
+
+int64_t ms_step_count(const ms_sim* s) { return s ? s->steps : -1; }
+
+ms_status ms_read_fields(ms_sim* s, int32_t which, int32_t sim, float* dst, size_t n) {
+  if (!s || !dst || s->drive != MS_DRIVE_FDTD || sim < 0 || sim >= s->g.nsim) return MS_EINVAL;
+  const size_t per = (size_t)s->g.ncell_sim;
+  if (n < 3 * per || (which != MS_FIELD_E && which != MS_FIELD_H)) return MS_EINVAL;
+  float* const* src = which == MS_FIELD_E ? s->g.E : s->g.H;
+  for (int c = 0; c < 3; ++c)
+    if (cudaMemcpyAsync(dst + c * per, src[c] + (size_t)sim * per, per * sizeof(float),
+                        cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+      return MS_ECUDA;
+  return latched(s);
+}
+
+ms_status ms_write_fields(ms_sim* s, int32_t which, int32_t sim, const float* src, size_t n) {
+  if (!s || !src || s->drive != MS_DRIVE_FDTD || sim < 0 || sim >= s->g.nsim) return MS_EINVAL;
+  const size_t per = (size_t)s->g.ncell_sim;
+  if (n < 3 * per || (which != MS_FIELD_E && which != MS_FIELD_H)) return MS_EINVAL;
+  float* const* dst = which == MS_FIELD_E ? s->g.E : s->g.H;
+  for (int c = 0; c < 3; ++c)
+    if (cudaMemcpyAsync(dst[c] + (size_t)sim * per, src + c * per, per * sizeof(float),
+                        cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+      return MS_ECUDA;
+  return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
+}
+
+static ms_status read_range(ms_sim* s, const double* dev, int width, int64_t first, int64_t count, double* dst) {
+  if (!dst) return MS_OK;
+  if (cudaMemcpyAsync(dst, dev + (size_t)width * first, (size_t)width * count * sizeof(double),
+                      cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+    return MS_ECUDA;
+  return MS_OK;
+}
+
+static ms_status read_pairs(ms_sim* s, const double* dev, int64_t first, int64_t count, double* a, double* b) {
+  if (!a && !b) return MS_OK;
+  std::vector<double> tmp(2 * (size_t)count);
+  MS_TRY(read_range(s, dev, 2, first, count, tmp.data()));
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
+  for (int64_t q = 0; q < count; ++q) {
+    if (a) a[q] = tmp[2 * q];
+    if (b) b[q] = tmp[2 * q + 1];
+  }
+  return MS_OK;
+}
+
+ms_status ms_read_populations(ms_sim* s, int64_t first, int64_t count, double* Pg, double* Pe) {
+  if (!s || first < 0 || count < 0 || first + count > s->nmol) return MS_EINVAL;
+  MS_TRY(read_pairs(s, s->md.pop, first, count, Pg, Pe));
+  return latched(s);
+}
+
+ms_status ms_read_dissociation(ms_sim* s, int64_t first, int64_t count, double* ag, double* ae,
+                               double* Rnum, double* Rden) {
+  if (!s || first < 0 || count < 0 || first + count > s->nmol) return MS_EINVAL;
+  MS_TRY(read_pairs(s, s->md.absorbed, first, count, ag, ae));
+  if (Rnum || Rden) {
+    for (int si = 0; si < s->nspecies; ++si) ms::launch_mol_observe(s->sp[si], s->md, s->stream);
+    if (cudaGetLastError() != cudaSuccess) return MS_ECUDA;
+    MS_TRY(read_range(s, s->md.Rnum, 1, first, count, Rnum));
+    MS_TRY(read_range(s, s->md.Rden, 1, first, count, Rden));
+  }
+  return latched(s);
+}
+
+ms_status ms_read_dipoles(ms_sim* s, int64_t first, int64_t count, double* mu) {
+  if (!s || !mu || first < 0 || count < 0 || first + count > s->nmol) return MS_EINVAL;
+  MS_TRY(read_range(s, s->md.mu, 3, first, count, mu));
+  return latched(s);
+}
+
+ms_status ms_set_prescribed_field(ms_sim* s, const float* amp, const float* wave, int64_t nsteps) {
+  if (!s || !amp || !wave || nsteps <= 0 || s->drive != MS_DRIVE_PRESCRIBED) return MS_EINVAL;
+  if (s->md.amp == nullptr) MS_TRY(upload(s, (float**)&s->md.amp, amp, 3 * (size_t)(s->nmol > 0 ? s->nmol : 1)));
+  else if (cudaMemcpyAsync((void*)s->md.amp, amp, 3 * sizeof(float) * s->nmol, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+    return MS_ECUDA;
+  float* w = nullptr;
+  MS_TRY(upload(s, &w, wave, (size_t)nsteps));
+  s->md.wave = w;
+  s->md.nwave = nsteps;
+  s->nwave = nsteps;
+  return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
+}
+
+size_t ms_device_bytes(const ms_sim* s) { return s ? s->bytes : 0; }
+
+void ms_destroy(ms_sim* s) {
+  if (!s) return;
+  s->release();
+  delete s;
+}
+
+}  // extern "C"

