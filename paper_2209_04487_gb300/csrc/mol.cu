@@ -1,25 +1,29 @@
 // Molecular split-operator step (Eqs. 3-5 with the surfaces of Eqs. 6-7),
 // one CTA per molecule, the molecule's whole state resident in shared memory.
 //
-// The library stores phi = T^{1/2} psi, so that one coupled step is
-//   chi  = Mask V^{1/2} K(E') V^{1/2} phi      (R-space pass, per radial point)
-//   phi' = T chi                               (kinetic pass, per channel)
+// The library stores s = T^{-1/2} psi, so that one coupled step is
+//   u  = T s                                   (kinetic pass, per channel)
+//   s' = Mask V^{1/2} K(E') V^{1/2} u          (R-space pass, per radial point)
 // which equals the paper's split-operator step T^{1/2} Mask V^{1/2} K V^{1/2}
 // T^{1/2} on psi (T commutes with the angular coupling because the
 // transition dipole is R-independent, and is unitary per channel, so
-// populations and the dipole can be taken from chi).
+// populations and the dipole can be taken from s').
 //
 // Norm-preserving FP32 arithmetic: every unit-modulus factor (potential
 // phase, kinetic phase, FFT twiddle) is carried as an FP32 hi+lo pair and
 // applied with a compensated product, so the factor is exact to ~1e-15 and
 // only unbiased output rounding remains.  Every factor of the step is close
 // to the identity (|V dtau| and |k^2 dtau/2mu| are a few 1e-2), so the step
-// is computed as a correction: d1 = (V - 1) phi + V^{1/2} S with
-// S = sum_{n>=1} (i theta sigma_x M)^n/n! V^{1/2} phi (Taylor series of the
-// coupling exponential, |theta M| << 1), chi = phi + d1,
-// d2 = (T - 1) chi, and phi' = phi + (d1 + d2): the full-magnitude state is
-// rounded once per step, which keeps the FP32 norm error a random walk of
-// about 1e-8 per step instead of a drift.
+// is computed as a correction: d2 = (T - 1) s, u = s + d2,
+// d1 = (V - 1) u + V^{1/2} S with S = sum_{n>=1} (i theta sigma_x M)^n/n!
+// V^{1/2} u (Taylor series of the coupling exponential, |theta M| << 1), and
+// s' = s + (d2 + d1): the full-magnitude state is rounded once per step,
+// which keeps the FP32 norm error a random walk of about 1e-8 per step
+// instead of a drift.  The coupling is evaluated in the frame turned about
+// z that puts E' in the xz plane (a diagonal phase on the correction only),
+// where M is real.
+#include <cmath>
+
 #include "ms_internal.cuh"
 
 namespace ms {
@@ -32,11 +36,11 @@ template <int NR>
 struct FFTShape;
 template <>
 struct FFTShape<64> {
-  static constexpr int N1 = 8, N2 = 8, THREADS = 128;
+  static constexpr int N1 = 8, N2 = 8, THREADS = 256;
 };
 template <>
 struct FFTShape<128> {
-  static constexpr int N1 = 16, N2 = 8, THREADS = 128;
+  static constexpr int N1 = 16, N2 = 8, THREADS = 256;
 };
 template <>
 struct FFTShape<256> {
@@ -84,9 +88,9 @@ __device__ __forceinline__ float2 twiddle16(float2 v) {
   } else if constexpr (T == 4) {
     return INV ? make_float2(-v.y, v.x) : make_float2(v.y, -v.x);
   } else {
-    constexpr double c = cos_pi8(T);
-    constexpr double s = INV ? sin_pi8(T) : -sin_pi8(T);
-    return cmul_c(v, hi_of(c), hi_of(s), lo_of(c), lo_of(s));
+    constexpr float c = (float)cos_pi8(T);
+    constexpr float s = INV ? (float)sin_pi8(T) : -(float)sin_pi8(T);
+    return make_float2(fmaf(v.x, c, -v.y * s), fmaf(v.x, s, v.y * c));
   }
 }
 
@@ -140,27 +144,19 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Four-step FFT kinetic pass on all `rows` rows (each NR complex, stride
-// NRP) held in shared memory: forward DFT, multiply by kph[k], inverse DFT.
-// n = n1 + N1 n2, k = k2 + N2 k1.  Step A: per n1, an N2-point DFT over n2
-// and the twiddle exp(-2 pi i n1 k2/NR); step B: per k2, an N1-point DFT
-// over n1.  Intermediate y[n1][k2] lives at n1 + N1 k2 (xor-swizzled within
-// each block of N1 so that step B is bank-conflict free).
-// MODE kInPlace: st <- T st (kph = full phases / NR).
-// MODE kDeltaOut: st holds chi = phi + d1 and D holds d1; with kph the
-// phase deltas (P_k - 1)/NR the pass forms d2 = (T - 1) chi and writes
-// phi' = phi + (d1 + d2) to gout, where gout still holds phi: the whole
-// step reaches the stored state through a single FP32 rounding.
-enum { kInPlace = 0, kDeltaOut = 1 };
-
-template <int NR, int MODE>
-__device__ void kinetic_pass(float2* st, int rows, const float4* __restrict__ kph,
-                             const float4* __restrict__ tw, float2* gout, const float2* D) {
+// Four-step FFT pass on all `rows` rows (each NR complex, stride NRP) held
+// in shared memory, in place: forward DFT, multiply by kph[k], inverse DFT.
+// With kph = (P_k - 1)/NR it produces (T - 1) x; with kph = P_k/NR it
+// applies T.  n = n1 + N1 n2, k = k2 + N2 k1.  Step A: per n1, an N2-point
+// DFT over n2 and the twiddle exp(-2 pi i n1 k2/NR); step B: per k2, an
+// N1-point DFT over n1.  The intermediate y[n1][k2] lives at n1 + N1 k2,
+// xor-swizzled within each block of N1 so that step B is conflict free.
+template <int NR>
+__device__ void kinetic_pass(float2* st, int rows, const float2* kph, const float2* tw) {
   using S = FFTShape<NR>;
   constexpr int N1 = S::N1, N2 = S::N2, NT = S::THREADS, NRP = NR + kPad;
   const int t = threadIdx.x;
-  // ---- step A: rows processed NT/N1 at a time
-  {
+  {  // step A
     constexpr int per = NT / N1;
     const int n1 = t % N1, rsub = t / N1;
     for (int r0 = 0; r0 < rows; r0 += per) {
@@ -170,21 +166,18 @@ __device__ void kinetic_pass(float2* st, int rows, const float4* __restrict__ kp
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) x[n2] = st[row * NRP + n1 + N1 * n2];
       }
-      __syncthreads();
+      __syncwarp();  // a row's N1 threads sit in one warp
       if (row < rows) {
         dft_reg<N2, false>(x);
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) {
-          const float4 w = __ldg(&tw[n1 * N2 + k2]);
-          const float2 y = cmul_c(x[k2], w.x, w.y, w.z, w.w);
-          st[row * NRP + (n1 ^ (k2 % N1)) + N1 * k2] = y;
-        }
+        for (int k2 = 0; k2 < N2; ++k2)
+          st[row * NRP + (n1 ^ (k2 % N1)) + N1 * k2] = cmul(x[k2], tw[k2 * N1 + n1]);
       }
-      __syncthreads();
+      __syncwarp();
     }
   }
-  // ---- step B (+ kinetic phase + inverse step B), in place per thread
-  {
+  __syncthreads();
+  {  // step B, the phase, inverse step B (in place per thread)
     constexpr int per = NT / N2;
     const int k2 = t % N2, rsub = t / N2;
     for (int r0 = 0; r0 < rows; r0 += per) {
@@ -195,19 +188,15 @@ __device__ void kinetic_pass(float2* st, int rows, const float4* __restrict__ kp
         for (int n1 = 0; n1 < N1; ++n1) x[n1] = st[row * NRP + (n1 ^ (k2 % N1)) + N1 * k2];
         dft_reg<N1, false>(x);  // x[k1] = X[k2 + N2 k1]
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          const float4 p = __ldg(&kph[k2 + N2 * k1]);
-          x[k1] = cmul_c(x[k1], p.x, p.y, p.z, p.w);
-        }
-        dft_reg<N1, true>(x);   // x[n1] = y'[n1][k2]
+        for (int k1 = 0; k1 < N1; ++k1) x[k1] = cmul(x[k1], kph[k2 + N2 * k1]);
+        dft_reg<N1, true>(x);
 #pragma unroll
         for (int n1 = 0; n1 < N1; ++n1) st[row * NRP + (n1 ^ (k2 % N1)) + N1 * k2] = x[n1];
       }
     }
   }
   __syncthreads();
-  // ---- inverse step A
-  {
+  {  // inverse step A
     constexpr int per = NT / N1;
     const int n1 = t % N1, rsub = t / N1;
     for (int r0 = 0; r0 < rows; r0 += per) {
@@ -216,36 +205,56 @@ __device__ void kinetic_pass(float2* st, int rows, const float4* __restrict__ kp
       if (row < rows) {
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
-          const float4 w = __ldg(&tw[n1 * N2 + k2]);
-          x[k2] = cmul_c(st[row * NRP + (n1 ^ (k2 % N1)) + N1 * k2], w.x, -w.y, w.z, -w.w);
+          const float2 w = tw[k2 * N1 + n1];
+          x[k2] = cmul(st[row * NRP + (n1 ^ (k2 % N1)) + N1 * k2], make_float2(w.x, -w.y));
         }
-        dft_reg<N2, true>(x);  // x[n2] = x'[n1 + N1 n2]
+        dft_reg<N2, true>(x);
       }
-      if constexpr (MODE == kDeltaOut) {
-        if (row < rows) {
+      __syncwarp();
+      if (row < rows) {
 #pragma unroll
-          for (int n2 = 0; n2 < N2; ++n2) {
-            const int p = n1 + N1 * n2;
-            const float2 d1 = D[row * NRP + p];
-            const float2 ph = gout[(long long)row * NR + p];
-            const float2 dd = make_float2(d1.x + x[n2].x, d1.y + x[n2].y);
-            gout[(long long)row * NR + p] = make_float2(ph.x + dd.x, ph.y + dd.y);
-          }
-        }
-      } else {
-        __syncthreads();
-        if (row < rows) {
-#pragma unroll
-          for (int n2 = 0; n2 < N2; ++n2) st[row * NRP + n1 + N1 * n2] = x[n2];
-        }
-        __syncthreads();
+        for (int n2 = 0; n2 < N2; ++n2) st[row * NRP + n1 + N1 * n2] = x[n2];
       }
+      __syncwarp();
     }
   }
+  __syncthreads();
 }
 
-__device__ __forceinline__ void load_state(float2* st, const float2* __restrict__ g, int rows, int NR,
-                                           int NRP) {
+// ---- TMA bulk copies (cp.async.bulk) completing on an mbarrier --------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// Wait for phase `parity` of the barrier, giving up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+constexpr long long kWaitPolls = 1LL << 24;  // far beyond any copy's duration
+
+__device__ __forceinline__ void load_state(float2* st, const float2* g, int rows, int NR, int NRP) {
   const float4* g4 = reinterpret_cast<const float4*>(g);
   const int per_row = NR / 2;
   const int total = rows * per_row;
@@ -255,79 +264,136 @@ __device__ __forceinline__ void load_state(float2* st, const float2* __restrict_
   }
 }
 
-struct Field3 {
-  float ez;      // E'_z
-  float2 ep;     // E+ = (E'_x - i E'_y)/2
-  float2 em;     // E- = conj(E+)
-};
-
-__device__ __forceinline__ float2 emult(const Field3& f, int kind) {
-  return kind == 0 ? make_float2(f.ez, 0.f) : (kind == 1 ? f.ep : f.em);
-}
-
-// one Taylor term: out[row] = (i theta / n) * (M in_{other surface})[c]
-__device__ __forceinline__ void taylor_term(const float2* __restrict__ in, float2* __restrict__ out,
-                                            int nrot, int G, int t, const int4* __restrict__ cp,
-                                            const Field3& f, float coef_n) {
-  for (int s = 0; s < 2; ++s) {
-    const int other = (1 - s) * nrot;
-    for (int c = 0; c < nrot; ++c) {
-      float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int e = 0; e < kMaxCoupl; ++e) {
-        const int4 q = __ldg(&cp[c * kMaxCoupl + e]);
-        if (q.x >= 0) {
-          const float2 v = in[(other + q.x) * G + t];
-          const float2 m = emult(f, q.y);
-          const float cf = __int_as_float(q.z);
-          const float2 mv = cmul(m, v);
-          acc.x = fmaf(cf, mv.x, acc.x);
-          acc.y = fmaf(cf, mv.y, acc.y);
-        }
-      }
-      // multiply by i * coef_n
-      out[(s * nrot + c) * G + t] = make_float2(-coef_n * acc.y, coef_n * acc.x);
-    }
-  }
-}
+__device__ __forceinline__ int j_of(int c) { return (int)sqrtf((float)c + 0.5f); }  // c = j^2+j+m
 
 }  // namespace
 
-// ----------------------------------------------------------------------------
-// the coupled molecular step
-// ----------------------------------------------------------------------------
-template <int NR>
-__global__ void __launch_bounds__(FFTShape<NR>::THREADS)
-    mol_step_kernel(SpeciesDev sp, MolDev md, Grid g, int prescribed, int G, int* err) {
-  constexpr int NRP = NR + kPad;
-  extern __shared__ float4 smem4[];
-  float2* st = reinterpret_cast<float2*>(smem4);
-  const int nrot = sp.nrot, rows = 2 * nrot;
-  float2* D = st + rows * NRP;             // d1 = chi - phi (running Taylor sum first)
-  float2* bufY = D + rows * NRP;           // Taylor terms, ping-pong, [rows][G]
-  float2* bufZ = bufY + rows * G;
-  __shared__ Field3 s_field;
-  __shared__ int s_nterms;
-  __shared__ double s_red[8][8];
+// Angular coupling tables, shared by every species (they depend only on the
+// channel (j, m), and a species with jmax < kMaxJ ignores entries whose
+// neighbour lies beyond its basis).  c_rot: rows of Ex' X + Ez' Z written in
+// the frame turned about z so that E'_y = 0 (kind 1: X entry, scaled by
+// E_perp; kind 0: Z entry, scaled by E'_z).  c_dip: rows of Z (kind 0),
+// S+ = sin(t)e^{ip} (kind 1) and S- (kind 2) for the dipole.
+__constant__ CouplEntry c_rot[kMaxRot * kMaxCoupl];
+__constant__ CouplEntry c_dip[kMaxRot * kMaxCoupl];
 
+cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip) {
+  cudaError_t e = cudaMemcpyToSymbol(c_rot, rot, sizeof(CouplEntry) * kMaxRot * kMaxCoupl);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(c_dip, dip, sizeof(CouplEntry) * kMaxRot * kMaxCoupl);
+}
+
+constexpr int kChunk = 32;            // widest R-space chunk (one radial point per lane)
+constexpr int kMaxRowsPerThread = 12;  // rows a thread owns in the R-space pass
+
+// ----------------------------------------------------------------------------
+// the coupled molecular step, s = T^{-1/2} psi stored:
+//   d2 = (T - 1) s           (kinetic pass, in shared memory)
+//   u  = s + d2 = T s        (per radial point)
+//   s' = Mask V^{1/2} K(E') V^{1/2} u, computed as s + (d2 + d1)
+// ----------------------------------------------------------------------------
+// e^{-i V dtau/2} from v = e^{-i V dtau} - 1: sqrt(1 + v) = 1 + v/2 - v^2/8 + O(v^3).
+// It only scales the small coupling correction, where an O(|V dtau|^3)
+// relative error is far below FP32 resolution of the state.
+__device__ __forceinline__ float2 vhalf_of(float2 v) {
+  const float2 v2 = cmul(v, v);
+  return make_float2(fmaf(0.5f, v.x, fmaf(-0.125f, v2.x, 1.f)), fmaf(0.5f, v.y, -0.125f * v2.y));
+}
+
+// compensated FP32 accumulation (TwoSum): hi + lo carries ~48 bits
+__device__ __forceinline__ void acc2(float& hi, float& lo, float x) {
+  const float t = hi + x;
+  const float z = t - hi;
+  lo += (hi - (t - z)) + (x - z);
+  hi = t;
+}
+
+template <int NR>
+__global__ void __launch_bounds__(FFTShape<NR>::THREADS, 2)
+    mol_step_kernel(SpeciesDev sp, MolDev md, Grid g, int prescribed, int CH, int* err) {
+  // CH radial points per chunk (32, 16 or 8): a warp covers 32/CH rows of CH points
+  constexpr int NT = FFTShape<NR>::THREADS, NRP = NR + kPad, NW = NT / 32;
+  extern __shared__ float4 smem4[];
+  const int nrot = sp.nrot, rows = 2 * nrot, J = sp.jmax;
+  float2* s_tw = reinterpret_cast<float2*>(smem4);      // [N2][N1] twiddles
+  float2* s_kd = s_tw + NR;                              // [NR] kinetic deltas
+  float2* st = s_kd + NR;                                // [rows][NRP] state, then d2
+  float2* bY = st + rows * NRP;                          // [rows][CH] Taylor terms / new state
+  float2* bZ = bY + rows * CH;                           // [rows][CH] Taylor terms
+  // per chunk, double buffered: old state [rows][CH], e^{-iV dtau} - 1
+  // [2(J+1)][CH] and absorber mask [CH]
+  const int cbuf = (rows + 2 * (J + 1) + 1) * CH;
+  float2* bC = bZ + rows * CH;
+  int2* s_prog = reinterpret_cast<int2*>(bC + 2 * cbuf);  // [nrot][6] (nbr*CH, coupling) this step
+  int2* s_rinfo = s_prog + nrot * kMaxCoupl;             // [rows] (table row, m + J)
+  __shared__ __align__(8) unsigned long long s_bar[3];   // [0] state, [1], [2] chunk buffers
+  __shared__ float2 s_ph[2 * kMaxJ + 1];                 // e^{+i m phi_E}
+  __shared__ float s_fld[2];                             // E_perp, E'_z (a.u.)
+  __shared__ int s_nterms;
+  __shared__ float2 s_red[NW][7];
+  __shared__ float s_fin[7], s_fin_lo[7];
+
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int LPR = 32 / CH;                       // row groups per warp
+  const int rl = lane & (CH - 1), rg = lane / CH;
+  const int row0 = w * LPR + rg, rstep = NW * LPR;
   const int lm = blockIdx.x;
   const int m = sp.mol[lm];
-  const int t = threadIdx.x;
-  float2* gpsi = sp.psi + (long long)lm * rows * NR;
+  float2* gs = sp.psi + (long long)lm * rows * NR;
 
-  load_state(st, gpsi, rows, NR, NRP);
+  // chunk copy: old state, potential deltas and mask of radial points [r0, r0 + CH)
+  // issued by the 32 lanes of the last warp (`ln` = lane), expect_tx first
+  auto issue_chunk = [&](int r0, int b, int ln) {
+    float2* bu = bC + b * cbuf;
+    float2* bv = bu + rows * CH;
+    float2* bm = bv + 2 * (J + 1) * CH;
+    if (ln == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&s_bar[1 + b], (unsigned)(cbuf * sizeof(float2)));
+    }
+    __syncwarp();
+    const int nv = 2 * (J + 1);
+    for (int q = ln; q < rows + nv + 1; q += 32) {
+      if (q < rows) bulk_g2s(bu + q * CH, gs + (long long)q * NR + r0, CH * sizeof(float2), &s_bar[1 + b]);
+      else if (q < rows + nv) bulk_g2s(bv + (q - rows) * CH, sp.vdelta + (q - rows) * NR + r0, CH * sizeof(float2), &s_bar[1 + b]);
+      else bulk_g2s(bm, sp.maskw + r0, CH * sizeof(float2), &s_bar[1 + b]);
+    }
+  };
+  const bool issuer = w == NW - 1;
+  if (t == 0) {
+    mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
+    mbar_init(&s_bar[2], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (issuer) {  // the whole state, one bulk copy per row; then the first chunk
+    if (lane == 0) mbar_expect_tx(&s_bar[0], (unsigned)(rows * NR * sizeof(float2)));
+    __syncwarp();
+    for (int row = lane; row < rows; row += 32)
+      bulk_g2s(st + row * NRP, gs + (long long)row * NR, NR * sizeof(float2), &s_bar[0]);
+    issue_chunk(0, 0, lane);
+  }
+  for (int q = t; q < NR; q += NT) {
+    s_tw[q] = __ldg(&sp.twiddle[q]);
+    s_kd[q] = __ldg(&sp.kdelta[q]);
+  }
+  for (int q = t; q < rows; q += NT) {
+    const int sf = q >= nrot, c = q - sf * nrot, j = j_of(c);
+    s_rinfo[q] = make_int2((sf * (J + 1) + j) * CH, c - j * j - j + J);
+  }
 
-  // ---- local field at the molecule, rotated into its frame (a.u.)
+  // ---- local field, rotated into the molecule frame (a.u.)
   if (t == 0) {
     float E[3];
     const long long n = *g.step;
     if (prescribed) {
       const long long nn = n < md.nwave ? n : md.nwave - 1;
       if (n >= md.nwave) atomicOr(err, kErrPrescribedRange);
-      const float w = md.wave[nn];
-      E[0] = md.amp[3 * (long long)m] * w;
-      E[1] = md.amp[3 * (long long)m + 1] * w;
-      E[2] = md.amp[3 * (long long)m + 2] * w;
+      const float wv = md.wave[nn];
+      E[0] = md.amp[3 * (long long)m] * wv;
+      E[1] = md.amp[3 * (long long)m + 1] * wv;
+      E[2] = md.amp[3 * (long long)m + 2] * wv;
     } else {
       const long long c = md.cell[m];
       E[0] = g.E[0][c];
@@ -339,157 +405,233 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS)
     float Ep[3];
 #pragma unroll
     for (int i = 0; i < 3; ++i) Ep[i] = (O[i] * E[0] + O[3 + i] * E[1] + O[6 + i] * E[2]) * inv_fau;
-    s_field.ez = Ep[2];
-    s_field.ep = make_float2(0.5f * Ep[0], -0.5f * Ep[1]);
-    s_field.em = make_float2(0.5f * Ep[0], 0.5f * Ep[1]);
-    // number of Taylor terms: (theta |E'|)^(n+1)/(n+1)! < 1e-13
-    const double x = sp.theta * sqrt((double)Ep[0] * Ep[0] + (double)Ep[1] * Ep[1] + (double)Ep[2] * Ep[2]);
+    const float eperp = sqrtf(Ep[0] * Ep[0] + Ep[1] * Ep[1]);
+    s_fld[0] = eperp;
+    s_fld[1] = Ep[2];
+    // e^{i phi_E} = (E'_x + i E'_y)/E_perp; e^{i m phi_E} by repeated products
+    const float2 e1 = eperp > 0.f ? make_float2(Ep[0] / eperp, Ep[1] / eperp) : make_float2(1.f, 0.f);
+    float2 pw = make_float2(1.f, 0.f);
+    s_ph[J] = pw;
+    for (int q = 1; q <= J; ++q) {
+      pw = cmul(pw, e1);
+      s_ph[J + q] = pw;
+      s_ph[J - q] = make_float2(pw.x, -pw.y);
+    }
+    // Taylor terms until (theta |E'|)^(n+1)/(n+1)! < 1e-10
+    const float x = (float)sp.theta * sqrtf(eperp * eperp + Ep[2] * Ep[2]);
     int nt = 0;
-    double term = 1.0;
-    if (x > 0.0) {
+    if (x > 0.f) {
       nt = 1;
-      term = x;
+      float term = x;
       while (nt < 24) {
-        const double next = term * x / (nt + 1);
-        if (next < 1e-13) break;
+        const float next = term * x / (float)(nt + 1);
+        if (next < 1e-10f) break;
         term = next;
         ++nt;
       }
-      if (nt >= 24 || x > 4.0) atomicOr(err, kErrCouplingSeries);
+      if (nt >= 24 || x > 4.f) atomicOr(err, kErrCouplingSeries);
     }
     s_nterms = nt;
   }
   __syncthreads();
-  const Field3 f = s_field;
+  {  // this step's coupling rows: slots 0-1 Z (times E'_z), 2-5 X (times E_perp)
+    const float eperp = s_fld[0], ez = s_fld[1];
+    for (int q = t; q < nrot * kMaxCoupl; q += NT) {
+      const CouplEntry e = c_rot[q];
+      const bool ok = (unsigned)e.nbr < (unsigned)nrot;
+      const float cf = ok ? e.coef * ((q % kMaxCoupl) >= 2 ? eperp : ez) : 0.f;
+      s_prog[q] = make_int2(ok ? e.nbr * CH : 0, __float_as_int(cf));
+    }
+  }
+  {
+    const bool ok = mbar_wait(&s_bar[0], 0, kWaitPolls);
+    if (!__syncthreads_and(ok)) {  // uniform decision; copies still in flight get a second bounded wait
+      if (t == 0) atomicOr(err, kErrTimeout);
+      if (!ok) mbar_wait(&s_bar[0], 0, kWaitPolls);
+      return;
+    }
+  }
+
+  // ---- kinetic pass: st <- d2 = (T - 1) s
+  kinetic_pass<NR>(st, rows, s_kd, s_tw);
+
+  // ---- R-space pass, CH radial points at a time; thread rows row0 + i*rstep
   const int nterms = s_nterms;
   const float theta = (float)sp.theta;
-  const int4* __restrict__ cp = sp.coupl;
-
-  // ---- R-space pass, G radial points at a time (thread t <-> r = r0 + t)
-  double pg = 0.0, pe = 0.0, ag = 0.0, ae = 0.0, dxs = 0.0, dys = 0.0, dzs = 0.0;
-  for (int r0 = 0; r0 < NR; r0 += G) {
-    const int r = r0 + t;
-    if (t < G) {
-      // xi = V^{1/2} phi into Z; the Taylor sum S accumulates in D's column
-      for (int row = 0; row < rows; ++row) {
-        const int s = row / nrot, c = row - s * nrot;
-        const int j = (int)sqrtf((float)c + 0.5f);  // c = j^2 + j + m
-        const float2 vh = __ldg(&sp.vhalf[(s * (sp.jmax + 1) + j) * NR + r]);
-        bufZ[row * G + t] = cmul(vh, st[row * NRP + r]);
-        D[row * NRP + r] = make_float2(0.f, 0.f);
+  float a_hi[7] = {0, 0, 0, 0, 0, 0, 0}, a_lo[7] = {0, 0, 0, 0, 0, 0, 0};
+  const int nchunks = NR / CH;
+  for (int ck = 0; ck < nchunks; ++ck) {
+    const int r0 = ck * CH, r = r0 + rl, b = ck & 1;
+    float2* bU = bC + b * cbuf;
+    const float2* bV = bU + rows * CH;
+    const float2* bM = bV + 2 * (J + 1) * CH;
+    // prefetch the next chunk into the other buffer (free since the last barrier)
+    if (issuer && ck + 1 < nchunks) issue_chunk(r0 + CH, b ^ 1, lane);
+    {
+      const bool ok = mbar_wait(&s_bar[1 + b], (ck >> 1) & 1, kWaitPolls);
+      if (!__syncthreads_and(ok)) {
+        if (t == 0) atomicOr(err, kErrTimeout);
+        if (!ok) mbar_wait(&s_bar[1 + b], (ck >> 1) & 1, kWaitPolls);
+        if (issuer && ck + 1 < nchunks) mbar_wait(&s_bar[2 - b], ((ck + 1) >> 1) & 1, kWaitPolls);
+        return;
       }
-      float2* in = bufZ;
-      float2* out = bufY;
-      for (int n = 1; n <= nterms; ++n) {
-        taylor_term(in, out, nrot, G, t, cp, f, theta / (float)n);
-        for (int row = 0; row < rows; ++row) {
-          const float2 a = D[row * NRP + r], b = out[row * G + t];
-          D[row * NRP + r] = make_float2(a.x + b.x, a.y + b.y);
-        }
-        float2* tmp = in;
-        in = out;
-        out = tmp;
-      }
-      // d1 = (V - 1) phi + V^{1/2} S ; chi = phi + d1 ; mask ; observables
-      const float mk = __ldg(&sp.maskw[r]).x;
-      float sg = 0.f, se = 0.f;
-      double wg = 0.0, we = 0.0;
-      for (int row = 0; row < rows; ++row) {
-        const int s = row / nrot, c = row - s * nrot;
-        const int j = (int)sqrtf((float)c + 0.5f);
-        const int ti = (s * (sp.jmax + 1) + j) * NR + r;
-        const float2 vh = __ldg(&sp.vhalf[ti]);
-        const float4 vd = __ldg(&sp.vdelta[ti]);
-        const float2 phi = st[row * NRP + r];
-        float2 d1 = cmul_c_add(phi, vd, cmul(vh, D[row * NRP + r]));
-        if (mk < 1.f) {
-          // mask the new value: d1 <- m (phi + d1) - phi; tally the norm removed
-          const double px = (double)phi.x + d1.x, py = (double)phi.y + d1.y;
-          d1.x = fmaf(mk - 1.f, phi.x, mk * d1.x);
-          d1.y = fmaf(mk - 1.f, phi.y, mk * d1.y);
-          const double qx = (double)phi.x + d1.x, qy = (double)phi.y + d1.y;
-          const double d2 = (px * px + py * py) - (qx * qx + qy * qy);
-          if (s == 0) wg += d2; else we += d2;
-        }
-        const float2 chi = make_float2(phi.x + d1.x, phi.y + d1.y);
-        const float b2 = chi.x * chi.x + chi.y * chi.y;
-        if (s == 0) sg += b2; else se += b2;
-        st[row * NRP + r] = chi;
-        D[row * NRP + r] = d1;
-      }
-      // dipole in the molecule frame: sum_c conj(chi_g[c]) (A chi_e)[c]
-      float2 accP = make_float2(0.f, 0.f), accM = accP, accZ = accP;
-      for (int c = 0; c < nrot; ++c) {
-        const float2 gc = st[c * NRP + r];
-#pragma unroll
-        for (int e = 0; e < kMaxCoupl; ++e) {
-          const int4 q = __ldg(&cp[c * kMaxCoupl + e]);
-          if (q.x >= 0) {
-            const float2 ev = st[(nrot + q.x) * NRP + r];
-            const float cf = __int_as_float(q.z);
-            // conj(gc) * ev
-            const float re = fmaf(gc.x, ev.x, gc.y * ev.y), im = fmaf(gc.x, ev.y, -gc.y * ev.x);
-            float2* acc = q.y == 0 ? &accZ : (q.y == 1 ? &accP : &accM);
-            acc->x = fmaf(cf, re, acc->x);
-            acc->y = fmaf(cf, im, acc->y);
-          }
-        }
-      }
-      pg += sg;
-      pe += se;
-      ag += wg;
-      ae += we;
-      dxs += (double)(accP.x + accM.x);
-      dys += (double)(accP.y - accM.y);
-      dzs += 2.0 * (double)accZ.x;
     }
-  }
-  // ---- block reduction (FP64)
-  {
-    double v[7] = {pg, pe, ag, ae, dxs, dys, dzs};
-    const int lane = t & 31, wid = t >> 5;
+    // eta = D^dagger V^{1/2} u (rotated frame) into bZ
+    float2 sacc[kMaxRowsPerThread];
 #pragma unroll
-    for (int q = 0; q < 7; ++q) v[q] = warp_sum(v[q]);
-    if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < 7; ++q) s_red[wid][q] = v[q];
+    for (int i = 0; i < kMaxRowsPerThread; ++i) {
+      sacc[i] = make_float2(0.f, 0.f);
+      const int row = row0 + i * rstep;
+      if (row < rows) {
+        const int2 ri = s_rinfo[row];
+        const float2 u = st[row * NRP + r] + bU[row * CH + rl];
+        bZ[row * CH + rl] = cmul(s_ph[ri.y], cmul(vhalf_of(bV[ri.x + rl]), u));
+      }
     }
     __syncthreads();
-    if (t == 0) {
-      double a[7] = {0, 0, 0, 0, 0, 0, 0};
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
-        for (int q = 0; q < 7; ++q) a[q] += s_red[w][q];
-      const double dR = sp.dR;
-      const double P0 = a[0] * dR, P1 = a[1] * dR;
-      md.pop[2 * (long long)m] = P0;
-      md.pop[2 * (long long)m + 1] = P1;
-      md.absorbed[2 * (long long)m] += a[2] * dR;
-      md.absorbed[2 * (long long)m + 1] += a[3] * dR;
-      if (!isfinite(P0) || !isfinite(P1)) atomicOr(err, kErrNonFinite);
-      // mu' = d dR (Re(S+ + S-), Im(S+ - S-), 2 Re Z), lab mu = O mu'
-      const double scale = sp.dipole * dR;
-      const double mup[3] = {a[4] * scale, a[5] * scale, a[6] * scale};
-      const float* O = md.rot + 9 * (long long)m;
-      double* mu = md.mu + 3 * (long long)m;
-      double* dmu = md.dmu + 3 * (long long)m;
+    float2* in = bZ;
+    float2* out = bY;
+    for (int n = 1; n <= nterms; ++n) {
+      const float cn = theta / (float)n;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
-        const double lab = (double)O[3 * i] * mup[0] + (double)O[3 * i + 1] * mup[1] +
-                           (double)O[3 * i + 2] * mup[2];
-        dmu[i] = lab - mu[i];
-        mu[i] = lab;
+      for (int i = 0; i < kMaxRowsPerThread; ++i) {
+        const int row = row0 + i * rstep;
+        if (row < rows) {
+          const int sf = row >= nrot, c = row - sf * nrot;
+          const float2* src = in + (1 - sf) * nrot * CH + rl;
+          const int2* pr = s_prog + c * kMaxCoupl;
+          float ax = 0.f, ay = 0.f;
+#pragma unroll
+          for (int e = 0; e < kMaxCoupl; ++e) {  // unused slots carry a zero coefficient
+            const int2 q = pr[e];
+            const float cf = __int_as_float(q.y);
+            const float2 v = src[q.x];
+            ax = fmaf(cf, v.x, ax);
+            ay = fmaf(cf, v.y, ay);
+          }
+          const float2 o = make_float2(-cn * ay, cn * ax);  // i (theta/n) (M_r in)
+          out[row * CH + rl] = o;
+          sacc[i].x += o.x;
+          sacc[i].y += o.y;
+        }
+      }
+      __syncthreads();
+      float2* tmp = in;
+      in = out;
+      out = tmp;
+    }
+    // d1 = (V - 1) u + V^{1/2} D S_r ; mask ; s' = s + (d2 + d1)
+    const float mk = bM[rl].x;
+    float sg = 0.f, se = 0.f, agf = 0.f, aef = 0.f;
+#pragma unroll
+    for (int i = 0; i < kMaxRowsPerThread; ++i) {
+      const int row = row0 + i * rstep;
+      if (row < rows) {
+        const int2 ri = s_rinfo[row];
+        const int sf = row >= nrot;
+        const float2 sv = bU[row * CH + rl];
+        const float2 d2 = st[row * NRP + r];
+        const float2 u = sv + d2;
+        const float2 ph = s_ph[ri.y];
+        const float2 vd = bV[ri.x + rl];
+        const float2 corr = cmul(vhalf_of(vd), cmul(make_float2(ph.x, -ph.y), sacc[i]));
+        float2 d1 = make_float2(fmaf(u.x, vd.x, fmaf(-u.y, vd.y, corr.x)), fmaf(u.x, vd.y, fmaf(u.y, vd.x, corr.y)));
+        if (mk < 1.f) {
+          const float px = u.x + d1.x, py = u.y + d1.y;
+          d1.x = fmaf(mk - 1.f, u.x, mk * d1.x);
+          d1.y = fmaf(mk - 1.f, u.y, mk * d1.y);
+          const float qx = u.x + d1.x, qy = u.y + d1.y;
+          const float dd = fmaf(px, px, py * py) - fmaf(qx, qx, qy * qy);
+          if (sf == 0) agf += dd; else aef += dd;
+        }
+        const float2 sn = sv + (d2 + d1);
+        gs[(long long)row * NR + r] = sn;
+        bY[row * CH + rl] = sn;
+        const float b2 = fmaf(sn.x, sn.x, sn.y * sn.y);
+        if (sf == 0) sg += b2; else se += b2;
       }
     }
+    acc2(a_hi[0], a_lo[0], sg);
+    acc2(a_hi[1], a_lo[1], se);
+    acc2(a_hi[2], a_lo[2], agf);
+    acc2(a_hi[3], a_lo[3], aef);
+    __syncthreads();
+    // dipole in the molecule frame: sum_c conj(g_c) (A e)_c for A = Z, S+, S-
+    {
+      float2 accP = make_float2(0.f, 0.f), accM = accP, accZ = accP;
+      for (int c = row0; c < nrot; c += rstep) {
+        const float2 gc = bY[c * CH + rl];
+        const float2* ee = bY + nrot * CH + rl;
+        float2 w3[3];
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {  // slots 0-1 Z, 2-3 S+, 4-5 S-
+          const CouplEntry q0 = c_dip[c * kMaxCoupl + 2 * kk], q1 = c_dip[c * kMaxCoupl + 2 * kk + 1];
+          const bool ok0 = (unsigned)q0.nbr < (unsigned)nrot, ok1 = (unsigned)q1.nbr < (unsigned)nrot;
+          const float c0 = ok0 ? q0.coef : 0.f, c1 = ok1 ? q1.coef : 0.f;
+          const float2 e0 = ee[ok0 ? q0.nbr * CH : 0], e1 = ee[ok1 ? q1.nbr * CH : 0];
+          w3[kk] = make_float2(fmaf(c0, e0.x, c1 * e1.x), fmaf(c0, e0.y, c1 * e1.y));
+        }
+        // conj(gc) * w
+        accZ.x += fmaf(gc.x, w3[0].x, gc.y * w3[0].y);
+        accZ.y += fmaf(gc.x, w3[0].y, -gc.y * w3[0].x);
+        accP.x += fmaf(gc.x, w3[1].x, gc.y * w3[1].y);
+        accP.y += fmaf(gc.x, w3[1].y, -gc.y * w3[1].x);
+        accM.x += fmaf(gc.x, w3[2].x, gc.y * w3[2].y);
+        accM.y += fmaf(gc.x, w3[2].y, -gc.y * w3[2].x);
+      }
+      acc2(a_hi[4], a_lo[4], accP.x + accM.x);
+      acc2(a_hi[5], a_lo[5], accP.y - accM.y);
+      acc2(a_hi[6], a_lo[6], 2.f * accZ.x);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  // ---- kinetic pass: phi' = phi + d1 + (T - 1) chi, written to global memory
-  kinetic_pass<NR, kDeltaOut>(st, rows, sp.kdelta, sp.twiddle, gpsi, D);
+  // ---- block reduction (compensated FP32; FP64 only for the final sums)
+  {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+      float hi = a_hi[q], lo = a_lo[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+        acc2(hi, lo, h2);
+        lo += l2;
+      }
+      if (lane == 0) s_red[w][q] = make_float2(hi, lo);
+    }
+    __syncthreads();
+    if (t < 7) {  // one quantity per thread, compensated over the warps
+      float hi = 0.f, lo = 0.f;
+      for (int ww = 0; ww < NW; ++ww) {
+        acc2(hi, lo, s_red[ww][t].x);
+        lo += s_red[ww][t].y;
+      }
+      s_fin[t] = hi + lo;  // FP32 sum; its rounding is 6e-8 relative
+      s_fin_lo[t] = lo - (s_fin[t] - hi);
+    }
+    __syncthreads();
+    if (t < 3) {  // lab dipole component t: mu = O mu', mu' = d dR (Re(S+ + S-), Im(S+ - S-), 2 Re Z)
+      const float* O = md.rot + 9 * (long long)m;
+      const float sc = (float)sp.dipole * sp.dR;
+      const float lab = sc * (O[3 * t] * s_fin[4] + O[3 * t + 1] * s_fin[5] + O[3 * t + 2] * s_fin[6]);
+      double* mu = md.mu + 3 * (long long)m + t;
+      const double nl = (double)lab;
+      md.dmu[3 * (long long)m + t] = nl - *mu;
+      *mu = nl;
+    } else if (t < 5) {  // populations P_g, P_e
+      const double P = ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
+      md.pop[2 * (long long)m + (t - 3)] = P;
+      if (!isfinite(P)) atomicOr(err, kErrNonFinite);
+    } else if (t < 7) {  // absorbed norm of this step
+      md.absorbed[2 * (long long)m + (t - 5)] += ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
+    }
+  }
 }
 
 }  // namespace ms
 
 // ----------------------------------------------------------------------------
-// Eq. 8 readout: psi = T^{-1/2} phi on the excited surface, then
+// Eq. 8 readout: psi = T^{1/2} s on the excited surface, then
 // <chi_e|R|chi_e> and <chi_e|chi_e> per molecule (FP64 reduction)
 // ----------------------------------------------------------------------------
 namespace ms {
@@ -499,15 +641,21 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS)
     mol_observe_kernel(SpeciesDev sp, MolDev md) {
   constexpr int NRP = NR + kPad;
   extern __shared__ float4 smem4[];
-  float2* st = reinterpret_cast<float2*>(smem4);
+  float2* s_tw = reinterpret_cast<float2*>(smem4);
+  float2* s_kh = s_tw + NR;
+  float2* st = s_kh + NR;
   __shared__ double s_red[8][2];
   const int nrot = sp.nrot;
   const int lm = blockIdx.x;
   const int m = sp.mol[lm];
+  for (int q = threadIdx.x; q < NR; q += blockDim.x) {
+    s_tw[q] = __ldg(&sp.twiddle[q]);
+    s_kh[q] = __ldg(&sp.khalf[q]);
+  }
   const float2* ge = sp.psi + ((long long)lm * 2 + 1) * nrot * NR;  // excited rows
   load_state(st, ge, nrot, NR, NRP);
   __syncthreads();
-  kinetic_pass<NR, kInPlace>(st, nrot, sp.kphase_inv, sp.twiddle, nullptr, nullptr);
+  kinetic_pass<NR>(st, nrot, s_kh, s_tw);
   double num = 0.0, den = 0.0;
   for (int r = threadIdx.x; r < NR; r += blockDim.x) {
     float a = 0.f;
@@ -528,9 +676,9 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS)
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0.0, b = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      a += s_red[w][0];
-      b += s_red[w][1];
+    for (int ww = 0; ww < (int)(blockDim.x >> 5); ++ww) {
+      a += s_red[ww][0];
+      b += s_red[ww][1];
     }
     md.Rnum[m] = a * sp.dR;
     md.Rden[m] = b * sp.dR;
@@ -559,15 +707,32 @@ size_t mol_state_smem(int nr, int rows) { return (size_t)rows * (nr + kPad) * si
 
 static int threads_for(int nr) { return nr == 256 ? 256 : 128; }
 
-// radial points per R-space chunk so that state + d1 + 2 Taylor buffers fit
-static int chunk_for(int nr, int nrot, size_t* smem) {
-  const size_t cap = 227 * 1024;
+static size_t step_smem(int nr, int nrot, int ch) {
   const int rows = 2 * nrot;
-  const size_t base = 2 * mol_state_smem(nr, rows);
-  int G = nr < threads_for(nr) ? nr : threads_for(nr);
-  while (G > 8 && base + 2 * (size_t)rows * G * sizeof(float2) > cap) G >>= 1;
-  *smem = base + 2 * (size_t)rows * G * sizeof(float2);
-  return G;
+  const int jm = (int)std::lround(std::sqrt((double)nrot)) - 1;
+  return 2 * (size_t)nr * sizeof(float2) + mol_state_smem(nr, rows) + 2 * (size_t)rows * ch * sizeof(float2) +
+         2 * (size_t)(rows + 2 * (jm + 1) + 1) * ch * sizeof(float2) +
+         (size_t)nrot * kMaxCoupl * sizeof(int2) + (size_t)rows * sizeof(int2);
+}
+
+// rows each thread owns at chunk width ch (8 warps; 32/ch row groups per warp)
+static int rows_per_thread(int nrot, int ch) {
+  const int rstep = 8 * (32 / ch);
+  return (2 * nrot + rstep - 1) / rstep;
+}
+
+// widest chunk that keeps two CTAs per SM, else the widest that fits one
+static int chunk_for(int nr, int nrot, size_t* smem) {
+  // two CTAs per SM: 2 x (dynamic + static (< 800 B) + 1 KB reserved) <= 228 KB
+  const size_t cap1 = 227 * 1024, cap2 = 228 * 1024 / 2 - 1024 - 800;
+  for (size_t cap : {cap2, cap1})
+    for (int ch = kChunk; ch >= 8; ch >>= 1)
+      if (rows_per_thread(nrot, ch) <= kMaxRowsPerThread && step_smem(nr, nrot, ch) <= cap) {
+        *smem = step_smem(nr, nrot, ch);
+        return ch;
+      }
+  *smem = (size_t)-1;  // does not fit: rejected at create
+  return 8;
 }
 
 size_t mol_step_smem(int nr, int nrot) {
@@ -580,9 +745,9 @@ template <int NR>
 static void launch_step_t(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed,
                           int* err, cudaStream_t s) {
   size_t smem;
-  const int G = chunk_for(NR, sp.nrot, &smem);
+  const int ch = chunk_for(NR, sp.nrot, &smem);
   cudaFuncSetAttribute(mol_step_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  mol_step_kernel<NR><<<sp.nmol, FFTShape<NR>::THREADS, smem, s>>>(sp, md, g, prescribed, G, err);
+  mol_step_kernel<NR><<<sp.nmol, FFTShape<NR>::THREADS, smem, s>>>(sp, md, g, prescribed, ch, err);
 }
 
 void launch_mol_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
@@ -597,7 +762,7 @@ void launch_mol_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int 
 
 template <int NR>
 static void launch_observe_t(const SpeciesDev& sp, const MolDev& md, cudaStream_t s) {
-  const size_t smem = mol_state_smem(NR, sp.nrot);
+  const size_t smem = 2 * (size_t)NR * sizeof(float2) + mol_state_smem(NR, sp.nrot);
   cudaFuncSetAttribute(mol_observe_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   mol_observe_kernel<NR><<<sp.nmol, FFTShape<NR>::THREADS, smem, s>>>(sp, md);
 }

@@ -38,6 +38,8 @@ cplx expm1i(double a) {
   return cplx(-2.0 * sh * sh, std::sin(a));
 }
 
+float2 f2(cplx z) { return make_float2((float)z.real(), (float)z.imag()); }
+
 float4 hilo(cplx z) {
   const float ch = (float)z.real(), sh = (float)z.imag();
   return make_float4(ch, sh, (float)(z.real() - (double)ch), (float)(z.imag() - (double)sh));
@@ -194,6 +196,50 @@ bool fgh_ground_state(int n, double dR, double mass, const std::vector<double>& 
 
 int channel(int j, int m) { return j * j + j + m; }
 
+// Angular matrix elements between complex spherical harmonics (Condon-
+// Shortley): cos(t) couples (j,m)-(j+1,m) with a(j,m); sin(t)e^{ip} takes
+// (j,m) to (j+1,m+1) with b(j,m) and to (j-1,m+1) with c(j,m).
+double ang_a(int j, int m) { return std::sqrt(((j + 1.0) * (j + 1) - m * m) / ((2.0 * j + 1) * (2.0 * j + 3))); }
+double ang_b(int j, int m) { return -std::sqrt((j + m + 1.0) * (j + m + 2) / ((2.0 * j + 1) * (2.0 * j + 3))); }
+double ang_c(int j, int m) { return std::sqrt((j - m) * (j - m - 1.0) / ((2.0 * j - 1) * (2.0 * j + 1))); }
+
+// Rows of E_perp X + E_z Z (the coupling in the frame where E'_y = 0) and of
+// Z, S+, S- (for the dipole), for every channel up to kMaxJ.
+ms_status upload_angular_tables() {
+  const int J = ms::kMaxJ;
+  auto valid = [J](int j, int m) { return j >= 0 && j <= J && m >= -j && m <= j; };
+  std::vector<ms::CouplEntry> rot(ms::kMaxRot * ms::kMaxCoupl, ms::CouplEntry{-1, 0.f, 0, 0});
+  std::vector<ms::CouplEntry> dip = rot;
+  // fixed slots: rot 0-1 Z, 2-5 X; dip 0-1 Z, 2-3 S+, 4-5 S- (unused: nbr -1)
+  for (int j = 0; j <= J; ++j)
+    for (int m = -j; m <= j; ++m) {
+      const size_t base = (size_t)channel(j, m) * ms::kMaxCoupl;
+      auto put = [&](std::vector<ms::CouplEntry>& t, int slot, int jn, int mn, double coef) {
+        if (!valid(jn, mn) || coef == 0.0) return;
+        t[base + slot] = ms::CouplEntry{channel(jn, mn), (float)coef, slot, 0};
+      };
+      const double z0 = valid(j - 1, m) ? ang_a(j - 1, m) : 0.0, z1 = ang_a(j, m);
+      // S+ row: from (j-1, m-1) and (j+1, m-1); S- row: from (j+1, m+1) and (j-1, m+1)
+      const double p0 = valid(j - 1, m - 1) ? ang_b(j - 1, m - 1) : 0.0;
+      const double p1 = valid(j + 1, m - 1) ? ang_c(j + 1, m - 1) : 0.0;
+      const double q0 = ang_b(j, m);
+      const double q1 = j >= 1 ? ang_c(j, m) : 0.0;
+      put(rot, 0, j - 1, m, z0);
+      put(rot, 1, j + 1, m, z1);
+      put(rot, 2, j - 1, m - 1, 0.5 * p0);  // X = (S+ + S-)/2, four distinct channels
+      put(rot, 3, j + 1, m - 1, 0.5 * p1);
+      put(rot, 4, j + 1, m + 1, 0.5 * q0);
+      put(rot, 5, j - 1, m + 1, 0.5 * q1);
+      put(dip, 0, j - 1, m, z0);
+      put(dip, 1, j + 1, m, z1);
+      put(dip, 2, j - 1, m - 1, p0);
+      put(dip, 3, j + 1, m - 1, p1);
+      put(dip, 4, j + 1, m + 1, q0);
+      put(dip, 5, j - 1, m + 1, q1);
+    }
+  return ms::upload_coupling_tables(rot.data(), dip.data()) == cudaSuccess ? MS_OK : MS_ECUDA;
+}
+
 ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const std::vector<int>& ids) {
   ms::SpeciesDev& sp = s->sp[si];
   const int nr = d.nr, J = d.jmax, nrot = (J + 1) * (J + 1);
@@ -215,28 +261,28 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
     Ue[i] = d.exc_A + d.exc_B * std::exp(-d.exc_beta * (r[i] - d.exc_rc));
   }
   // potential phases per (surface, j, r)
-  std::vector<float4> vdelta((size_t)2 * (J + 1) * nr);
+  std::vector<float2> vdelta((size_t)2 * (J + 1) * nr);
   std::vector<float2> vhalf((size_t)2 * (J + 1) * nr);
   for (int sf = 0; sf < 2; ++sf)
     for (int j = 0; j <= J; ++j)
       for (int i = 0; i < nr; ++i) {
         const double V = (sf == 0 ? Ug[i] : Ue[i]) + j * (j + 1) / (2.0 * mu * r[i] * r[i]);
         const size_t q = ((size_t)sf * (J + 1) + j) * nr + i;
-        vdelta[q] = hilo(expm1i(-V * dtau));
+        vdelta[q] = f2(expm1i(-V * dtau));
         const cplx h = std::polar(1.0, -0.5 * V * dtau);
         vhalf[q] = make_float2((float)h.real(), (float)h.imag());
       }
   // kinetic phases (natural DFT order) and four-step twiddles
-  std::vector<float4> kph(nr), kphi(nr), tw(nr);
+  std::vector<float2> kph(nr), kphi(nr), tw(nr);
   for (int k = 0; k < nr; ++k) {
     const int p = k < nr / 2 ? k : k - nr;
     const double kk = 2.0 * kPi * p / (nr * dR);
-    kph[k] = hilo(expm1i(-kk * kk * dtau / (2.0 * mu)) / (double)nr);
-    kphi[k] = hilo(std::polar(1.0 / nr, +kk * kk * dtau / (4.0 * mu)));
+    kph[k] = f2(expm1i(-kk * kk * dtau / (2.0 * mu)) / (double)nr);
+    kphi[k] = f2(std::polar(1.0 / nr, -kk * kk * dtau / (4.0 * mu)));
   }
   const int N1 = nr == 64 ? 8 : 16, N2 = nr / N1;
   for (int n1 = 0; n1 < N1; ++n1)
-    for (int k2 = 0; k2 < N2; ++k2) tw[n1 * N2 + k2] = hilo(std::polar(1.0, -2.0 * kPi * n1 * k2 / nr));
+    for (int k2 = 0; k2 < N2; ++k2) tw[k2 * N1 + n1] = f2(std::polar(1.0, -2.0 * kPi * n1 * k2 / nr));
   // absorber
   std::vector<float2> mw(nr);
   std::vector<float> rf(nr);
@@ -249,31 +295,7 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
     mw[i] = make_float2((float)m, (float)(1.0 - m * m));
     rf[i] = (float)r[i];
   }
-  // coupling rows of R^hat = x X + y Y + z Z written with S+ = sin(t)e^{ip}:
-  // M = E+ S+ + E- S- + Ez Z, E+- = (E'x -+ i E'y)/2
-  auto a_c = [](int j, int m) { return std::sqrt(((j + 1.0) * (j + 1) - m * m) / ((2.0 * j + 1) * (2.0 * j + 3))); };
-  auto b_c = [](int j, int m) { return -std::sqrt((j + m + 1.0) * (j + m + 2) / ((2.0 * j + 1) * (2.0 * j + 3))); };
-  auto c_c = [](int j, int m) { return std::sqrt((j - m) * (j - m - 1.0) / ((2.0 * j - 1) * (2.0 * j + 1))); };
-  auto valid = [J](int j, int m) { return j >= 0 && j <= J && m >= -j && m <= j; };
-  std::vector<int4> cp((size_t)nrot * ms::kMaxCoupl, make_int4(-1, 0, 0, 0));
-  for (int j = 0; j <= J; ++j)
-    for (int m = -j; m <= j; ++m) {
-      int e = 0;
-      auto add = [&](int jn, int mn, int kind, double coef) {
-        if (!valid(jn, mn) || coef == 0.0) return;
-        float cf = (float)coef;
-        int bits;
-        std::memcpy(&bits, &cf, 4);
-        cp[(size_t)channel(j, m) * ms::kMaxCoupl + e++] = make_int4(channel(jn, mn), kind, bits, 0);
-      };
-      add(j - 1, m, 0, valid(j - 1, m) ? a_c(j - 1, m) : 0.0);  // Z
-      add(j + 1, m, 0, a_c(j, m));
-      add(j - 1, m - 1, 1, valid(j - 1, m - 1) ? b_c(j - 1, m - 1) : 0.0);  // S+ row
-      add(j + 1, m - 1, 1, valid(j + 1, m - 1) ? c_c(j + 1, m - 1) : 0.0);
-      add(j + 1, m + 1, 2, b_c(j, m));  // S- row
-      add(j - 1, m + 1, 2, j >= 1 ? c_c(j, m) : 0.0);
-    }
-  // initial state: v=0, j=0 Fourier-grid ground state, phi0 = T^{1/2} psi0
+  // initial state: v=0, j=0 Fourier-grid ground state, stored as s0 = T^{-1/2} psi0
   std::vector<double> psi0;
   if (!fgh_ground_state(nr, dR, mu, Ug, psi0)) return MS_EINVAL;
   std::vector<cplx> spec(nr), phi0(nr);
@@ -281,7 +303,7 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
     const double k = 2.0 * kPi * p / (nr * dR);
     cplx acc = 0.0;
     for (int b = 0; b < nr; ++b) acc += psi0[b] * std::polar(1.0, -k * b * dR);
-    spec[p + nr / 2] = acc * std::polar(1.0, -k * k * dtau / (4.0 * mu));
+    spec[p + nr / 2] = acc * std::polar(1.0, +k * k * dtau / (4.0 * mu));
   }
   for (int a = 0; a < nr; ++a) {
     cplx acc = 0.0;
@@ -299,14 +321,13 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   MS_TRY(upload(s, &d_row0, row0.data(), row0.size()));
   if (ms::launch_broadcast_row(sp.psi, d_row0, nr, per, (long long)ids.size(), s->stream) != cudaSuccess)
     return MS_ECUDA;
-  MS_TRY(upload(s, (float4**)&sp.vdelta, vdelta.data(), vdelta.size()));
+  MS_TRY(upload(s, (float2**)&sp.vdelta, vdelta.data(), vdelta.size()));
   MS_TRY(upload(s, (float2**)&sp.vhalf, vhalf.data(), vhalf.size()));
-  MS_TRY(upload(s, (float4**)&sp.kdelta, kph.data(), kph.size()));
-  MS_TRY(upload(s, (float4**)&sp.kphase_inv, kphi.data(), kphi.size()));
-  MS_TRY(upload(s, (float4**)&sp.twiddle, tw.data(), tw.size()));
+  MS_TRY(upload(s, (float2**)&sp.kdelta, kph.data(), kph.size()));
+  MS_TRY(upload(s, (float2**)&sp.khalf, kphi.data(), kphi.size()));
+  MS_TRY(upload(s, (float2**)&sp.twiddle, tw.data(), tw.size()));
   MS_TRY(upload(s, (float2**)&sp.maskw, mw.data(), mw.size()));
   MS_TRY(upload(s, (float**)&sp.r, rf.data(), rf.size()));
-  MS_TRY(upload(s, (int4**)&sp.coupl, cp.data(), cp.size()));
   MS_TRY(upload(s, (int**)&sp.mol, ids.data(), ids.size()));
   // populations at t = 0
   double n0 = 0.0;
@@ -345,6 +366,7 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
   MS_TRY(zeros(s, &g.step, 1));
   s->d_step = g.step;
   MS_TRY(zeros(s, &s->d_err, 1));
+  MS_TRY(upload_angular_tables());
   // materials
   ms::MaterialCoef* mc = g.mc;
   for (int i = 0; i < M->n_materials; ++i) {
@@ -624,6 +646,7 @@ static ms_status latched(ms_sim* s) {
     return MS_ECUDA;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
   if (e & ms::kErrPrescribedRange) return MS_EINVAL;
+  if (e & ms::kErrTimeout) return MS_ETIMEOUT;
   return e ? MS_ENUMERIC : MS_OK;
 }
 

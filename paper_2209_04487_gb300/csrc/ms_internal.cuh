@@ -19,6 +19,7 @@ enum : int {
   kErrNonFinite = 1,      // a molecule produced a non-finite population
   kErrCouplingSeries = 2, // |theta E'| too large for the coupling series
   kErrPrescribedRange = 4,
+  kErrTimeout = 8,        // a bounded wait on an asynchronous copy gave up
 };
 
 // Incident pulse parameters of one sim.
@@ -79,20 +80,25 @@ struct SpeciesDev {
   int nmol;                 // molecules of this species
   const int* mol;           // their global ids (sorted by species, then by id)
   float2* psi;              // state [nmol][2][nrot][nr] (phi = T^{1/2} psi form)
-  // phase deltas e^{-i V dtau} - 1 as hi/lo (c_hi, s_hi, c_lo, s_lo) per (s, j, r)
-  const float4* vdelta;     // [2][jmax+1][nr]
-  const float2* vhalf;      // [2][jmax+1][nr] e^{-i V dtau/2}
-  const float4* kdelta;     // [nr] (e^{-i k^2 dtau / 2mu} - 1) / nr (hi/lo), natural k order
-  const float4* kphase_inv; // [nr] e^{+i k^2 dtau / 4mu} / nr, for T^{-1/2} readout
-  const float4* twiddle;    // [n1][n2]: exp(-2 pi i n1 k2 / nr) hi/lo
+  // per (s, j, r): e^{-i V dtau} - 1 and e^{-i V dtau/2}
+  const float2* vdelta;     // [2][jmax+1][nr]
+  const float2* vhalf;      // [2][jmax+1][nr]
+  const float2* kdelta;     // [nr] (e^{-i k^2 dtau / 2mu} - 1) / nr, natural k order
+  const float2* khalf;      // [nr] e^{-i k^2 dtau / 4mu} / nr, for the psi = T^{1/2} s readout
+  const float2* twiddle;    // [n2][n1]: exp(-2 pi i n1 k2 / nr)
   const float2* maskw;      // [nr]: (m, 1 - m^2)
   const float* r;           // [nr]
-  // coupling rows: for each channel c of one surface, kMaxCoupl entries
-  // (neighbor channel, coefficient, kind: 0 = Z (Ez), 1 = S+ (E+), 2 = S- (E-))
-  const int4* coupl;        // [nrot][kMaxCoupl]: x = nbr, y = kind, z = float bits of coef, w unused
   double theta;             // d * dtau
   double dipole;            // d (e a0)
   float dR;
+};
+
+// One nonzero of an angular coupling row.
+struct CouplEntry {
+  int nbr;     // neighbour channel j^2 + j + m, -1 = unused
+  float coef;
+  int kind;
+  int pad;
 };
 
 // Per-molecule data shared by all species.
@@ -123,6 +129,7 @@ void launch_mol_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int 
                      int* err, cudaStream_t s);
 void launch_mol_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s);
 size_t mol_step_smem(int nr, int nrot);
+cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip);
 void launch_step_counter(long long* step, cudaStream_t s);
 cudaError_t launch_broadcast_row(float2* psi, const float2* row, int nr, size_t per, long long nmol,
                                  cudaStream_t s);
