@@ -52,17 +52,18 @@ def _peaks():
 
 
 def _kernel_traffic(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, valid only while
+    """DRAM bytes per launch from the committed ncu summary, valid only while
     the kernel's source is unchanged (sha256 of the .cu file)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    d = json.load(open(path)).get(kernel)
-    if not d:
-        return None
-    src = os.path.join(ROOT, "paper_2209_04487_gb300", "csrc", d["source"])
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return d["bytes_per_launch"] if sha == d["sha256"] else None
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel:
+            src = os.path.join(ROOT, "paper_2209_04487_gb300", "csrc", f[1])
+            sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+            return float(f[3]) if sha == f[2] else None
+    return None
 
 
 class Clocks:

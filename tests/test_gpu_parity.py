@@ -149,3 +149,67 @@ def test_config0_full_coupled_parity(B):
     assert np.abs(P - Po).max() < 1e-5
     sel = Po[:, 1] > 1e-10
     assert np.max(np.abs(P[sel, 1] - Po[sel, 1]) / Po[sel, 1]) < 1e-3
+
+
+def test_splitring_full_size_molecules_sampled(B):
+    """The benchmark workload's molecule set at full size (50,000 molecules,
+    the bench's launch configuration), driven by a seeded prescribed field;
+    a seeded sample is integrated one by one by the oracle."""
+    wl = W.config1(nsteps=120)
+    n = wl.n_molecules
+    amp, wave = W.prescribed_drive(n, wl.nsteps, wl.dt, E0=2e10, carrier_ev=6.5, fwhm=0.4e-15,
+                                   t0=0.15e-15)
+    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED)
+    sim.set_prescribed(amp, wave)
+    sim.step(wl.nsteps)
+    P = sim.populations()
+    mu = sim.dipoles()
+    absb, _ = sim.dissociation()
+    sample = np.sort(np.random.default_rng(99).choice(n, 24, replace=False))
+    o = PrescribedOracle(wl, amp, wave, select=sample).run(wl.nsteps)
+    Po = o.populations()
+    assert np.abs(P[sample] - Po).max() < 1e-5
+    sel = Po[:, 1] > 1e-10
+    assert sel.sum() > 10
+    assert np.max(np.abs(P[sample][sel, 1] - Po[sel, 1]) / Po[sel, 1]) < 1e-3
+    assert np.abs(mu[sample] - o.mu).max() < 1e-4 * np.abs(o.mu).max()
+    # every molecule, any size: norm bookkeeping and finite values
+    tot = P.sum(axis=1) + absb.sum(axis=1)
+    assert np.isfinite(P).all() and np.abs(tot - 1).max() < 2e-6
+
+
+def test_splitring_full_grid_fields(B):
+    """The benchmark grid at full size (128x128x192, silver rings, glass,
+    CPML, TF/SF) without molecules, 40 steps of a short pulse, against the
+    oracle on the whole grid."""
+    import workloads.configs as C
+    wl = C.custom("split ring grid", 128, 128, 192, src_k=20, pulses=[[1e9, 1.8, 0.5e-15, 0.2e-15]],
+                  geometry=C._srr_geometry, n_per_sim=0, nsteps=40)
+    sim = B.Simulation(wl)
+    sim.step(wl.nsteps)
+    E, H = sim.fields(B.MS_FIELD_E), sim.fields(B.MS_FIELD_H)
+    o = CoupledOracle(wl).run(wl.nsteps)
+    Eo, Ho = _fields_oracle(o)
+    assert np.abs(Eo).max() > 1e7
+    assert _rel(E, Eo) < 1e-4
+    assert _rel(H, Ho) < 1e-4
+
+
+def test_independent_sims_in_one_launch(B):
+    """Two independent simulations (different carriers, the frequency-sweep
+    pattern) advance in the same launches and each matches its own oracle."""
+    sp = W.species_config0(jmax=2)
+    wl = W.custom("two sims", 12, 12, 48, nsim=2, src_k=14,
+                  pulses=[[2e10, 1.3, 2e-15, 2e-15], [2e10, 2.3, 2e-15, 2e-15]],
+                  layer=(22, 25), n_per_sim=40, species=[sp], seed=8, nsteps=300)
+    sim = B.Simulation(wl)
+    sim.step(wl.nsteps)
+    o = CoupledOracle(wl).run(wl.nsteps)
+    for s in range(2):
+        E = sim.fields(B.MS_FIELD_E, s)
+        Eo = np.stack([o.f.Ex[s], o.f.Ey[s], o.f.Ez[s]])
+        assert _rel(E, Eo) < 1e-4
+    P = sim.populations()
+    assert np.abs(P - o.populations()).max() < 1e-5
+    # the two carriers give different responses
+    assert np.abs(sim.fields(B.MS_FIELD_E, 0) - sim.fields(B.MS_FIELD_E, 1)).max() > 1e6

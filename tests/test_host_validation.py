@@ -1,0 +1,111 @@
+"""Host-side descriptor validation of ms_create (runs before any device
+call, so it needs no GPU): invalid inputs return MS_EINVAL, valid inputs on
+a machine without an sm_103 device return MS_EUNSUPPORTED, never a crash."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2209_04487_gb300 import build
+    build.build()
+    from paper_2209_04487_gb300 import binding
+    return binding
+
+
+def _create(B, wl, mutate=None):
+    keep = []
+    src = np.ascontiguousarray(wl.src, np.float64)
+    g = B.GridDesc(wl.nx, wl.ny, wl.nz, wl.nsim, wl.dx, wl.dt, wl.pml, B.MS_BC_PML, wl.src_k,
+                   src.ctypes.data_as(C.POINTER(C.c_double)))
+    eps = np.array([m[0] for m in wl.materials])
+    wp = np.array([m[1] for m in wl.materials])
+    ga = np.array([m[2] for m in wl.materials])
+    mid = np.ascontiguousarray(wl.mat_id)
+    keep += [src, eps, wp, ga, mid]
+    m = B.MaterialsDesc(len(eps), eps.ctypes.data_as(C.POINTER(C.c_double)),
+                        wp.ctypes.data_as(C.POINTER(C.c_double)),
+                        ga.ctypes.data_as(C.POINTER(C.c_double)),
+                        mid.ctypes.data_as(C.POINTER(C.c_uint8)))
+    sp = (B.SpeciesDesc * 1)(B.species_desc(wl.species[0]))
+    sid = np.ascontiguousarray(wl.species_id)
+    simid = np.ascontiguousarray(wl.sim_id)
+    pos = np.ascontiguousarray(wl.pos)
+    q = np.ascontiguousarray(wl.quat)
+    keep += [sp, sid, simid, pos, q]
+    d = B.MoleculesDesc(1, sp, wl.n_molecules, sid.ctypes.data_as(C.POINTER(C.c_int32)),
+                        simid.ctypes.data_as(C.POINTER(C.c_int32)),
+                        pos.ctypes.data_as(C.POINTER(C.c_double)), q.ctypes.data_as(C.POINTER(C.c_double)))
+    o = B.Options()
+    o.drive = B.MS_DRIVE_FDTD
+    o.mol_substeps = 1
+    if mutate:
+        mutate(g, m, d, o, keep)
+    h = C.c_void_p()
+    rc = B.LIB.ms_create(C.byref(g), C.byref(m), C.byref(d), C.byref(o), C.byref(h))
+    if rc == B.MS_OK:
+        B.LIB.ms_destroy(h)
+    return rc
+
+
+def _wl():
+    return W.custom("v", 8, 8, 48, src_k=14, layer=(20, 24), n_per_sim=5, nsteps=10)
+
+
+def test_valid_descriptor_reaches_the_device_check(B):
+    import torch
+    rc = _create(B, _wl())
+    if torch.cuda.is_available():
+        assert rc == B.MS_OK
+    else:
+        assert rc == B.MS_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("what", ["courant", "nx", "pml", "src_in_pml", "material_id", "species_nr",
+                                  "jmax", "position", "quaternion", "precision_mixed", "alloc_half"])
+def test_invalid_descriptors_are_rejected(B, what):
+    def mutate(g, m, d, o, keep):
+        if what == "courant":
+            g.dt_s = g.dx_m / 299792458.0
+        elif what == "nx":
+            g.nx = 0
+        elif what == "pml":
+            g.pml_cells = 30
+        elif what == "src_in_pml":
+            g.src_plane_z = 5
+        elif what == "material_id":
+            bad = np.full(8 * 8 * 48, 7, np.uint8)
+            keep.append(bad)
+            m.material_id = bad.ctypes.data_as(C.POINTER(C.c_uint8))
+        elif what == "species_nr":
+            d.species[0].nr = 100
+        elif what == "jmax":
+            d.species[0].jmax = 12
+        elif what == "position":
+            p = np.array(np.ctypeslib.as_array(d.pos_m, shape=(3 * d.n_molecules,)))
+            p[2] = 1.0
+            keep.append(p)
+            d.pos_m = p.ctypes.data_as(C.POINTER(C.c_double))
+        elif what == "quaternion":
+            qz = np.zeros(4 * d.n_molecules)
+            keep.append(qz)
+            d.orient = qz.ctypes.data_as(C.POINTER(C.c_double))
+        elif what == "precision_mixed":
+            o.precision = B.MS_PREC_MIXED_BF16X3
+        elif what == "alloc_half":
+            o.alloc = B._ALLOC(lambda n, c: None)
+    rc = _create(B, _wl(), mutate)
+    expect = {"species_nr": B.MS_EUNSUPPORTED, "jmax": B.MS_EUNSUPPORTED,
+              "precision_mixed": B.MS_EUNSUPPORTED}.get(what, B.MS_EINVAL)
+    assert rc == expect, (what, rc)
+
+
+def test_null_handles(B):
+    assert B.LIB.ms_step(None, 1) == B.MS_EINVAL
+    assert B.LIB.ms_read_populations(None, 0, 0, None, None) == B.MS_EINVAL
+    assert B.LIB.ms_step_count(None) == -1
+    B.LIB.ms_destroy(None)
