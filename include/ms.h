@@ -64,6 +64,13 @@ enum { MS_BC_PML = 0, MS_BC_PERIODIC = 1 };
 enum { MS_PREC_FP32 = 0, MS_PREC_MIXED_BF16X3 = 1 };
 enum { MS_DRIVE_FDTD = 0, MS_DRIVE_PRESCRIBED = 1 };
 enum { MS_FIELD_E = 0, MS_FIELD_H = 1 };
+/* Molecular kernel layout: MS_MOL_AUTO picks per species; MS_MOL_FUSED keeps
+ * each molecule's state in shared memory for the whole step (species whose
+ * state fits, up to J = 8 at N_r = 64); MS_MOL_STREAMING runs the kinetic
+ * pass over blocks of rows into a device scratch buffer of the state's size
+ * and then streams state and scratch through the R-space pass (any species
+ * up to J = 16). */
+enum { MS_MOL_AUTO = 0, MS_MOL_FUSED = 1, MS_MOL_STREAMING = 2 };
 
 /* Grid and source.  dt must satisfy dt <= dx/(sqrt(3) c) (checked).
  * src_plane_z: absolute z index of the TF/SF plane (total field for
@@ -94,7 +101,7 @@ typedef struct {
 
 /* One molecular species (atomic units).  Radial grid r_i = rmin + i dR,
  * dR = (rmax - rmin)/(nr - 1), nr in {64, 128, 256}; rotational channels
- * j <= jmax, |m| <= j ((jmax+1)^2 per surface), jmax <= 8.
+ * j <= jmax, |m| <= j ((jmax+1)^2 per surface), jmax <= 16.
  * Ground surface De (1 - exp(-a (r - re)))^2 - De (Eq. 6); excited surface
  * A + B exp(-beta (r - rc)) (Eq. 7 is A = 0, B = 2 D_e); constant
  * transition dipole d [e a0]; absorbing mask cos(pi/2 (r-ra)/(rmax-ra))^p
@@ -134,6 +141,7 @@ typedef struct {
   void (*free)(void* ptr, void* ctx);
   void* alloc_ctx;
   void* stream;
+  int32_t mol_path;     /* MS_MOL_AUTO, MS_MOL_FUSED or MS_MOL_STREAMING */
 } ms_options;
 
 /* Create a simulation: validates the descriptors, builds the species

@@ -30,7 +30,7 @@ namespace ms {
 
 namespace {
 
-constexpr int kPad = 8;  // row padding (float2): keeps rows 16-byte aligned and banks spread
+constexpr int kPad = 0;  // state rows are stored unpadded (one bulk copy per molecule)
 
 template <int NR>
 struct FFTShape;
@@ -151,6 +151,15 @@ __device__ __forceinline__ double warp_sum(double v) {
 // DFT over n2 and the twiddle exp(-2 pi i n1 k2/NR); step B: per k2, an
 // N1-point DFT over n1.  The intermediate y[n1][k2] lives at n1 + N1 k2,
 // xor-swizzled within each block of N1 so that step B is conflict free.
+// Position of y[n1][k2] of `row` within the row: the xor with (k2 mod N1)
+// spreads step B's N2 threads over distinct banks, the xor with CR for odd
+// rows keeps the two rows that share a half-warp apart.
+template <int N1, int N2>
+__device__ __forceinline__ int swz(int n1, int k2, int row) {
+  constexpr int CR = N1 > N2 ? N2 : (N1 == N2 && N1 == 8 ? 1 : 0);
+  return (n1 ^ (k2 % N1) ^ ((row & 1) * CR)) + N1 * k2;
+}
+
 template <int NR>
 __device__ void kinetic_pass(float2* st, int rows, const float2* kph, const float2* tw) {
   using S = FFTShape<NR>;
@@ -171,7 +180,7 @@ __device__ void kinetic_pass(float2* st, int rows, const float2* kph, const floa
         dft_reg<N2, false>(x);
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2)
-          st[row * NRP + (n1 ^ (k2 % N1)) + N1 * k2] = cmul(x[k2], tw[k2 * N1 + n1]);
+          st[row * NRP + swz<N1, N2>(n1, k2, row)] = cmul(x[k2], tw[k2 * N1 + n1]);
       }
       __syncwarp();
     }
@@ -185,13 +194,13 @@ __device__ void kinetic_pass(float2* st, int rows, const float2* kph, const floa
       if (row < rows) {
         float2 x[N1];
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) x[n1] = st[row * NRP + (n1 ^ (k2 % N1)) + N1 * k2];
+        for (int n1 = 0; n1 < N1; ++n1) x[n1] = st[row * NRP + swz<N1, N2>(n1, k2, row)];
         dft_reg<N1, false>(x);  // x[k1] = X[k2 + N2 k1]
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) x[k1] = cmul(x[k1], kph[k2 + N2 * k1]);
         dft_reg<N1, true>(x);
 #pragma unroll
-        for (int n1 = 0; n1 < N1; ++n1) st[row * NRP + (n1 ^ (k2 % N1)) + N1 * k2] = x[n1];
+        for (int n1 = 0; n1 < N1; ++n1) st[row * NRP + swz<N1, N2>(n1, k2, row)] = x[n1];
       }
     }
   }
@@ -206,7 +215,7 @@ __device__ void kinetic_pass(float2* st, int rows, const float2* kph, const floa
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
           const float2 w = tw[k2 * N1 + n1];
-          x[k2] = cmul(st[row * NRP + (n1 ^ (k2 % N1)) + N1 * k2], make_float2(w.x, -w.y));
+          x[k2] = cmul(st[row * NRP + swz<N1, N2>(n1, k2, row)], make_float2(w.x, -w.y));
         }
         dft_reg<N2, true>(x);
       }
@@ -254,6 +263,14 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
 }
 constexpr long long kWaitPolls = 1LL << 24;  // far beyond any copy's duration
 
+// 16-byte asynchronous global -> shared copies (per thread), completed by
+// cp.async.wait_group.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void load_state(float2* st, const float2* g, int rows, int NR, int NRP) {
   const float4* g4 = reinterpret_cast<const float4*>(g);
   const int per_row = NR / 2;
@@ -284,7 +301,6 @@ cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip)
 }
 
 constexpr int kChunk = 32;            // widest R-space chunk (one radial point per lane)
-constexpr int kMaxRowsPerThread = 12;  // rows a thread owns in the R-space pass
 
 // ----------------------------------------------------------------------------
 // the coupled molecular step, s = T^{-1/2} psi stored:
@@ -308,25 +324,33 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, float x) {
   hi = t;
 }
 
-template <int NR>
-__global__ void __launch_bounds__(FFTShape<NR>::THREADS, 2)
+// FUSED: the whole state is staged in shared memory and the kinetic pass runs
+// in this kernel.  Otherwise (streaming form) d2 = (T - 1) s comes from the
+// scratch written by mol_kinetic_kernel and is streamed chunk by chunk with s.
+// MAXR bounds the rows a thread owns in the R-space pass.
+template <int NR, bool FUSED, int MAXR>
+__global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 ? 4 : (MAXR <= 12 ? 2 : 1)))
     mol_step_kernel(SpeciesDev sp, MolDev md, Grid g, int prescribed, int CH, int* err) {
-  // CH radial points per chunk (32, 16 or 8): a warp covers 32/CH rows of CH points
+  // CH radial points per chunk (32 down to 4): a warp covers 32/CH rows of CH points
   constexpr int NT = FFTShape<NR>::THREADS, NRP = NR + kPad, NW = NT / 32;
   extern __shared__ float4 smem4[];
   const int nrot = sp.nrot, rows = 2 * nrot, J = sp.jmax;
-  float2* s_tw = reinterpret_cast<float2*>(smem4);      // [N2][N1] twiddles
-  float2* s_kd = s_tw + NR;                              // [NR] kinetic deltas
-  float2* st = s_kd + NR;                                // [rows][NRP] state, then d2
-  float2* bY = st + rows * NRP;                          // [rows][CH] Taylor terms / new state
+  float2* s_tw = reinterpret_cast<float2*>(smem4);      // [N2][N1] twiddles (fused)
+  float2* s_kd = s_tw + (FUSED ? NR : 0);                // [NR] kinetic deltas (fused)
+  float2* st = s_kd + (FUSED ? NR : 0);                  // [rows][NRP] state, then d2 (fused)
+  float2* bY = st + (FUSED ? rows * NRP : 0);            // [rows][CH] Taylor terms / new state
   float2* bZ = bY + rows * CH;                           // [rows][CH] Taylor terms
-  // per chunk, double buffered: old state [rows][CH], e^{-iV dtau} - 1
-  // [2(J+1)][CH] and absorber mask [CH]
-  const int cbuf = (rows + 2 * (J + 1) + 1) * CH;
+  // per chunk, double buffered: old state [rows][CH], (streaming: d2
+  // [rows][CH]), e^{-iV dtau} - 1 [2(J+1)][CH] and absorber mask [CH]
+  const int nd = FUSED ? 0 : rows;
+  const int cbuf = (rows + nd + 2 * (J + 1) + 1) * CH;
   float2* bC = bZ + rows * CH;
   int2* s_prog = reinterpret_cast<int2*>(bC + 2 * cbuf);  // [nrot][6] (nbr*CH, coupling) this step
   int2* s_rinfo = s_prog + nrot * kMaxCoupl;             // [rows] (table row, m + J)
-  __shared__ __align__(8) unsigned long long s_bar[3];   // [0] state, [1], [2] chunk buffers
+  __shared__ __align__(8) unsigned long long s_bar[1];   // the state copy
+  __shared__ float s_rot[9];                             // molecule -> lab rotation
+  __shared__ double s_mu[3];                             // lab dipole of the previous step
+  __shared__ double s_abs[2];                            // absorbed norm so far
   __shared__ float2 s_ph[2 * kMaxJ + 1];                 // e^{+i m phi_E}
   __shared__ float s_fld[2];                             // E_perp, E'_z (a.u.)
   __shared__ int s_nterms;
@@ -342,41 +366,41 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, 2)
   float2* gs = sp.psi + (long long)lm * rows * NR;
 
   // chunk copy: old state, potential deltas and mask of radial points [r0, r0 + CH)
-  // issued by the 32 lanes of the last warp (`ln` = lane), expect_tx first
-  auto issue_chunk = [&](int r0, int b, int ln) {
-    float2* bu = bC + b * cbuf;
-    float2* bv = bu + rows * CH;
-    float2* bm = bv + 2 * (J + 1) * CH;
-    if (ln == 0) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      mbar_expect_tx(&s_bar[1 + b], (unsigned)(cbuf * sizeof(float2)));
+  // every thread copies 16-byte pieces (cp.async); rows: old state, then
+  // the potential deltas, then the mask
+  const float2* gd = FUSED ? nullptr : sp.d2 + (long long)lm * rows * NR;
+  auto issue_chunk = [&](int r0, int b) {
+    float2* buf = bC + b * cbuf;
+    const int nv = 2 * (J + 1), per_row = CH / 2, nunits = (rows + nd + nv + 1) * per_row;
+    for (int u = t; u < nunits; u += NT) {
+      const int q = u / per_row, c2 = 2 * (u - q * per_row);
+      const float2* src;
+      if (q < rows) src = gs + (long long)q * NR;
+      else if (q < rows + nd) src = gd + (long long)(q - rows) * NR;
+      else if (q < rows + nd + nv) src = sp.vdelta + (long long)(q - rows - nd) * NR;
+      else src = sp.maskw;
+      cp_async16(buf + q * CH + c2, src + r0 + c2);
     }
-    __syncwarp();
-    const int nv = 2 * (J + 1);
-    for (int q = ln; q < rows + nv + 1; q += 32) {
-      if (q < rows) bulk_g2s(bu + q * CH, gs + (long long)q * NR + r0, CH * sizeof(float2), &s_bar[1 + b]);
-      else if (q < rows + nv) bulk_g2s(bv + (q - rows) * CH, sp.vdelta + (q - rows) * NR + r0, CH * sizeof(float2), &s_bar[1 + b]);
-      else bulk_g2s(bm, sp.maskw + r0, CH * sizeof(float2), &s_bar[1 + b]);
-    }
+    cp_async_commit();
   };
-  const bool issuer = w == NW - 1;
   if (t == 0) {
     mbar_init(&s_bar[0], 1);
-    mbar_init(&s_bar[1], 1);
-    mbar_init(&s_bar[2], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (issuer) {  // the whole state, one bulk copy per row; then the first chunk
-    if (lane == 0) mbar_expect_tx(&s_bar[0], (unsigned)(rows * NR * sizeof(float2)));
-    __syncwarp();
-    for (int row = lane; row < rows; row += 32)
-      bulk_g2s(st + row * NRP, gs + (long long)row * NR, NR * sizeof(float2), &s_bar[0]);
-    issue_chunk(0, 0, lane);
+  if (FUSED && t == 0) {  // the whole (contiguous) state in one bulk copy
+    mbar_expect_tx(&s_bar[0], (unsigned)(rows * NR * sizeof(float2)));
+    bulk_g2s(st, gs, (unsigned)(rows * NR * sizeof(float2)), &s_bar[0]);
   }
-  for (int q = t; q < NR; q += NT) {
-    s_tw[q] = __ldg(&sp.twiddle[q]);
-    s_kd[q] = __ldg(&sp.kdelta[q]);
+  issue_chunk(0, 0);
+  if (t < 9) s_rot[t] = md.rot[9 * (long long)m + t];
+  else if (t < 12) s_mu[t - 9] = md.mu[3 * (long long)m + (t - 9)];
+  else if (t < 14) s_abs[t - 12] = md.absorbed[2 * (long long)m + (t - 12)];
+  if (FUSED) {
+    for (int q = t; q < NR; q += NT) {
+      s_tw[q] = __ldg(&sp.twiddle[q]);
+      s_kd[q] = __ldg(&sp.kdelta[q]);
+    }
   }
   for (int q = t; q < rows; q += NT) {
     const int sf = q >= nrot, c = q - sf * nrot, j = j_of(c);
@@ -443,17 +467,19 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, 2)
       s_prog[q] = make_int2(ok ? e.nbr * CH : 0, __float_as_int(cf));
     }
   }
-  {
+  if (FUSED) {
     const bool ok = mbar_wait(&s_bar[0], 0, kWaitPolls);
     if (!__syncthreads_and(ok)) {  // uniform decision; copies still in flight get a second bounded wait
       if (t == 0) atomicOr(err, kErrTimeout);
       if (!ok) mbar_wait(&s_bar[0], 0, kWaitPolls);
+      cp_async_wait_all();
       return;
     }
+    // ---- kinetic pass: st <- d2 = (T - 1) s
+    kinetic_pass<NR>(st, rows, s_kd, s_tw);
+  } else {
+    __syncthreads();
   }
-
-  // ---- kinetic pass: st <- d2 = (T - 1) s
-  kinetic_pass<NR>(st, rows, s_kd, s_tw);
 
   // ---- R-space pass, CH radial points at a time; thread rows row0 + i*rstep
   const int nterms = s_nterms;
@@ -463,38 +489,36 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, 2)
   for (int ck = 0; ck < nchunks; ++ck) {
     const int r0 = ck * CH, r = r0 + rl, b = ck & 1;
     float2* bU = bC + b * cbuf;
-    const float2* bV = bU + rows * CH;
+    const float2* bD = bU + rows * CH;              // streaming form: d2 of the chunk
+    const float2* bV = bD + nd * CH;
     const float2* bM = bV + 2 * (J + 1) * CH;
-    // prefetch the next chunk into the other buffer (free since the last barrier)
-    if (issuer && ck + 1 < nchunks) issue_chunk(r0 + CH, b ^ 1, lane);
-    {
-      const bool ok = mbar_wait(&s_bar[1 + b], (ck >> 1) & 1, kWaitPolls);
-      if (!__syncthreads_and(ok)) {
-        if (t == 0) atomicOr(err, kErrTimeout);
-        if (!ok) mbar_wait(&s_bar[1 + b], (ck >> 1) & 1, kWaitPolls);
-        if (issuer && ck + 1 < nchunks) mbar_wait(&s_bar[2 - b], ((ck + 1) >> 1) & 1, kWaitPolls);
-        return;
-      }
-    }
-    // eta = D^dagger V^{1/2} u (rotated frame) into bZ
-    float2 sacc[kMaxRowsPerThread];
-#pragma unroll
-    for (int i = 0; i < kMaxRowsPerThread; ++i) {
-      sacc[i] = make_float2(0.f, 0.f);
-      const int row = row0 + i * rstep;
-      if (row < rows) {
-        const int2 ri = s_rinfo[row];
-        const float2 u = st[row * NRP + r] + bU[row * CH + rl];
-        bZ[row * CH + rl] = cmul(s_ph[ri.y], cmul(vhalf_of(bV[ri.x + rl]), u));
-      }
-    }
+    // this chunk's copies (issued one chunk earlier) are complete and
+    // visible; the other buffer is free since the previous chunk's barriers
+    cp_async_wait_all();
     __syncthreads();
+    if (ck + 1 < nchunks) issue_chunk(r0 + CH, b ^ 1);
+    // eta = D^dagger V^{1/2} u (rotated frame) into bZ (no coupling work when E' = 0)
+    float2 sacc[MAXR];
+#pragma unroll
+    for (int i = 0; i < MAXR; ++i) sacc[i] = make_float2(0.f, 0.f);
+    if (nterms > 0) {
+#pragma unroll
+      for (int i = 0; i < MAXR; ++i) {
+        const int row = row0 + i * rstep;
+        if (row < rows) {
+          const int2 ri = s_rinfo[row];
+          const float2 u = (FUSED ? st[row * NRP + r] : bD[row * CH + rl]) + bU[row * CH + rl];
+          bZ[row * CH + rl] = cmul(s_ph[ri.y], cmul(vhalf_of(bV[ri.x + rl]), u));
+        }
+      }
+      __syncthreads();
+    }
     float2* in = bZ;
     float2* out = bY;
     for (int n = 1; n <= nterms; ++n) {
       const float cn = theta / (float)n;
 #pragma unroll
-      for (int i = 0; i < kMaxRowsPerThread; ++i) {
+      for (int i = 0; i < MAXR; ++i) {
         const int row = row0 + i * rstep;
         if (row < rows) {
           const int sf = row >= nrot, c = row - sf * nrot;
@@ -524,13 +548,13 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, 2)
     const float mk = bM[rl].x;
     float sg = 0.f, se = 0.f, agf = 0.f, aef = 0.f;
 #pragma unroll
-    for (int i = 0; i < kMaxRowsPerThread; ++i) {
+    for (int i = 0; i < MAXR; ++i) {
       const int row = row0 + i * rstep;
       if (row < rows) {
         const int2 ri = s_rinfo[row];
         const int sf = row >= nrot;
         const float2 sv = bU[row * CH + rl];
-        const float2 d2 = st[row * NRP + r];
+        const float2 d2 = FUSED ? st[row * NRP + r] : bD[row * CH + rl];
         const float2 u = sv + d2;
         const float2 ph = s_ph[ri.y];
         const float2 vd = bV[ri.x + rl];
@@ -611,19 +635,18 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, 2)
     }
     __syncthreads();
     if (t < 3) {  // lab dipole component t: mu = O mu', mu' = d dR (Re(S+ + S-), Im(S+ - S-), 2 Re Z)
-      const float* O = md.rot + 9 * (long long)m;
       const float sc = (float)sp.dipole * sp.dR;
-      const float lab = sc * (O[3 * t] * s_fin[4] + O[3 * t + 1] * s_fin[5] + O[3 * t + 2] * s_fin[6]);
-      double* mu = md.mu + 3 * (long long)m + t;
+      const float lab = sc * (s_rot[3 * t] * s_fin[4] + s_rot[3 * t + 1] * s_fin[5] + s_rot[3 * t + 2] * s_fin[6]);
       const double nl = (double)lab;
-      md.dmu[3 * (long long)m + t] = nl - *mu;
-      *mu = nl;
+      md.dmu[3 * (long long)m + t] = nl - s_mu[t];
+      md.mu[3 * (long long)m + t] = nl;
     } else if (t < 5) {  // populations P_g, P_e
       const double P = ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
       md.pop[2 * (long long)m + (t - 3)] = P;
       if (!isfinite(P)) atomicOr(err, kErrNonFinite);
-    } else if (t < 7) {  // absorbed norm of this step
-      md.absorbed[2 * (long long)m + (t - 5)] += ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
+    } else if (t < 7) {  // absorbed norm, cumulative
+      md.absorbed[2 * (long long)m + (t - 5)] =
+          s_abs[t - 5] + ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
     }
   }
 }
@@ -638,7 +661,7 @@ namespace ms {
 
 template <int NR>
 __global__ void __launch_bounds__(FFTShape<NR>::THREADS)
-    mol_observe_kernel(SpeciesDev sp, MolDev md) {
+    mol_observe_kernel(SpeciesDev sp, MolDev md, int RB) {
   constexpr int NRP = NR + kPad;
   extern __shared__ float4 smem4[];
   float2* s_tw = reinterpret_cast<float2*>(smem4);
@@ -653,18 +676,22 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS)
     s_kh[q] = __ldg(&sp.khalf[q]);
   }
   const float2* ge = sp.psi + ((long long)lm * 2 + 1) * nrot * NR;  // excited rows
-  load_state(st, ge, nrot, NR, NRP);
-  __syncthreads();
-  kinetic_pass<NR>(st, nrot, s_kh, s_tw);
   double num = 0.0, den = 0.0;
-  for (int r = threadIdx.x; r < NR; r += blockDim.x) {
-    float a = 0.f;
-    for (int row = 0; row < nrot; ++row) {
-      const float2 v = st[row * NRP + r];
-      a = fmaf(v.x, v.x, fmaf(v.y, v.y, a));
+  for (int b0 = 0; b0 < nrot; b0 += RB) {  // blocks of RB rows
+    const int nb = min(RB, nrot - b0);
+    __syncthreads();
+    load_state(st, ge + (long long)b0 * NR, nb, NR, NRP);
+    __syncthreads();
+    kinetic_pass<NR>(st, nb, s_kh, s_tw);  // psi = T^{1/2} s
+    for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+      float a = 0.f;
+      for (int row = 0; row < nb; ++row) {
+        const float2 v = st[row * NRP + r];
+        a = fmaf(v.x, v.x, fmaf(v.y, v.y, a));
+      }
+      den += (double)a;
+      num += (double)a * (double)__ldg(&sp.r[r]);
     }
-    den += (double)a;
-    num += (double)a * (double)__ldg(&sp.r[r]);
   }
   num = warp_sum(num);
   den = warp_sum(den);
@@ -703,15 +730,57 @@ cudaError_t launch_broadcast_row(float2* psi, const float2* row, int nr, size_t 
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------
+// streaming form, first pass: d2 = (T - 1) s for blocks of rows (rows of all
+// molecules of a species are independent here); one bulk copy per block
+// ----------------------------------------------------------------------------
+template <int NR>
+__global__ void __launch_bounds__(FFTShape<NR>::THREADS)
+    mol_kinetic_kernel(SpeciesDev sp, long long rows_total, int RB, int* err) {
+  extern __shared__ float4 smem4[];
+  float2* s_tw = reinterpret_cast<float2*>(smem4);
+  float2* s_kd = s_tw + NR;
+  float2* st = s_kd + NR;
+  __shared__ __align__(8) unsigned long long s_bar;
+  const long long r0 = blockIdx.x * (long long)RB;
+  const int nrows = (int)min((long long)RB, rows_total - r0);
+  const int t = threadIdx.x;
+  if (t == 0) {
+    mbar_init(&s_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (t == 0) {
+    mbar_expect_tx(&s_bar, (unsigned)(nrows * NR * sizeof(float2)));
+    bulk_g2s(st, sp.psi + r0 * NR, (unsigned)(nrows * NR * sizeof(float2)), &s_bar);
+  }
+  for (int q = t; q < NR; q += blockDim.x) {
+    s_tw[q] = __ldg(&sp.twiddle[q]);
+    s_kd[q] = __ldg(&sp.kdelta[q]);
+  }
+  const bool ok = mbar_wait(&s_bar, 0, kWaitPolls);
+  if (!__syncthreads_and(ok)) {
+    if (t == 0) atomicOr(err, kErrTimeout);
+    if (!ok) mbar_wait(&s_bar, 0, kWaitPolls);
+    return;
+  }
+  kinetic_pass<NR>(st, nrows, s_kd, s_tw);
+  const float4* s4 = reinterpret_cast<const float4*>(st);
+  float4* d4 = reinterpret_cast<float4*>(sp.d2 + r0 * NR);
+  for (int q = t; q < nrows * NR / 2; q += blockDim.x) d4[q] = s4[q];
+}
+
 size_t mol_state_smem(int nr, int rows) { return (size_t)rows * (nr + kPad) * sizeof(float2); }
 
 static int threads_for(int nr) { return nr == 256 ? 256 : 128; }
 
-static size_t step_smem(int nr, int nrot, int ch) {
+static size_t step_smem(int nr, int nrot, int ch, bool fused) {
   const int rows = 2 * nrot;
   const int jm = (int)std::lround(std::sqrt((double)nrot)) - 1;
-  return 2 * (size_t)nr * sizeof(float2) + mol_state_smem(nr, rows) + 2 * (size_t)rows * ch * sizeof(float2) +
-         2 * (size_t)(rows + 2 * (jm + 1) + 1) * ch * sizeof(float2) +
+  const size_t nd = fused ? 0 : rows;
+  return (fused ? 2 * (size_t)nr * sizeof(float2) + mol_state_smem(nr, rows) : 0) +
+         2 * (size_t)rows * ch * sizeof(float2) +
+         2 * (size_t)(rows + nd + 2 * (jm + 1) + 1) * ch * sizeof(float2) +
          (size_t)nrot * kMaxCoupl * sizeof(int2) + (size_t)rows * sizeof(int2);
 }
 
@@ -721,33 +790,66 @@ static int rows_per_thread(int nrot, int ch) {
   return (2 * nrot + rstep - 1) / rstep;
 }
 
-// widest chunk that keeps two CTAs per SM, else the widest that fits one
-static int chunk_for(int nr, int nrot, size_t* smem) {
-  // two CTAs per SM: 2 x (dynamic + static (< 800 B) + 1 KB reserved) <= 228 KB
-  const size_t cap1 = 227 * 1024, cap2 = 228 * 1024 / 2 - 1024 - 800;
-  for (size_t cap : {cap2, cap1})
-    for (int ch = kChunk; ch >= 8; ch >>= 1)
-      if (rows_per_thread(nrot, ch) <= kMaxRowsPerThread && step_smem(nr, nrot, ch) <= cap) {
-        *smem = step_smem(nr, nrot, ch);
-        return ch;
-      }
-  *smem = (size_t)-1;  // does not fit: rejected at create
-  return 8;
+// Launch shape of one species: chunk width, rows-per-thread bound, shared
+// memory.  Fused: the widest chunk keeping two CTAs per SM.  Streaming: the
+// widest chunk with at most 4 rows per thread (64 registers, four CTAs per
+// SM), else at most 12.
+struct StepShape {
+  int ch, maxr;
+  size_t smem;
+  bool ok;
+};
+static StepShape step_shape(int nr, int nrot, bool fused) {
+  // k CTAs per SM: k x (dynamic + static (< 800 B) + 1 KB reserved) <= 228 KB
+  auto cap = [](int k) { return (size_t)(228 * 1024 / k - 1024 - 800); };
+  if (fused) {
+    for (int k : {2, 1})
+      for (int ch = kChunk; ch >= 8; ch >>= 1)
+        if (rows_per_thread(nrot, ch) <= 12 && step_smem(nr, nrot, ch, true) <= cap(k))
+          return {ch, 12, step_smem(nr, nrot, ch, true), true};
+    return {8, 12, 0, false};
+  }
+  for (int maxr : {4, 12, 24})
+    for (int ch = kChunk; ch >= 4; ch >>= 1)
+      if (rows_per_thread(nrot, ch) <= maxr &&
+          step_smem(nr, nrot, ch, false) <= cap(maxr == 4 ? 4 : (maxr == 12 ? 2 : 1)))
+        return {ch, maxr, step_smem(nr, nrot, ch, false), true};
+  return {4, 24, 0, false};
 }
 
-size_t mol_step_smem(int nr, int nrot) {
-  size_t s;
-  chunk_for(nr, nrot, &s);
-  return s;
+bool mol_step_supported(int nr, int nrot, int path) {
+  return step_shape(nr, nrot, path == MS_MOL_FUSED).ok;
+}
+
+// rows per kinetic block: 32 KB of state
+static int kinetic_rows(int nr) { return 4096 / nr; }
+
+template <int NR, bool FUSED, int MAXR>
+static void launch_step_tt(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                           const StepShape& sh, cudaStream_t s) {
+  auto k = mol_step_kernel<NR, FUSED, MAXR>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+  k<<<sp.nmol, FFTShape<NR>::THREADS, sh.smem, s>>>(sp, md, g, prescribed, sh.ch, err);
 }
 
 template <int NR>
 static void launch_step_t(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed,
                           int* err, cudaStream_t s) {
-  size_t smem;
-  const int ch = chunk_for(NR, sp.nrot, &smem);
-  cudaFuncSetAttribute(mol_step_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  mol_step_kernel<NR><<<sp.nmol, FFTShape<NR>::THREADS, smem, s>>>(sp, md, g, prescribed, ch, err);
+  const bool fused = sp.path == MS_MOL_FUSED;
+  const StepShape sh = step_shape(NR, sp.nrot, fused);
+  if (fused) {
+    launch_step_tt<NR, true, 12>(sp, md, g, prescribed, err, sh, s);
+    return;
+  }
+  const long long rows_total = (long long)sp.nmol * 2 * sp.nrot;
+  const int RB = kinetic_rows(NR);
+  const size_t ksmem = 2 * (size_t)NR * sizeof(float2) + (size_t)RB * NR * sizeof(float2);
+  cudaFuncSetAttribute(mol_kinetic_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem);
+  mol_kinetic_kernel<NR><<<(unsigned)((rows_total + RB - 1) / RB), FFTShape<NR>::THREADS, ksmem, s>>>(
+      sp, rows_total, RB, err);
+  if (sh.maxr == 4) launch_step_tt<NR, false, 4>(sp, md, g, prescribed, err, sh, s);
+  else if (sh.maxr == 12) launch_step_tt<NR, false, 12>(sp, md, g, prescribed, err, sh, s);
+  else launch_step_tt<NR, false, 24>(sp, md, g, prescribed, err, sh, s);
 }
 
 void launch_mol_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
@@ -762,9 +864,10 @@ void launch_mol_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int 
 
 template <int NR>
 static void launch_observe_t(const SpeciesDev& sp, const MolDev& md, cudaStream_t s) {
-  const size_t smem = 2 * (size_t)NR * sizeof(float2) + mol_state_smem(NR, sp.nrot);
+  const int RB = min(sp.nrot, 4096 / NR);
+  const size_t smem = 2 * (size_t)NR * sizeof(float2) + mol_state_smem(NR, RB);
   cudaFuncSetAttribute(mol_observe_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  mol_observe_kernel<NR><<<sp.nmol, FFTShape<NR>::THREADS, smem, s>>>(sp, md);
+  mol_observe_kernel<NR><<<sp.nmol, FFTShape<NR>::THREADS, smem, s>>>(sp, md, RB);
 }
 
 void launch_mol_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s) {

@@ -240,9 +240,12 @@ ms_status upload_angular_tables() {
   return ms::upload_coupling_tables(rot.data(), dip.data()) == cudaSuccess ? MS_OK : MS_ECUDA;
 }
 
-ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const std::vector<int>& ids) {
+ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const std::vector<int>& ids,
+                        int path) {
   ms::SpeciesDev& sp = s->sp[si];
   const int nr = d.nr, J = d.jmax, nrot = (J + 1) * (J + 1);
+  // layout: the streaming form unless the caller asks for the fused one
+  sp.path = path == MS_MOL_FUSED ? MS_MOL_FUSED : MS_MOL_STREAMING;
   sp.nr = nr;
   sp.jmax = J;
   sp.nrot = nrot;
@@ -317,6 +320,8 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   std::vector<float2> row0(nr);
   for (int a = 0; a < nr; ++a) row0[a] = make_float2((float)phi0[a].real(), (float)phi0[a].imag());
   MS_TRY(zeros(s, &sp.psi, per * ids.size()));
+  sp.d2 = nullptr;
+  if (sp.path == MS_MOL_STREAMING) MS_TRY(zeros(s, &sp.d2, per * ids.size()));
   float2* d_row0 = nullptr;
   MS_TRY(upload(s, &d_row0, row0.data(), row0.size()));
   if (ms::launch_broadcast_row(sp.psi, d_row0, nr, per, (long long)ids.size(), s->stream) != cudaSuccess)
@@ -518,7 +523,7 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
     std::vector<int> ids;
     for (long long q = 0; q < n; ++q)
       if (D->species_id[q] == si) ids.push_back((int)q);
-    MS_TRY(build_species(s, si, D->species[si], dt, ids));
+    MS_TRY(build_species(s, si, D->species[si], dt, ids, O ? O->mol_path : MS_MOL_AUTO));
   }
   return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
 }
@@ -551,6 +556,7 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
   if (O && O->precision != MS_PREC_FP32) return MS_EUNSUPPORTED;
   if (O && O->mol_substeps != 0 && O->mol_substeps != 1) return MS_EUNSUPPORTED;
   if (O && ((O->alloc == nullptr) != (O->free == nullptr))) return MS_EINVAL;
+  if (O && (O->mol_path < MS_MOL_AUTO || O->mol_path > MS_MOL_STREAMING)) return MS_EINVAL;
   if (D && D->n_molecules > 0) {
     if (D->n_species <= 0 || D->n_species > ms::kMaxSpecies || !D->species || !D->species_id ||
         !D->pos_m || !D->orient)
@@ -562,7 +568,11 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
       if (sp.jmax < 0 || sp.jmax > ms::kMaxJ) return MS_EUNSUPPORTED;
       if (!(sp.rmax > sp.rmin) || !(sp.rmin > 0) || !(sp.mass_me > 0) || sp.absorber_power < 0)
         return MS_EINVAL;
-      if (ms::mol_step_smem(sp.nr, (sp.jmax + 1) * (sp.jmax + 1)) > 227 * 1024) return MS_EUNSUPPORTED;
+      const int nrot = (sp.jmax + 1) * (sp.jmax + 1);
+      const int path = O ? O->mol_path : MS_MOL_AUTO;
+      if (path == MS_MOL_FUSED ? !ms::mol_step_supported(sp.nr, nrot, MS_MOL_FUSED)
+                               : !ms::mol_step_supported(sp.nr, nrot, MS_MOL_STREAMING))
+        return MS_EUNSUPPORTED;
     }
     for (long long q = 0; q < D->n_molecules; ++q) {
       const int si = D->species_id[q];

@@ -10,8 +10,8 @@ namespace ms {
 
 constexpr int kMaxMaterials = 16;
 constexpr int kMaxSpecies = 8;
-constexpr int kMaxJ = 8;
-constexpr int kMaxRot = (kMaxJ + 1) * (kMaxJ + 1);  // 81 channels per surface
+constexpr int kMaxJ = 16;
+constexpr int kMaxRot = (kMaxJ + 1) * (kMaxJ + 1);  // 289 channels per surface
 constexpr int kMaxCoupl = 6;                          // nonzeros of R^hat per row
 
 // error bits latched in the device error word
@@ -79,7 +79,9 @@ struct SpeciesDev {
   int nr, jmax, nrot;
   int nmol;                 // molecules of this species
   const int* mol;           // their global ids (sorted by species, then by id)
-  float2* psi;              // state [nmol][2][nrot][nr] (phi = T^{1/2} psi form)
+  float2* psi;              // state [nmol][2][nrot][nr], s = T^{-1/2} psi
+  float2* d2;               // streaming form: scratch (T - 1) s, same layout
+  int path;                 // MS_MOL_FUSED or MS_MOL_STREAMING
   // per (s, j, r): e^{-i V dtau} - 1 and e^{-i V dtau/2}
   const float2* vdelta;     // [2][jmax+1][nr]
   const float2* vhalf;      // [2][jmax+1][nr]
@@ -128,7 +130,7 @@ void launch_aux_e(const Grid& g, cudaStream_t s);
 void launch_mol_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed,
                      int* err, cudaStream_t s);
 void launch_mol_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s);
-size_t mol_step_smem(int nr, int nrot);
+bool mol_step_supported(int nr, int nrot, int path);
 cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip);
 void launch_step_counter(long long* step, cudaStream_t s);
 cudaError_t launch_broadcast_row(float2* psi, const float2* row, int nr, size_t per, long long nmol,

@@ -57,14 +57,19 @@ def test_fields_match_oracle(B, geo, nx, ny, nz, steps):
     assert np.abs(Eo).max() > 1e8
 
 
-@pytest.mark.parametrize("nr,jmax,nmol", [(64, 1, 37), (128, 4, 19), (64, 8, 9), (256, 2, 5)])
-def test_prescribed_molecules_match_oracle(B, nr, jmax, nmol):
+@pytest.mark.parametrize("nr,jmax,nmol,path", [
+    (64, 1, 37, "fused"), (64, 1, 37, "streaming"), (128, 4, 19, "fused"), (128, 4, 19, "streaming"),
+    (64, 8, 9, "fused"), (64, 8, 9, "streaming"), (256, 2, 5, "streaming"), (128, 8, 4, "streaming"),
+    (256, 12, 2, "streaming"),
+])
+def test_prescribed_molecules_match_oracle(B, nr, jmax, nmol, path):
     sp = W.Species(nr=nr, jmax=jmax, A=0.05)       # nearer resonance: visible P_e
     wl = W.custom("prescribed", 8, 8, 48, n_per_sim=nmol, species=[sp], layer=(20, 24),
                   seed=nr + jmax, nsteps=300)
     amp, wave = W.prescribed_drive(nmol, 300, wl.dt, E0=3e10, carrier_ev=6.0, fwhm=0.5e-15,
                                    t0=0.5e-15)
-    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED)
+    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED,
+                       mol_path=B.MS_MOL_FUSED if path == "fused" else B.MS_MOL_STREAMING)
     sim.set_prescribed(amp, wave)
     sim.step(300)
     P = sim.populations()
@@ -87,11 +92,12 @@ def test_prescribed_molecules_match_oracle(B, nr, jmax, nmol):
     assert np.abs(tot - 1).max() < 2e-5
 
 
-def test_coupled_small_matches_oracle(B):
+@pytest.mark.parametrize("path", ["fused", "streaming"])
+def test_coupled_small_matches_oracle(B, path):
     wl = W.custom("coupled small", 16, 16, 48, src_k=14, pulses=[[2e10, 1.5498, 2e-15, 2e-15]],
                   layer=(22, 26), n_per_sim=150, species=[W.species_config0(jmax=1)], seed=5,
                   nsteps=400)
-    sim = B.Simulation(wl)
+    sim = B.Simulation(wl, mol_path=B.MS_MOL_FUSED if path == "fused" else B.MS_MOL_STREAMING)
     sim.step(wl.nsteps)
     E = sim.fields(B.MS_FIELD_E)
     P = sim.populations()

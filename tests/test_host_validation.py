@@ -84,7 +84,7 @@ def test_invalid_descriptors_are_rejected(B, what):
         elif what == "species_nr":
             d.species[0].nr = 100
         elif what == "jmax":
-            d.species[0].jmax = 12
+            d.species[0].jmax = 20
         elif what == "position":
             p = np.array(np.ctypeslib.as_array(d.pos_m, shape=(3 * d.n_molecules,)))
             p[2] = 1.0
