@@ -346,7 +346,8 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
   const int cbuf = (rows + nd + 2 * (J + 1) + 1) * CH;
   float2* bC = bZ + rows * CH;
   int2* s_prog = reinterpret_cast<int2*>(bC + 2 * cbuf);  // [nrot][6] (nbr*CH, coupling) this step
-  int2* s_rinfo = s_prog + nrot * kMaxCoupl;             // [rows] (table row, m + J)
+  int2* s_dipp = s_prog + nrot * kMaxCoupl;              // [nrot][6] (nbr*CH, dipole coefficient)
+  int2* s_rinfo = s_dipp + nrot * kMaxCoupl;             // [rows] (table row, m + J)
   __shared__ __align__(8) unsigned long long s_bar[1];   // the state copy
   __shared__ float s_rot[9];                             // molecule -> lab rotation
   __shared__ double s_mu[3];                             // lab dipole of the previous step
@@ -369,17 +370,18 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
   // every thread copies 16-byte pieces (cp.async); rows: old state, then
   // the potential deltas, then the mask
   const float2* gd = FUSED ? nullptr : sp.d2 + (long long)lm * rows * NR;
+  const int cp_per_row = CH / 2;                   // 16-byte pieces per chunk row
+  const int cp_c2 = 2 * (t % cp_per_row), cp_q0 = t / cp_per_row, cp_qs = NT / cp_per_row;
   auto issue_chunk = [&](int r0, int b) {
     float2* buf = bC + b * cbuf;
-    const int nv = 2 * (J + 1), per_row = CH / 2, nunits = (rows + nd + nv + 1) * per_row;
-    for (int u = t; u < nunits; u += NT) {
-      const int q = u / per_row, c2 = 2 * (u - q * per_row);
+    const int nv = 2 * (J + 1), nq = rows + nd + nv + 1;
+    for (int q = cp_q0; q < nq; q += cp_qs) {
       const float2* src;
       if (q < rows) src = gs + (long long)q * NR;
       else if (q < rows + nd) src = gd + (long long)(q - rows) * NR;
       else if (q < rows + nd + nv) src = sp.vdelta + (long long)(q - rows - nd) * NR;
       else src = sp.maskw;
-      cp_async16(buf + q * CH + c2, src + r0 + c2);
+      cp_async16(buf + q * CH + cp_c2, src + r0 + cp_c2);
     }
     cp_async_commit();
   };
@@ -405,6 +407,11 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
   for (int q = t; q < rows; q += NT) {
     const int sf = q >= nrot, c = q - sf * nrot, j = j_of(c);
     s_rinfo[q] = make_int2((sf * (J + 1) + j) * CH, c - j * j - j + J);
+  }
+  for (int q = t; q < nrot * kMaxCoupl; q += NT) {  // dipole rows: slots 0-1 Z, 2-3 S+, 4-5 S-
+    const CouplEntry e = c_dip[q];
+    const bool ok = (unsigned)e.nbr < (unsigned)nrot;
+    s_dipp[q] = make_int2(ok ? e.nbr * CH : 0, __float_as_int(ok ? e.coef : 0.f));
   }
 
   // ---- local field, rotated into the molecule frame (a.u.)
@@ -586,13 +593,13 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
       for (int c = row0; c < nrot; c += rstep) {
         const float2 gc = bY[c * CH + rl];
         const float2* ee = bY + nrot * CH + rl;
+        const int2* pr = s_dipp + c * kMaxCoupl;
         float2 w3[3];
 #pragma unroll
-        for (int kk = 0; kk < 3; ++kk) {  // slots 0-1 Z, 2-3 S+, 4-5 S-
-          const CouplEntry q0 = c_dip[c * kMaxCoupl + 2 * kk], q1 = c_dip[c * kMaxCoupl + 2 * kk + 1];
-          const bool ok0 = (unsigned)q0.nbr < (unsigned)nrot, ok1 = (unsigned)q1.nbr < (unsigned)nrot;
-          const float c0 = ok0 ? q0.coef : 0.f, c1 = ok1 ? q1.coef : 0.f;
-          const float2 e0 = ee[ok0 ? q0.nbr * CH : 0], e1 = ee[ok1 ? q1.nbr * CH : 0];
+        for (int kk = 0; kk < 3; ++kk) {  // slots 0-1 Z, 2-3 S+, 4-5 S- (unused: zero coefficient)
+          const int2 q0 = pr[2 * kk], q1 = pr[2 * kk + 1];
+          const float c0 = __int_as_float(q0.y), c1 = __int_as_float(q1.y);
+          const float2 e0 = ee[q0.x], e1 = ee[q1.x];
           w3[kk] = make_float2(fmaf(c0, e0.x, c1 * e1.x), fmaf(c0, e0.y, c1 * e1.y));
         }
         // conj(gc) * w
@@ -781,7 +788,7 @@ static size_t step_smem(int nr, int nrot, int ch, bool fused) {
   return (fused ? 2 * (size_t)nr * sizeof(float2) + mol_state_smem(nr, rows) : 0) +
          2 * (size_t)rows * ch * sizeof(float2) +
          2 * (size_t)(rows + nd + 2 * (jm + 1) + 1) * ch * sizeof(float2) +
-         (size_t)nrot * kMaxCoupl * sizeof(int2) + (size_t)rows * sizeof(int2);
+         2 * (size_t)nrot * kMaxCoupl * sizeof(int2) + (size_t)rows * sizeof(int2);
 }
 
 // rows each thread owns at chunk width ch (8 warps; 32/ch row groups per warp)
