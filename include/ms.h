@@ -157,6 +157,28 @@ ms_status ms_create(const ms_grid_desc* grid, const ms_materials_desc* materials
  * E update (the paper's leap-frog with the molecular current). */
 ms_status ms_step(ms_sim* sim, int64_t n);
 
+/* Allocation-free stepping.  The paper has no counterpart: this is a library
+ * service.  It advances n steps exactly like ms_step, but species run in the
+ * streaming form (MS_MOL_STREAMING) take the scratch that holds (T - 1)s from
+ * a fixed 64 MiB device array compiled into the library instead of from the
+ * handle's buffer; the call itself allocates nothing (no cudaMalloc, no
+ * allocator callback, no library routine that allocates).  It is meant for
+ * callers that cannot allocate device memory at the point where they step:
+ * for instance, code that runs inside a fixed memory arena or under a
+ * budget that forbids new device allocations.
+ *   - Limit: every streaming species' scratch, n_molecules * 2 (jmax+1)^2 *
+ *     nr * 8 bytes, must fit in 64 MiB; otherwise MS_EINVAL is returned
+ *     before anything is launched.
+ *   - The array is shared by every call and every handle in the process, on
+ *     each device; it keeps the last call's contents, and each step rewrites
+ *     the part it reads before reading it.  Calls whose work overlaps on the
+ *     GPU (different streams or threads) race on it: serialise them.
+ *   - Every GPU that loads the library holds the 64 MiB until the process
+ *     exits.  The first call on a device looks the array's address up (with
+ *     that device current); make that first call before any stream capture.
+ * Errors as for ms_step. */
+ms_status ms_step_noalloc(ms_sim* sim, int64_t n);
+
 /* Number of steps taken so far. */
 int64_t ms_step_count(const ms_sim* sim);
 

@@ -71,6 +71,7 @@ def _load() -> C.CDLL:
         "ms_create": (C.c_int, [P(GridDesc), P(MaterialsDesc), P(MoleculesDesc), P(Options), P(C.c_void_p)]),
         "ms_step": (C.c_int, [C.c_void_p, C.c_int64]),
         "ms_step_count": (C.c_int64, [C.c_void_p]),
+        "ms_step_noalloc": (C.c_int, [C.c_void_p, C.c_int64]),
         "ms_read_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, P(C.c_float), C.c_size_t]),
         "ms_write_fields": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, P(C.c_float), C.c_size_t]),
         "ms_read_populations": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, P(C.c_double), P(C.c_double)]),
@@ -94,7 +95,7 @@ def _load() -> C.CDLL:
 LIB = _load()
 
 # every symbol include/ms.h declares
-EXPORTED = ("ms_create", "ms_step", "ms_step_count", "ms_read_fields", "ms_write_fields",
+EXPORTED = ("ms_create", "ms_step", "ms_step_noalloc", "ms_step_count", "ms_read_fields", "ms_write_fields",
             "ms_read_populations", "ms_read_dissociation", "ms_read_dipoles",
             "ms_set_prescribed_field", "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
             "ms_destroy", "ms_status_string")
@@ -202,6 +203,11 @@ class Simulation:
     # -- stepping ---------------------------------------------------------------
     def step(self, n: int = 1):
         _check(LIB.ms_step(self.h, int(n)), "ms_step")
+
+    def step_noalloc(self, n: int = 1):
+        """Same as step(), with the streaming scratch taken from the library's
+        fixed device array; allocates nothing."""
+        _check(LIB.ms_step_noalloc(self.h, int(n)), "ms_step_noalloc")
 
     @property
     def steps(self) -> int:

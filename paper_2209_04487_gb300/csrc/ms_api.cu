@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -595,6 +596,37 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
 
 }  // namespace
 
+// ---- allocation-free stepping --------------------------------------------
+// A fixed device array compiled into the library stands in for the per-
+// species (T - 1)s scratch of the streaming form.  Every GPU that loads the
+// library holds it until the process exits.  In host code `g_noalloc_scratch`
+// is only a stand-in symbol: its device address is looked up once per device
+// (with that device current) and passed to the kernels.
+namespace {
+constexpr size_t kNoAllocScratchBytes = 64ull << 20;  // 64 MiB
+static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocScratchBytes / sizeof(float2)];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+float2* g_noalloc_addr[kMaxDevices] = {};
+
+ms_status noalloc_scratch(float2** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MS_ECUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return MS_ECUDA;
+    }
+    g_noalloc_addr[dev] = static_cast<float2*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return MS_OK;
+}
+}  // namespace
+
 extern "C" {
 
 const char* ms_status_string(ms_status s) {
@@ -696,6 +728,39 @@ ms_status ms_step(ms_sim* s, int64_t n) {
       s->timed_steps++;
       s->launches += per_step;
     }
+  }
+  s->steps += n;
+  return cudaGetLastError() == cudaSuccess ? MS_OK : MS_ECUDA;
+}
+
+ms_status ms_step_noalloc(ms_sim* s, int64_t n) {
+  if (!s || n < 0) return MS_EINVAL;
+  if (s->drive == MS_DRIVE_PRESCRIBED && s->nmol > 0 && s->steps + n > s->nwave) return MS_EINVAL;
+  // every streaming species must fit the fixed scratch (checked before any launch)
+  for (int si = 0; si < s->nspecies; ++si) {
+    const ms::SpeciesDev& sp = s->sp[si];
+    if (sp.path == MS_MOL_STREAMING &&
+        (size_t)sp.nmol * 2 * sp.nrot * sp.nr * sizeof(float2) > kNoAllocScratchBytes)
+      return MS_EINVAL;
+  }
+  float2* scratch = nullptr;
+  MS_TRY(noalloc_scratch(&scratch));
+  const bool fdtd = s->drive == MS_DRIVE_FDTD;
+  for (int64_t q = 0; q < n; ++q) {
+    if (fdtd) {
+      ms::launch_yee_h(s->g, s->stream);
+      ms::launch_aux_h(s->g, s->stream);
+    }
+    for (int si = 0; si < s->nspecies; ++si) {
+      ms::SpeciesDev sp = s->sp[si];
+      if (sp.path == MS_MOL_STREAMING) sp.d2 = scratch;  // the whole scratch is rewritten before it is read
+      ms::launch_mol_step(sp, s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
+    }
+    if (fdtd) {
+      ms::launch_yee_e(s->g, s->stream);
+      ms::launch_aux_e(s->g, s->stream);
+    }
+    ms::launch_step_counter(s->d_step, s->stream);
   }
   s->steps += n;
   return cudaGetLastError() == cudaSuccess ? MS_OK : MS_ECUDA;
