@@ -22,7 +22,14 @@
 // instead of a drift.  The coupling is evaluated in the frame turned about
 // z that puts E' in the xz plane (a diagonal phase on the correction only),
 // where M is real.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cmath>
+#include <cstddef>
+#include <mutex>
+#include <type_traits>
+#include <vector>
 
 #include "ms_internal.cuh"
 
@@ -248,6 +255,15 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned by
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// 2-D tensor copy global -> shared (box of the map at element (x, y)).
+__device__ __forceinline__ void tensor2d_g2s(void* dst, const CUtensorMap* map, int x, int y,
+                                             unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
 // Wait for phase `parity` of the barrier, giving up after `limit` polls.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit) {
   for (long long it = 0; it < limit; ++it) {
@@ -298,6 +314,60 @@ cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip)
   cudaError_t e = cudaMemcpyToSymbol(c_rot, rot, sizeof(CouplEntry) * kMaxRot * kMaxCoupl);
   if (e != cudaSuccess) return e;
   return cudaMemcpyToSymbol(c_dip, dip, sizeof(CouplEntry) * kMaxRot * kMaxCoupl);
+}
+
+// Local field at molecule m in its own frame (a.u.): fld = (E_perp, E'_z), the
+// phases e^{i m' phi_E} (ph[m' + J], m' = -J..J) of the frame turned about z
+// so that E'_y = 0, and the number of coupling-series terms, until
+// (theta |E'|)^(n+1)/(n+1)! < 1e-10.  Run by one thread.
+__device__ __noinline__ void molecule_field(const MolDev& md, const Grid& g, int prescribed, int m, int J,
+                                            double theta, float* fld, float2* ph, int* nterms, int* err) {
+  float E[3];
+  const long long n = *g.step;
+  if (prescribed) {
+    const long long nn = n < md.nwave ? n : md.nwave - 1;
+    if (n >= md.nwave) atomicOr(err, kErrPrescribedRange);
+    const float wv = md.wave[nn];
+    E[0] = md.amp[3 * (long long)m] * wv;
+    E[1] = md.amp[3 * (long long)m + 1] * wv;
+    E[2] = md.amp[3 * (long long)m + 2] * wv;
+  } else {
+    const long long c = md.cell[m];
+    E[0] = g.E[0][c];
+    E[1] = g.E[1][c];
+    E[2] = g.E[2][c];
+  }
+  const float* O = md.rot + 9 * (long long)m;  // molecule -> lab, row-major
+  const float inv_fau = 1.0f / 5.14220674763e11f;
+  float Ep[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Ep[i] = (O[i] * E[0] + O[3 + i] * E[1] + O[6 + i] * E[2]) * inv_fau;
+  const float eperp = sqrtf(Ep[0] * Ep[0] + Ep[1] * Ep[1]);
+  fld[0] = eperp;
+  fld[1] = Ep[2];
+  // e^{i phi_E} = (E'_x + i E'_y)/E_perp; e^{i m phi_E} by repeated products
+  const float2 e1 = eperp > 0.f ? make_float2(Ep[0] / eperp, Ep[1] / eperp) : make_float2(1.f, 0.f);
+  float2 pw = make_float2(1.f, 0.f);
+  ph[J] = pw;
+  for (int q = 1; q <= J; ++q) {
+    pw = cmul(pw, e1);
+    ph[J + q] = pw;
+    ph[J - q] = make_float2(pw.x, -pw.y);
+  }
+  const float x = (float)theta * sqrtf(eperp * eperp + Ep[2] * Ep[2]);
+  int nt = 0;
+  if (x > 0.f) {
+    nt = 1;
+    float term = x;
+    while (nt < 24) {
+      const float next = term * x / (float)(nt + 1);
+      if (next < 1e-10f) break;
+      term = next;
+      ++nt;
+    }
+    if (nt >= 24 || x > 4.f) atomicOr(err, kErrCouplingSeries);
+  }
+  *nterms = nt;
 }
 
 constexpr int kChunk = 32;            // widest R-space chunk (one radial point per lane)
@@ -415,55 +485,7 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
   }
 
   // ---- local field, rotated into the molecule frame (a.u.)
-  if (t == 0) {
-    float E[3];
-    const long long n = *g.step;
-    if (prescribed) {
-      const long long nn = n < md.nwave ? n : md.nwave - 1;
-      if (n >= md.nwave) atomicOr(err, kErrPrescribedRange);
-      const float wv = md.wave[nn];
-      E[0] = md.amp[3 * (long long)m] * wv;
-      E[1] = md.amp[3 * (long long)m + 1] * wv;
-      E[2] = md.amp[3 * (long long)m + 2] * wv;
-    } else {
-      const long long c = md.cell[m];
-      E[0] = g.E[0][c];
-      E[1] = g.E[1][c];
-      E[2] = g.E[2][c];
-    }
-    const float* O = md.rot + 9 * (long long)m;  // molecule -> lab, row-major
-    const float inv_fau = 1.0f / 5.14220674763e11f;
-    float Ep[3];
-#pragma unroll
-    for (int i = 0; i < 3; ++i) Ep[i] = (O[i] * E[0] + O[3 + i] * E[1] + O[6 + i] * E[2]) * inv_fau;
-    const float eperp = sqrtf(Ep[0] * Ep[0] + Ep[1] * Ep[1]);
-    s_fld[0] = eperp;
-    s_fld[1] = Ep[2];
-    // e^{i phi_E} = (E'_x + i E'_y)/E_perp; e^{i m phi_E} by repeated products
-    const float2 e1 = eperp > 0.f ? make_float2(Ep[0] / eperp, Ep[1] / eperp) : make_float2(1.f, 0.f);
-    float2 pw = make_float2(1.f, 0.f);
-    s_ph[J] = pw;
-    for (int q = 1; q <= J; ++q) {
-      pw = cmul(pw, e1);
-      s_ph[J + q] = pw;
-      s_ph[J - q] = make_float2(pw.x, -pw.y);
-    }
-    // Taylor terms until (theta |E'|)^(n+1)/(n+1)! < 1e-10
-    const float x = (float)sp.theta * sqrtf(eperp * eperp + Ep[2] * Ep[2]);
-    int nt = 0;
-    if (x > 0.f) {
-      nt = 1;
-      float term = x;
-      while (nt < 24) {
-        const float next = term * x / (float)(nt + 1);
-        if (next < 1e-10f) break;
-        term = next;
-        ++nt;
-      }
-      if (nt >= 24 || x > 4.f) atomicOr(err, kErrCouplingSeries);
-    }
-    s_nterms = nt;
-  }
+  if (t == 0) molecule_field(md, g, prescribed, m, J, sp.theta, s_fld, s_ph, &s_nterms, err);
   __syncthreads();
   {  // this step's coupling rows: slots 0-1 Z (times E'_z), 2-5 X (times E_perp)
     const float eperp = s_fld[0], ez = s_fld[1];
@@ -658,6 +680,727 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
   }
 }
 
+
+// ----------------------------------------------------------------------------
+// R-space pass of the streaming form, one CTA per molecule, 32 radial points
+// per chunk (one per lane).  The rows (surface, channel) are spread over the
+// warps, RPW per warp: warp w owns rows w, w + NW, w + 2 NW, ...  The state s
+// and d2 = (T - 1) s of a chunk arrive by bulk copies (one 256-byte row
+// segment each) and stay in registers; the coupling series exchanges values
+// between rows through two term buffers in shared memory.
+//
+// Neighbour structure: the angular couplings of channel (j, m) reach the
+// channels (j + 1, m - 1 .. m + 1) and (j - 1, m - 1 .. m + 1), two runs of
+// three consecutive channels (c + 2j + 1 .. c + 2j + 3 and c - 2j - 1 ..
+// c - 2j + 1, c = j^2 + j + m).  A row therefore needs two base offsets and
+// six coefficients: for the coupling E_perp X + E'_z Z in the turned frame
+// (X = (S+ + S-)/2) and for the dipole (Z, S+, S-).  Coefficients of channels
+// outside the basis are zero and their reads land on finite data: kTriGuard
+// zero rows precede each buffer, and a missing run points at them.
+// ----------------------------------------------------------------------------
+// Per channel, on the two runs (j + 1, .) and (j - 1, .): .x S+ (from m - 1),
+// .y Z (from m), .z S- (from m + 1), .w 0.
+__device__ float4 g_tri_up[kMaxRot], g_tri_dn[kMaxRot];
+
+cudaError_t upload_triplet_tables(const CouplEntry* dip) {
+  // dipole slots: 0 Z (j-1, m), 1 Z (j+1, m), 2 S+ (j-1, m-1), 3 S+ (j+1, m-1), 4 S- (j+1, m+1), 5 S- (j-1, m+1)
+  std::vector<float4> up(kMaxRot, make_float4(0.f, 0.f, 0.f, 0.f)), dn = up;
+  for (int c = 0; c < kMaxRot; ++c) {
+    auto cf = [&](int slot) { const CouplEntry& e = dip[c * kMaxCoupl + slot]; return e.nbr >= 0 ? e.coef : 0.f; };
+    up[c] = make_float4(cf(3), cf(1), cf(4), 0.f);
+    dn[c] = make_float4(cf(2), cf(0), cf(5), 0.f);
+  }
+  cudaError_t e = cudaMemcpyToSymbol(g_tri_up, up.data(), sizeof(float4) * kMaxRot);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpyToSymbol(g_tri_dn, dn.data(), sizeof(float4) * kMaxRot);
+}
+
+constexpr int kTile = 32;     // radial points per chunk
+constexpr int kSeg = kTile * (int)sizeof(float2);  // bytes of one row segment
+constexpr int kTriGuard = 3;  // zero rows ahead of each term buffer
+
+// Tensor maps of one species for the R-space kernel: 8-byte elements (one
+// complex FP32 value), boxes of kTile radial points by all rows of a block.
+struct RspaceMaps {
+  CUtensorMap s, d2;  // [n_mol * rows][nr], box kTile x rows
+  CUtensorMap vd, vh; // [2 (J + 1)][nr], box kTile x 2 (J + 1)
+  CUtensorMap mk;     // [1][nr], box kTile x 1
+};
+
+struct RowT {
+  float4 cu, cd;  // theta x coupling on the runs (j + 1, .) and (j - 1, .)
+  float4 du, dd;  // dipole coefficients on the runs
+  float2 ph, pad; // e^{i m phi_E}
+};
+constexpr int kRtCu = (int)offsetof(RowT, cu), kRtCd = (int)offsetof(RowT, cd), kRtDu = (int)offsetof(RowT, du),
+              kRtDd = (int)offsetof(RowT, dd), kRtPh = (int)offsetof(RowT, ph);
+
+// Wait for phase `parity`, suspending up to 1 ms per try until it completes;
+// gives up after 2000 tries.
+__device__ __forceinline__ bool mbar_wait_sleep(unsigned long long* bar, unsigned parity) {
+  for (int it = 0; it < 2000; ++it) {
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(1000000)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+// Layout of the R-space kernel for basis size J: NW = 2 (J + 1) warps of
+// RPW = J + 1 rows cover the 2 (J + 1)^2 rows exactly (warp w owns rows
+// w + NW i), so every row index, buffer offset and stride is known at
+// compile time.  Shared memory, from a 128-byte aligned base:
+//   [2 ROWS] s and d2 of the chunk, [2][NV] e^{-iV dtau} - 1, [2][NV]
+//   e^{-iV dtau/2} (double buffered), [1] mask, two term buffers of
+//   kTriGuard + ROWS rows, the row table.
+template <int J>
+struct RsDims {
+  static constexpr int NROT = (J + 1) * (J + 1), ROWS = 2 * NROT, NV = 2 * (J + 1);
+  static constexpr int NW = 2 * (J + 1), RPW = J + 1, NT = 32 * NW;
+  static constexpr int TBB = (kTriGuard + ROWS) * kSeg;  // bytes of a term buffer
+  static constexpr int O_STG = 0, O_VD = O_STG + 2 * ROWS * kSeg, O_VH = O_VD + 2 * NV * kSeg;
+  static constexpr int O_MK = O_VH + 2 * NV * kSeg, O_TB = O_MK + kSeg, O_RT = O_TB + 2 * TBB;
+  static constexpr int BYTES = 128 + O_RT + ROWS * (int)sizeof(RowT);
+  static constexpr int MINB = J <= 4 ? 3 : 1;
+};
+
+template <int OFF>
+__device__ __forceinline__ float2 lds2(const unsigned char* base, int off) {
+  return *reinterpret_cast<const float2*>(base + off + OFF);
+}
+template <int OFF>
+__device__ __forceinline__ void sts2(unsigned char* base, int off, float2 v) {
+  *reinterpret_cast<float2*>(base + off + OFF) = v;
+}
+
+template <int J>
+__global__ void __launch_bounds__(RsDims<J>::NT, RsDims<J>::MINB)
+    mol_rspace_kernel(SpeciesDev sp, MolDev md, Grid g, int prescribed, int* err,
+                      const __grid_constant__ RspaceMaps maps) {
+  using D = RsDims<J>;
+  constexpr int NROT = D::NROT, ROWS = D::ROWS, NV = D::NV, NW = D::NW, RPW = D::RPW, NT = D::NT;
+  constexpr int TBB = D::TBB, G0 = kTriGuard * kSeg;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long s_bar[1];
+  __shared__ float s_rot[9];
+  __shared__ double s_mu[3], s_abs[2];
+  __shared__ float2 s_ph[2 * kMaxJ + 1];
+  __shared__ float s_fld[2];
+  __shared__ int s_nterms;
+  __shared__ float s_red[NW][9];
+  __shared__ float s_fin[7], s_fin_lo[2];
+
+  const int NR = sp.nr;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int pad = (int)((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+  unsigned char* const sm = smem_raw;
+  // this thread's byte offsets: own rows (w + NW i) at lane, and the row table
+  const int own = pad + w * kSeg + lane * 8;
+  const int rtw = pad + D::O_RT + w * (int)sizeof(RowT);
+  const int lm = blockIdx.x;
+  const int m = sp.mol[lm];
+  float2* gs = sp.psi + (long long)lm * ROWS * NR;
+  auto issue = [&](int ck) {
+    const int r0 = ck * kTile, b = ck & 1;
+    unsigned char* base = sm + pad;
+    tensor2d_g2s(base + D::O_STG, &maps.s, r0, lm * ROWS, &s_bar[0]);
+    tensor2d_g2s(base + D::O_STG + ROWS * kSeg, &maps.d2, r0, lm * ROWS, &s_bar[0]);
+    tensor2d_g2s(base + D::O_VD + b * NV * kSeg, &maps.vd, r0, 0, &s_bar[0]);
+    tensor2d_g2s(base + D::O_VH + b * NV * kSeg, &maps.vh, r0, 0, &s_bar[0]);
+    tensor2d_g2s(base + D::O_MK, &maps.mk, r0, 0, &s_bar[0]);
+  };
+  constexpr unsigned kChunkBytes = (2 * ROWS + 2 * NV + 1) * kSeg;
+
+  if (t == 0) {
+    mbar_init(&s_bar[0], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&s_bar[0], kChunkBytes);
+  }
+  for (int q = t; q < kTriGuard * kTile; q += NT) {
+    reinterpret_cast<float2*>(sm + pad + D::O_TB)[q] = make_float2(0.f, 0.f);
+    reinterpret_cast<float2*>(sm + pad + D::O_TB + TBB)[q] = make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  if (t == 0) {
+    issue(0);
+    molecule_field(md, g, prescribed, m, J, sp.theta, s_fld, s_ph, &s_nterms, err);
+  } else if (t >= 32 && t < 41) {
+    s_rot[t - 32] = md.rot[9 * (long long)m + (t - 32)];
+  } else if (t >= 41 && t < 44) {
+    s_mu[t - 41] = md.mu[3 * (long long)m + (t - 41)];
+  } else if (t >= 44 && t < 46) {
+    s_abs[t - 44] = md.absorbed[2 * (long long)m + (t - 44)];
+  }
+  // neighbour runs and potential row of this thread's rows (bytes from sm)
+  int ou[RPW], od[RPW], vo[RPW];
+#pragma unroll
+  for (int i = 0; i < RPW; ++i) {
+    const int q = w + NW * i;
+    const int sf = q >= NROT, c = q - sf * NROT, j = j_of(c);
+    const int other = kTriGuard + (1 - sf) * NROT;
+    ou[i] = pad + D::O_TB + lane * 8 + (j < J ? (other + c + 2 * j + 1) * kSeg : 0);
+    od[i] = pad + D::O_TB + lane * 8 + (j > 0 ? (other + c - 2 * j - 1) * kSeg : 0);
+    vo[i] = pad + lane * 8 + (sf * (J + 1) + j) * kSeg;
+  }
+  __syncthreads();
+  if (t < ROWS) {  // the row table of this step
+    const float th = (float)sp.theta, ep = 0.5f * s_fld[0] * th, ez = s_fld[1] * th;
+    const int q = t, sf = q >= NROT, c = q - sf * NROT, j = j_of(c), mm = c - j * j - j;
+    RowT r;
+    r.ph = s_ph[mm + J];
+    r.pad = make_float2(0.f, 0.f);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    r.du = j < J ? g_tri_up[c] : z4;
+    r.dd = j > 0 ? g_tri_dn[c] : z4;
+    r.cu = make_float4(ep * r.du.x, ez * r.du.y, ep * r.du.z, 0.f);
+    r.cd = make_float4(ep * r.dd.x, ez * r.dd.y, ep * r.dd.z, 0.f);
+    *reinterpret_cast<RowT*>(sm + pad + D::O_RT + q * (int)sizeof(RowT)) = r;
+  }
+  const int nterms = s_nterms;
+  const int nchunks = NR / kTile;  // even: NR is 64, 128 or 256
+  float2 sv[RPW], dv[RPW], sacc[RPW];
+  float p_hi[2] = {0.f, 0.f}, p_lo[2] = {0.f, 0.f};  // populations, compensated
+  float a_gf = 0.f, a_ef = 0.f, dP = 0.f, dQ = 0.f, dZ = 0.f;
+  // ground rows: q = w + NW i < NROT
+  auto ground = [&](int i) { return NW * i + NW <= NROT || (NW * i < NROT && w < NROT - NW * i); };
+
+  // one coupling-series term reading term buffer P (compile-time), writing
+  // the other one unless it is the last
+  auto term = [&](auto Pc, int n) {
+    constexpr int P = decltype(Pc)::value;
+    const float cn = 1.f / (float)n;
+    const bool store = n < nterms;
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+      const float4 cu = *reinterpret_cast<const float4*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtCu);
+      const float4 cd = *reinterpret_cast<const float4*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtCd);
+      const float2 u0 = lds2<P * TBB>(sm, ou[i]), u1 = lds2<P * TBB + kSeg>(sm, ou[i]),
+                   u2 = lds2<P * TBB + 2 * kSeg>(sm, ou[i]);
+      const float2 d0 = lds2<P * TBB>(sm, od[i]), d1 = lds2<P * TBB + kSeg>(sm, od[i]),
+                   d2 = lds2<P * TBB + 2 * kSeg>(sm, od[i]);
+      float ax = cu.x * u0.x, ay = cu.x * u0.y;
+      ax = fmaf(cu.y, u1.x, ax); ay = fmaf(cu.y, u1.y, ay);
+      ax = fmaf(cu.z, u2.x, ax); ay = fmaf(cu.z, u2.y, ay);
+      ax = fmaf(cd.x, d0.x, ax); ay = fmaf(cd.x, d0.y, ay);
+      ax = fmaf(cd.y, d1.x, ax); ay = fmaf(cd.y, d1.y, ay);
+      ax = fmaf(cd.z, d2.x, ax); ay = fmaf(cd.z, d2.y, ay);
+      const float2 o = make_float2(-cn * ay, cn * ax);  // i (theta/n) M in
+      sacc[i].x += o.x;
+      sacc[i].y += o.y;
+      if (store) sts2<(1 - P) * TBB + G0>(sm, own + D::O_TB + NW * i * kSeg, o);
+    }
+    if (store) __syncthreads();
+  };
+
+  // one chunk with the buffer parity B known at compile time; false on a timeout
+  auto chunk = [&](auto Bc, int ck) -> bool {
+    constexpr int B = decltype(Bc)::value;
+    constexpr int OVD = D::O_VD + B * NV * kSeg, OVH = D::O_VH + B * NV * kSeg;
+    const bool ok = mbar_wait_sleep(&s_bar[0], (unsigned)B);
+    if (!__syncthreads_and(ok)) {
+      if (t == 0) atomicOr(err, kErrTimeout);
+      if (!ok) mbar_wait_sleep(&s_bar[0], (unsigned)B);
+      return false;
+    }
+    const float mk = reinterpret_cast<const float2*>(sm + pad + D::O_MK)[lane].x;
+    // ---- s, d2; eta = e^{i m phi} V^{1/2} u into term buffer 0
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+      sv[i] = lds2<D::O_STG>(sm, own + NW * i * kSeg);
+      dv[i] = lds2<D::O_STG + ROWS * kSeg>(sm, own + NW * i * kSeg);
+      sacc[i] = make_float2(0.f, 0.f);
+      if (nterms > 0) {
+        const float2 vh = lds2<OVH>(sm, vo[i]);
+        const float2 ph = *reinterpret_cast<const float2*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtPh);
+        sts2<D::O_TB + G0>(sm, own + NW * i * kSeg, cmul(ph, cmul(vh, sv[i] + dv[i])));
+      }
+    }
+    __syncthreads();
+    if (t == 0 && ck + 1 < nchunks) {  // the staging buffer is free
+      mbar_expect_tx(&s_bar[0], kChunkBytes);
+      issue(ck + 1);
+    }
+    for (int n = 1; n <= nterms; n += 2) {
+      term(std::integral_constant<int, 0>(), n);
+      if (n + 1 <= nterms) term(std::integral_constant<int, 1>(), n + 1);
+    }
+    // ---- d1 = (V - 1) u + V^{1/2} e^{-i m phi} S ; mask ; s' = s + (d2 + d1)
+    const int sbo = (nterms & 1) * TBB;  // s' buffer: not read by the last term
+    float2* gsw = gs + (long long)w * NR + ck * kTile + lane;
+    float sg = 0.f, se = 0.f;
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+      const float2 u = sv[i] + dv[i];
+      const float2 vd = lds2<OVD>(sm, vo[i]);
+      float2 d1 = cmul(vd, u);
+      if (nterms > 0) {
+        const float2 vh = lds2<OVH>(sm, vo[i]);
+        const float2 ph = *reinterpret_cast<const float2*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtPh);
+        d1 = d1 + cmul(vh, cmul(make_float2(ph.x, -ph.y), sacc[i]));
+      }
+      const bool gr = ground(i);
+      if (mk < 1.f) {
+        const float px = u.x + d1.x, py = u.y + d1.y;
+        d1.x = fmaf(mk - 1.f, u.x, mk * d1.x);
+        d1.y = fmaf(mk - 1.f, u.y, mk * d1.y);
+        const float dd = (1.f - mk * mk) * fmaf(px, px, py * py);
+        if (gr) a_gf += dd; else a_ef += dd;
+      }
+      const float2 sn = sv[i] + (dv[i] + d1);
+      gsw[(long long)(NW * i) * NR] = sn;
+      sts2<D::O_TB + G0>(sm, own + sbo + NW * i * kSeg, sn);
+      sv[i] = sn;
+      const float b2 = fmaf(sn.x, sn.x, sn.y * sn.y);
+      if (gr) sg += b2; else se += b2;
+    }
+    acc2(p_hi[0], p_lo[0], sg);
+    acc2(p_hi[1], p_lo[1], se);
+    __syncthreads();
+    // ---- dipole in the molecule frame: sum_c conj(g_c) (A e)_c for A = Z, S+, S-
+    float2 accP = make_float2(0.f, 0.f), accM = accP, accZ = accP;
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+      if (ground(i)) {
+        const float2 gc = sv[i];
+        const float4 du = *reinterpret_cast<const float4*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtDu);
+        const float4 dd = *reinterpret_cast<const float4*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtDd);
+        const int a = ou[i] + sbo, c = od[i] + sbo;
+        const float2 u0 = lds2<0>(sm, a), u1 = lds2<kSeg>(sm, a), u2 = lds2<2 * kSeg>(sm, a);
+        const float2 e0 = lds2<0>(sm, c), e1 = lds2<kSeg>(sm, c), e2 = lds2<2 * kSeg>(sm, c);
+        const float2 wP = make_float2(fmaf(du.x, u0.x, dd.x * e0.x), fmaf(du.x, u0.y, dd.x * e0.y));
+        const float2 wZ = make_float2(fmaf(du.y, u1.x, dd.y * e1.x), fmaf(du.y, u1.y, dd.y * e1.y));
+        const float2 wM = make_float2(fmaf(du.z, u2.x, dd.z * e2.x), fmaf(du.z, u2.y, dd.z * e2.y));
+        accZ.x += fmaf(gc.x, wZ.x, gc.y * wZ.y);
+        accZ.y += fmaf(gc.x, wZ.y, -gc.y * wZ.x);
+        accP.x += fmaf(gc.x, wP.x, gc.y * wP.y);
+        accP.y += fmaf(gc.x, wP.y, -gc.y * wP.x);
+        accM.x += fmaf(gc.x, wM.x, gc.y * wM.y);
+        accM.y += fmaf(gc.x, wM.y, -gc.y * wM.x);
+      }
+    }
+    dP += accP.x + accM.x;
+    dQ += accP.y - accM.y;
+    dZ += 2.f * accZ.x;
+    return true;
+  };
+
+  for (int ck = 0; ck < nchunks; ck += 2) {
+    if (!chunk(std::integral_constant<int, 0>(), ck)) return;
+    if (!chunk(std::integral_constant<int, 1>(), ck + 1)) return;
+  }
+  // ---- block reduction: populations compensated, the rest plain FP32
+  {
+    float v[7] = {p_hi[0], p_hi[1], a_gf, a_ef, dP, dQ, dZ};
+    float lo[2] = {p_lo[0], p_lo[1]};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, v[k], o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo[k], o);
+        acc2(v[k], lo[k], h2);
+        lo[k] += l2;
+      }
+#pragma unroll
+      for (int k = 2; k < 7; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) s_red[w][k] = v[k];
+      s_red[w][7] = lo[0];
+      s_red[w][8] = lo[1];
+    }
+    __syncthreads();
+    if (t < 7) {
+      float hi = 0.f, l = 0.f;
+      for (int ww = 0; ww < NW; ++ww) {
+        acc2(hi, l, s_red[ww][t]);
+        if (t < 2) l += s_red[ww][7 + t];
+      }
+      s_fin[t] = hi + l;
+      if (t < 2) s_fin_lo[t] = l - (s_fin[t] - hi);
+    }
+    __syncthreads();
+    if (t < 3) {  // lab dipole: mu = O mu', mu' = d dR (Re(S+ + S-), Im(S+ - S-), 2 Re Z)
+      const float sc = (float)sp.dipole * sp.dR;
+      const float lab = sc * (s_rot[3 * t] * s_fin[4] + s_rot[3 * t + 1] * s_fin[5] + s_rot[3 * t + 2] * s_fin[6]);
+      const double nl = (double)lab;
+      md.dmu[3 * (long long)m + t] = nl - s_mu[t];
+      md.mu[3 * (long long)m + t] = nl;
+    } else if (t < 5) {
+      const double P = ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
+      md.pop[2 * (long long)m + (t - 3)] = P;
+      if (!isfinite(P)) atomicOr(err, kErrNonFinite);
+    } else if (t < 7) {
+      md.absorbed[2 * (long long)m + (t - 5)] = s_abs[t - 5] + (double)s_fin[t - 3] * (double)sp.dR;
+    }
+  }
+}
+
+
+// ----------------------------------------------------------------------------
+// R-space pass of the streaming form, point-resident layout (J <= 4): one CTA
+// per molecule, one thread per (radial point, surface).  A thread holds the
+// channel vector of its surface at its point in registers, so the angular
+// couplings become register arithmetic with indices fixed at compile time;
+// the coupling series (sigma_x swaps the surfaces) and the dipole only
+// exchange the other surface's vector, through one shared buffer.
+// ----------------------------------------------------------------------------
+template <int I, int N, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (I < N) {
+    f(std::integral_constant<int, I>());
+    static_for<I + 1, N>(f);
+  }
+}
+constexpr int ch_j(int c) { return c < 1 ? 0 : (c < 4 ? 1 : (c < 9 ? 2 : (c < 16 ? 3 : (c < 25 ? 4 : -1)))); }
+__host__ __device__ constexpr int j_of_c(int c) { return ch_j(c); }
+constexpr int ch_m(int c) { return c - ch_j(c) * ch_j(c) - ch_j(c); }
+// channel of (j, m), or -1 outside the basis of size J
+constexpr int ch_of(int j, int m, int J) { return (j < 0 || j > J || m < -j || m > j) ? -1 : j * j + j + m; }
+
+// ---- angular coefficients as compile-time constants ------------------------
+// square root by Newton's iteration in double precision (x >= 0)
+constexpr double c_sqrt(double x) {
+  if (x <= 0.0) return 0.0;
+  double r = x < 1.0 ? 1.0 : x;
+  for (int i = 0; i < 64; ++i) r = 0.5 * (r + x / r);
+  return r;
+}
+constexpr bool ch_valid(int j, int m) { return j >= 0 && m >= -j && m <= j; }
+// <j+1, m|cos t|j, m>, -<j+1, m+1|sin t e^{i p}|j, m> and <j-1, m+1|sin t e^{i p}|j, m>
+// in the Condon-Shortley phase convention
+constexpr double c_ang_a(int j, int m) {
+  return c_sqrt(((j + 1.0) * (j + 1) - (double)m * m) / ((2.0 * j + 1) * (2.0 * j + 3)));
+}
+constexpr double c_ang_b(int j, int m) {
+  return -c_sqrt((j + m + 1.0) * (j + m + 2) / ((2.0 * j + 1) * (2.0 * j + 3)));
+}
+constexpr double c_ang_c(int j, int m) {
+  return c_sqrt((j - m) * (j - m - 1.0) / ((2.0 * j - 1) * (2.0 * j + 1)));
+}
+// Row (j, m) of Z, S+ = sin t e^{ip} and S- = sin t e^{-ip} on the runs (j + 1, .) and (j - 1, .):
+// Z from (j +- 1, m), S+ from (j +- 1, m - 1), S- from (j +- 1, m + 1).
+constexpr float c_zu(int j, int m) { return (float)c_ang_a(j, m); }
+constexpr float c_zd(int j, int m) { return ch_valid(j - 1, m) ? (float)c_ang_a(j - 1, m) : 0.f; }
+constexpr float c_pu(int j, int m) { return ch_valid(j + 1, m - 1) ? (float)c_ang_c(j + 1, m - 1) : 0.f; }
+constexpr float c_pd(int j, int m) { return ch_valid(j - 1, m - 1) ? (float)c_ang_b(j - 1, m - 1) : 0.f; }
+constexpr float c_mu(int j, int m) { return (float)c_ang_b(j, m); }
+constexpr float c_md(int j, int m) { return j >= 1 ? (float)c_ang_c(j, m) : 0.f; }
+
+// Per molecule of a streaming species: the local field in the molecule frame
+// scaled by theta, (theta E'_z, theta E'_x / 2, theta E'_y / 2), and the
+// number of coupling-series terms, until (theta |E'|)^(n+1)/(n+1)! < 1e-10.
+__global__ void mol_field_kernel(SpeciesDev sp, MolDev md, Grid g, int prescribed, int* err) {
+  const int lm = blockIdx.x * blockDim.x + threadIdx.x;
+  if (lm >= sp.nmol) return;
+  const int m = sp.mol[lm];
+  float E[3];
+  const long long n = *g.step;
+  if (prescribed) {
+    const long long nn = n < md.nwave ? n : md.nwave - 1;
+    if (n >= md.nwave) atomicOr(err, kErrPrescribedRange);
+    const float wv = md.wave[nn];
+    E[0] = md.amp[3 * (long long)m] * wv;
+    E[1] = md.amp[3 * (long long)m + 1] * wv;
+    E[2] = md.amp[3 * (long long)m + 2] * wv;
+  } else {
+    const long long c = md.cell[m];
+    E[0] = g.E[0][c];
+    E[1] = g.E[1][c];
+    E[2] = g.E[2][c];
+  }
+  const float* O = md.rot + 9 * (long long)m;  // molecule -> lab, row-major
+  const float inv_fau = 1.0f / 5.14220674763e11f;
+  float Ep[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Ep[i] = (O[i] * E[0] + O[3 + i] * E[1] + O[6 + i] * E[2]) * inv_fau;
+  const float th = (float)sp.theta;
+  const float x = th * sqrtf(Ep[0] * Ep[0] + Ep[1] * Ep[1] + Ep[2] * Ep[2]);
+  int nt = 0;
+  if (x > 0.f) {
+    nt = 1;
+    float term = x;
+    while (nt < 24) {
+      const float next = term * x / (float)(nt + 1);
+      if (next < 1e-10f) break;
+      term = next;
+      ++nt;
+    }
+    if (nt >= 24 || x > 4.f) atomicOr(err, kErrCouplingSeries);
+  }
+  sp.fld[lm] = make_float4(th * Ep[2], 0.5f * th * Ep[0], 0.5f * th * Ep[1], __int_as_float(nt));
+}
+
+// i (theta/n) (M in)_c for channel c = (j, m) of a basis of size J, M = E'_z Z +
+// (E'_x - i E'_y)/2 S+ + (E'_x + i E'_y)/2 S- (the molecule-frame coupling);
+// f = (theta E'_z, theta E'_x/2, theta E'_y/2)
+template <int J, int C, class V>
+__device__ __forceinline__ float2 coupling_row(const V& in, float fz, float fx, float fy, float cn) {
+  constexpr int j = ch_j(C), mm = ch_m(C);
+  constexpr bool up = j < J;
+  float2 az = make_float2(0.f, 0.f), ap = az, am = az;
+  auto mac = [&](float2& a, float cf, auto ni) {
+    constexpr int q = decltype(ni)::value;
+    if constexpr (q >= 0) {
+      a.x = fmaf(cf, in[q].x, a.x);
+      a.y = fmaf(cf, in[q].y, a.y);
+    }
+  };
+  if constexpr (up) {
+    mac(az, c_zu(j, mm), std::integral_constant<int, ch_of(j + 1, mm, J)>());
+    mac(ap, c_pu(j, mm), std::integral_constant<int, ch_of(j + 1, mm - 1, J)>());
+    mac(am, c_mu(j, mm), std::integral_constant<int, ch_of(j + 1, mm + 1, J)>());
+  }
+  if constexpr (j > 0) {
+    mac(az, c_zd(j, mm), std::integral_constant<int, c_zd(j, mm) != 0.f ? ch_of(j - 1, mm, J) : -1>());
+    mac(ap, c_pd(j, mm), std::integral_constant<int, c_pd(j, mm) != 0.f ? ch_of(j - 1, mm - 1, J) : -1>());
+    mac(am, c_md(j, mm), std::integral_constant<int, c_md(j, mm) != 0.f ? ch_of(j - 1, mm + 1, J) : -1>());
+  }
+  // a = fz Z-part + fx (S+ + S-) - i fy (S+ - S-)
+  const float bx = ap.x + am.x, by = ap.y + am.y, cx = ap.x - am.x, cy = ap.y - am.y;
+  const float ax = fmaf(fz, az.x, fmaf(fx, bx, fy * cy));
+  const float ay = fmaf(fz, az.y, fmaf(fx, by, -fy * cx));
+  return make_float2(-cn * ay, cn * ax);
+}
+
+// Dipole sums over rows [C0, C1): sum_c conj(g_c) (A e)_c for A = S+, S-, Z
+// (g the ground vector, e the excited one at one radial point)
+template <int J, int C, class V>
+__device__ __forceinline__ void dipole_row(const V& gv, const V& ev, float2& accP, float2& accM, float2& accZ) {
+  constexpr int j = ch_j(C), mm = ch_m(C);
+  float2 wP = make_float2(0.f, 0.f), wZ = wP, wM = wP;
+  auto mac = [&](float2& a, float cf, auto ni) {
+    constexpr int q = decltype(ni)::value;
+    if constexpr (q >= 0) {
+      a.x = fmaf(cf, ev[q].x, a.x);
+      a.y = fmaf(cf, ev[q].y, a.y);
+    }
+  };
+  if constexpr (j < J) {
+    mac(wZ, c_zu(j, mm), std::integral_constant<int, ch_of(j + 1, mm, J)>());
+    mac(wP, c_pu(j, mm), std::integral_constant<int, ch_of(j + 1, mm - 1, J)>());
+    mac(wM, c_mu(j, mm), std::integral_constant<int, ch_of(j + 1, mm + 1, J)>());
+  }
+  if constexpr (j > 0) {
+    mac(wZ, c_zd(j, mm), std::integral_constant<int, c_zd(j, mm) != 0.f ? ch_of(j - 1, mm, J) : -1>());
+    mac(wP, c_pd(j, mm), std::integral_constant<int, c_pd(j, mm) != 0.f ? ch_of(j - 1, mm - 1, J) : -1>());
+    mac(wM, c_md(j, mm), std::integral_constant<int, c_md(j, mm) != 0.f ? ch_of(j - 1, mm + 1, J) : -1>());
+  }
+  const float2 gc = gv[C];
+  accZ.x += fmaf(gc.x, wZ.x, gc.y * wZ.y);
+  accZ.y += fmaf(gc.x, wZ.y, -gc.y * wZ.x);
+  accP.x += fmaf(gc.x, wP.x, gc.y * wP.y);
+  accP.y += fmaf(gc.x, wP.y, -gc.y * wP.x);
+  accM.x += fmaf(gc.x, wM.x, gc.y * wM.y);
+  accM.y += fmaf(gc.x, wM.y, -gc.y * wM.x);
+}
+template <int J, int C0, int C1, class V>
+__device__ __forceinline__ void dipole_rows(const V& gv, const V& ev, float2& accP, float2& accM, float2& accZ) {
+  if constexpr (C0 < C1) {
+    dipole_row<J, C0>(gv, ev, accP, accM, accZ);
+    dipole_rows<J, C0 + 1, C1>(gv, ev, accP, accM, accZ);
+  }
+}
+
+template <int J, int NR>
+__global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
+    mol_rpoint_kernel(SpeciesDev sp, MolDev md, int* err) {
+  constexpr int NROT = (J + 1) * (J + 1), NT = 2 * NR, NW = NT / 32;
+  extern __shared__ __align__(16) float4 smem4[];
+  float2* X = reinterpret_cast<float2*>(smem4);  // [2 NROT][NR] exchange buffer
+  __shared__ float s_rot[9];
+  __shared__ double s_mu[3], s_abs[2];
+  __shared__ float s_red[NW][9];
+  __shared__ float s_fin[7], s_fin_lo[2];
+
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int sf = t >= NR, p = t - sf * NR;  // surface (warp-uniform) and radial point
+  const int lm = blockIdx.x;
+  const int m = sp.mol[lm];
+  const long long row0 = ((long long)lm * 2 + sf) * NROT;  // first row of this surface
+  float2* gs = sp.psi + row0 * NR + p;
+  const float2* gd = sp.d2 + row0 * NR + p;
+  float2* Xo = X + sf * NROT * NR + p;              // own vector
+  const float2* Xt = X + (1 - sf) * NROT * NR + p;  // the other surface's
+  const float2* vdp = sp.vdelta + sf * (J + 1) * NR + p;
+  const float2* vhp = sp.vhalf + sf * (J + 1) * NR + p;
+
+  // the state and d2 of this point, requested first
+  float2 sa[NROT], da[NROT];
+#pragma unroll
+  for (int c = 0; c < NROT; ++c) {
+    sa[c] = gs[c * NR];
+    da[c] = __ldg(gd + c * NR);
+  }
+  if (t < 9) s_rot[t] = md.rot[9 * (long long)m + t];
+  else if (t >= 32 && t < 35) s_mu[t - 32] = md.mu[3 * (long long)m + (t - 32)];
+  else if (t >= 35 && t < 37) s_abs[t - 35] = md.absorbed[2 * (long long)m + (t - 35)];
+  const float4 f = __ldg(&sp.fld[lm]);
+  const int nterms = __float_as_int(f.w);
+  const float mk = sp.maskw[p].x;
+
+  // ---- eta = V^{1/2} u, u = s + d2, to the exchange buffer
+  if (nterms > 0) {
+    float2 vh[J + 1];
+#pragma unroll
+    for (int j = 0; j <= J; ++j) vh[j] = __ldg(vhp + j * NR);
+#pragma unroll
+    for (int c = 0; c < NROT; ++c) Xo[c * NR] = cmul(vh[j_of_c(c)], sa[c] + da[c]);
+  }
+  __syncthreads();
+  // ---- coupling series: S = sum_n (i theta M sigma_x)^n eta / n!
+  float2 sacc[NROT], in[NROT];
+#pragma unroll
+  for (int c = 0; c < NROT; ++c) sacc[c] = make_float2(0.f, 0.f);
+  for (int n = 1; n <= nterms; ++n) {
+#pragma unroll
+    for (int c = 0; c < NROT; ++c) in[c] = Xt[c * NR];
+    __syncthreads();  // every thread has its input: the buffer may be overwritten
+    const float cn = 1.f / (float)n;
+    const bool store = n < nterms;
+    static_for<0, NROT>([&](auto ci) {
+      constexpr int c = decltype(ci)::value;
+      const float2 o = coupling_row<J, c>(in, f.x, f.y, f.z, cn);
+      sacc[c].x += o.x;
+      sacc[c].y += o.y;
+      if (store) Xo[c * NR] = o;
+    });
+    if (store) __syncthreads();
+  }
+  // ---- d1 = (V - 1) u + V^{1/2} S ; mask ; s' = s + (d2 + d1)
+  float sn2 = 0.f, absd = 0.f;
+  {
+    float2 vh[J + 1], vd[J + 1];
+#pragma unroll
+    for (int j = 0; j <= J; ++j) {
+      vd[j] = __ldg(vdp + j * NR);
+      vh[j] = __ldg(vhp + j * NR);
+    }
+    // s and d2 again (from L2), in two batches each requested in full first
+    constexpr int NB = (NROT + 1) / 2;
+    float2 sb[NB], db[NB];
+    auto fetch = [&](int c0) {
+#pragma unroll
+      for (int k = 0; k < NB; ++k)
+        if (c0 + k < NROT) {
+          sb[k] = __ldcs(gs + (c0 + k) * NR);
+          db[k] = __ldcs(gd + (c0 + k) * NR);
+        }
+    };
+    fetch(0);
+#pragma unroll
+    for (int c = 0; c < NROT; ++c) {
+      if (c == NB) fetch(NB);
+      const int j = j_of_c(c);
+      const float2 sv = sb[c % NB], dv = db[c % NB];
+      const float2 u = sv + dv;
+      float2 d1 = cmul(vd[j], u);
+      if (nterms > 0) d1 = d1 + cmul(vh[j], sacc[c]);
+      if (mk < 1.f) {
+        const float px = u.x + d1.x, py = u.y + d1.y;
+        d1.x = fmaf(mk - 1.f, u.x, mk * d1.x);
+        d1.y = fmaf(mk - 1.f, u.y, mk * d1.y);
+        absd += (1.f - mk * mk) * fmaf(px, px, py * py);
+      }
+      const float2 s1 = sv + (dv + d1);
+      __stcs(gs + c * NR, s1);
+      sn2 += fmaf(s1.x, s1.x, s1.y * s1.y);
+      sacc[c] = s1;  // the new state of this surface, kept for the dipole
+      Xo[c * NR] = s1;
+    }
+  }
+  __syncthreads();
+  // ---- dipole in the molecule frame: sum_c conj(g_c) (A e)_c for A = Z, S+, S-;
+  // rows c < NH on the ground-surface threads, the rest on the excited ones
+  float dP = 0.f, dQ = 0.f, dZ = 0.f;
+  {
+    constexpr int NH = (NROT + 1) / 2;
+#pragma unroll
+    for (int c = 0; c < NROT; ++c) in[c] = Xt[c * NR];
+    float2 accP = make_float2(0.f, 0.f), accM = accP, accZ = accP;
+    if (sf == 0) dipole_rows<J, 0, NH>(sacc, in, accP, accM, accZ);
+    else dipole_rows<J, NH, NROT>(in, sacc, accP, accM, accZ);
+    dP = accP.x + accM.x;
+    dQ = accP.y - accM.y;
+    dZ = 2.f * accZ.x;
+  }
+  // ---- block reduction: populations compensated, the rest plain FP32
+  {
+    float v[7] = {sf ? 0.f : sn2, sf ? sn2 : 0.f, sf ? 0.f : absd, sf ? absd : 0.f, dP, dQ, dZ};
+    float lo[2] = {0.f, 0.f};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, v[k], o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, lo[k], o);
+        acc2(v[k], lo[k], h2);
+        lo[k] += l2;
+      }
+#pragma unroll
+      for (int k = 2; k < 7; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < 7; ++k) s_red[w][k] = v[k];
+      s_red[w][7] = lo[0];
+      s_red[w][8] = lo[1];
+    }
+    __syncthreads();
+    if (t < 7) {
+      float hi = 0.f, l = 0.f;
+      for (int ww = 0; ww < NW; ++ww) {
+        acc2(hi, l, s_red[ww][t]);
+        if (t < 2) l += s_red[ww][7 + t];
+      }
+      s_fin[t] = hi + l;
+      if (t < 2) s_fin_lo[t] = l - (s_fin[t] - hi);
+    }
+    __syncthreads();
+    if (t < 3) {  // lab dipole: mu = O mu', mu' = d dR (Re(S+ + S-), Im(S+ - S-), 2 Re Z)
+      const float sc = (float)sp.dipole * sp.dR;
+      const float lab = sc * (s_rot[3 * t] * s_fin[4] + s_rot[3 * t + 1] * s_fin[5] + s_rot[3 * t + 2] * s_fin[6]);
+      const double nl = (double)lab;
+      md.dmu[3 * (long long)m + t] = nl - s_mu[t];
+      md.mu[3 * (long long)m + t] = nl;
+    } else if (t < 5) {
+      const double P = ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
+      md.pop[2 * (long long)m + (t - 3)] = P;
+      if (!isfinite(P)) atomicOr(err, kErrNonFinite);
+    } else if (t < 7) {
+      md.absorbed[2 * (long long)m + (t - 5)] = s_abs[t - 5] + (double)s_fin[t - 3] * (double)sp.dR;
+    }
+  }
+}
+
+template <int J, int NR>
+static void launch_rpoint_jn(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                             cudaStream_t s) {
+  constexpr int NROT = (J + 1) * (J + 1);
+  const size_t smem = (size_t)2 * NROT * NR * sizeof(float2);
+  mol_field_kernel<<<(sp.nmol + 127) / 128, 128, 0, s>>>(sp, md, g, prescribed, err);
+  auto k = mol_rpoint_kernel<J, NR>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  k<<<sp.nmol, 2 * NR, smem, s>>>(sp, md, err);
+}
+
+template <int NR>
+static void launch_rpoint_n(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                            cudaStream_t s) {
+  switch (sp.jmax) {
+    case 0: launch_rpoint_jn<0, NR>(sp, md, g, prescribed, err, s); break;
+    case 1: launch_rpoint_jn<1, NR>(sp, md, g, prescribed, err, s); break;
+    case 2: launch_rpoint_jn<2, NR>(sp, md, g, prescribed, err, s); break;
+    case 3: launch_rpoint_jn<3, NR>(sp, md, g, prescribed, err, s); break;
+    case 4: launch_rpoint_jn<4, NR>(sp, md, g, prescribed, err, s); break;
+  }
+}
 }  // namespace ms
 
 // ----------------------------------------------------------------------------
@@ -828,6 +1571,96 @@ bool mol_step_supported(int nr, int nrot, int path) {
   return step_shape(nr, nrot, path == MS_MOL_FUSED).ok;
 }
 
+// The streaming R-space kernel covers J <= 7 (rows <= 128) on radial grids of
+// whole 32-point chunks.
+static bool rspace_ok(int nr, int jmax) { return nr % kTile == 0 && (nr / kTile) % 2 == 0 && jmax <= 7; }
+
+template <int J>
+static void launch_rspace_j(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                            const RspaceMaps& maps, cudaStream_t s) {
+  using D = RsDims<J>;
+  auto k = mol_rspace_kernel<J>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, D::BYTES);
+  cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  k<<<sp.nmol, D::NT, D::BYTES, s>>>(sp, md, g, prescribed, err, maps);
+}
+
+static void launch_rspace(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                          const RspaceMaps& maps, cudaStream_t s) {
+  switch (sp.jmax) {
+    case 0: launch_rspace_j<0>(sp, md, g, prescribed, err, maps, s); break;
+    case 1: launch_rspace_j<1>(sp, md, g, prescribed, err, maps, s); break;
+    case 2: launch_rspace_j<2>(sp, md, g, prescribed, err, maps, s); break;
+    case 3: launch_rspace_j<3>(sp, md, g, prescribed, err, maps, s); break;
+    case 4: launch_rspace_j<4>(sp, md, g, prescribed, err, maps, s); break;
+    case 5: launch_rspace_j<5>(sp, md, g, prescribed, err, maps, s); break;
+    case 6: launch_rspace_j<6>(sp, md, g, prescribed, err, maps, s); break;
+    case 7: launch_rspace_j<7>(sp, md, g, prescribed, err, maps, s); break;
+  }
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  });
+  return fn;
+}
+
+// [nrows][nr] array of complex FP32 values (8-byte elements), box kTile x box_rows
+static bool encode_rows(CUtensorMap* m, const void* base, unsigned long long nr, unsigned long long nrows,
+                        unsigned box_rows) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
+  if (!fn || !base) return false;
+  const cuuint64_t dims[2] = {nr, nrows};
+  const cuuint64_t strides[1] = {nr * sizeof(float2)};
+  const cuuint32_t box[2] = {(cuuint32_t)kTile, box_rows};
+  const cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, const_cast<void*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The species' tensor maps, encoded on first use of a given set of arrays
+// (a few entries are kept: each handle, and the allocation-free scratch).
+static bool rspace_maps(const SpeciesDev& sp, RspaceMaps* out) {
+  struct Entry {
+    const void *psi, *d2, *vd, *vh, *mk;
+    int nmol, nr, nrot;
+    RspaceMaps maps;
+  };
+  static std::mutex mu;
+  static std::vector<Entry> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  for (const Entry& e : cache)
+    if (e.psi == sp.psi && e.d2 == sp.d2 && e.vd == sp.vdelta && e.vh == sp.vhalf && e.mk == sp.maskw &&
+        e.nmol == sp.nmol && e.nr == sp.nr && e.nrot == sp.nrot) {
+      *out = e.maps;
+      return true;
+    }
+  Entry e{sp.psi, sp.d2, sp.vdelta, sp.vhalf, sp.maskw, sp.nmol, sp.nr, sp.nrot, {}};
+  const unsigned rows = 2 * sp.nrot, nv = 2 * (sp.jmax + 1);
+  const unsigned long long nr = sp.nr;
+  if (!encode_rows(&e.maps.s, sp.psi, nr, (unsigned long long)sp.nmol * rows, rows) ||
+      !encode_rows(&e.maps.d2, sp.d2, nr, (unsigned long long)sp.nmol * rows, rows) ||
+      !encode_rows(&e.maps.vd, sp.vdelta, nr, nv, nv) || !encode_rows(&e.maps.vh, sp.vhalf, nr, nv, nv) ||
+      !encode_rows(&e.maps.mk, sp.maskw, nr, 1, 1))
+    return false;
+  if (cache.size() >= 32) cache.erase(cache.begin());
+  cache.push_back(e);
+  *out = e.maps;
+  return true;
+}
+
 // rows per kinetic block: 32 KB of state
 static int kinetic_rows(int nr) { return 4096 / nr; }
 
@@ -854,6 +1687,15 @@ static void launch_step_t(const SpeciesDev& sp, const MolDev& md, const Grid& g,
   cudaFuncSetAttribute(mol_kinetic_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem);
   mol_kinetic_kernel<NR><<<(unsigned)((rows_total + RB - 1) / RB), FFTShape<NR>::THREADS, ksmem, s>>>(
       sp, rows_total, RB, err);
+  if (sp.jmax <= 4) {  // point-resident R-space pass
+    launch_rpoint_n<NR>(sp, md, g, prescribed, err, s);
+    return;
+  }
+  RspaceMaps maps;
+  if (rspace_ok(NR, sp.jmax) && rspace_maps(sp, &maps)) {
+    launch_rspace(sp, md, g, prescribed, err, maps, s);
+    return;
+  }
   if (sh.maxr == 4) launch_step_tt<NR, false, 4>(sp, md, g, prescribed, err, sh, s);
   else if (sh.maxr == 12) launch_step_tt<NR, false, 12>(sp, md, g, prescribed, err, sh, s);
   else launch_step_tt<NR, false, 24>(sp, md, g, prescribed, err, sh, s);

@@ -238,7 +238,8 @@ ms_status upload_angular_tables() {
       put(dip, 4, j + 1, m + 1, q0);
       put(dip, 5, j - 1, m + 1, q1);
     }
-  return ms::upload_coupling_tables(rot.data(), dip.data()) == cudaSuccess ? MS_OK : MS_ECUDA;
+  if (ms::upload_coupling_tables(rot.data(), dip.data()) != cudaSuccess) return MS_ECUDA;
+  return ms::upload_triplet_tables(dip.data()) == cudaSuccess ? MS_OK : MS_ECUDA;
 }
 
 ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const std::vector<int>& ids,
@@ -322,7 +323,11 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   for (int a = 0; a < nr; ++a) row0[a] = make_float2((float)phi0[a].real(), (float)phi0[a].imag());
   MS_TRY(zeros(s, &sp.psi, per * ids.size()));
   sp.d2 = nullptr;
-  if (sp.path == MS_MOL_STREAMING) MS_TRY(zeros(s, &sp.d2, per * ids.size()));
+  sp.fld = nullptr;
+  if (sp.path == MS_MOL_STREAMING) {
+    MS_TRY(zeros(s, &sp.d2, per * ids.size()));
+    MS_TRY(zeros(s, &sp.fld, ids.size()));
+  }
   float2* d_row0 = nullptr;
   MS_TRY(upload(s, &d_row0, row0.data(), row0.size()));
   if (ms::launch_broadcast_row(sp.psi, d_row0, nr, per, (long long)ids.size(), s->stream) != cudaSuccess)

@@ -81,6 +81,7 @@ struct SpeciesDev {
   const int* mol;           // their global ids (sorted by species, then by id)
   float2* psi;              // state [nmol][2][nrot][nr], s = T^{-1/2} psi
   float2* d2;               // streaming form: scratch (T - 1) s, same layout
+  float4* fld;              // streaming form: per molecule (theta E'_z, theta E'_x/2, theta E'_y/2, terms)
   int path;                 // MS_MOL_FUSED or MS_MOL_STREAMING
   // per (s, j, r): e^{-i V dtau} - 1 and e^{-i V dtau/2}
   const float2* vdelta;     // [2][jmax+1][nr]
@@ -132,6 +133,7 @@ void launch_mol_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int 
 void launch_mol_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s);
 bool mol_step_supported(int nr, int nrot, int path);
 cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip);
+cudaError_t upload_triplet_tables(const CouplEntry* dip);
 void launch_step_counter(long long* step, cudaStream_t s);
 cudaError_t launch_broadcast_row(float2* psi, const float2* row, int nr, size_t per, long long nmol,
                                  cudaStream_t s);
