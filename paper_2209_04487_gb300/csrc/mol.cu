@@ -1211,8 +1211,11 @@ template <int J, int NR>
 __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
     mol_rpoint_kernel(SpeciesDev sp, MolDev md, int* err) {
   constexpr int NROT = (J + 1) * (J + 1), NT = 2 * NR, NW = NT / 32;
+  constexpr unsigned kStateBytes = 2u * NROT * NR * sizeof(float2);  // one molecule's state
   extern __shared__ __align__(16) float4 smem4[];
-  float2* X = reinterpret_cast<float2*>(smem4);  // [2 NROT][NR] exchange buffer
+  float2* X = reinterpret_cast<float2*>(smem4);  // [2 NROT][NR]: s, then eta and the series terms, then s'
+  float2* D = X + 2 * NROT * NR;                 // [2 NROT][NR]: d2
+  __shared__ __align__(8) unsigned long long s_bar[1];
   __shared__ float s_rot[9];
   __shared__ double s_mu[3], s_abs[2];
   __shared__ float s_red[NW][9];
@@ -1222,35 +1225,47 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
   const int sf = t >= NR, p = t - sf * NR;  // surface (warp-uniform) and radial point
   const int lm = blockIdx.x;
   const int m = sp.mol[lm];
-  const long long row0 = ((long long)lm * 2 + sf) * NROT;  // first row of this surface
-  float2* gs = sp.psi + row0 * NR + p;
-  const float2* gd = sp.d2 + row0 * NR + p;
+  const long long mol0 = (long long)lm * 2 * NROT * NR;  // first element of this molecule
+  float2* gs = sp.psi + mol0 + sf * NROT * NR + p;
   float2* Xo = X + sf * NROT * NR + p;              // own vector
   const float2* Xt = X + (1 - sf) * NROT * NR + p;  // the other surface's
+  const float2* Do = D + sf * NROT * NR + p;
   const float2* vdp = sp.vdelta + sf * (J + 1) * NR + p;
   const float2* vhp = sp.vhalf + sf * (J + 1) * NR + p;
 
-  // the state and d2 of this point, requested first
-  float2 sa[NROT], da[NROT];
-#pragma unroll
-  for (int c = 0; c < NROT; ++c) {
-    sa[c] = gs[c * NR];
-    da[c] = __ldg(gd + c * NR);
+  // the molecule's state and d2, one bulk copy each (contiguous in global memory)
+  if (t == 0) {
+    mbar_init(&s_bar[0], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&s_bar[0], 2 * kStateBytes);
+    bulk_g2s(X, sp.psi + mol0, kStateBytes, &s_bar[0]);
+    bulk_g2s(D, sp.d2 + mol0, kStateBytes, &s_bar[0]);
   }
-  if (t < 9) s_rot[t] = md.rot[9 * (long long)m + t];
-  else if (t >= 32 && t < 35) s_mu[t - 32] = md.mu[3 * (long long)m + (t - 32)];
-  else if (t >= 35 && t < 37) s_abs[t - 35] = md.absorbed[2 * (long long)m + (t - 35)];
+  if (t >= 32 && t < 41) s_rot[t - 32] = md.rot[9 * (long long)m + (t - 32)];
+  else if (t >= 64 && t < 67) s_mu[t - 64] = md.mu[3 * (long long)m + (t - 64)];
+  else if (t >= 67 && t < 69) s_abs[t - 67] = md.absorbed[2 * (long long)m + (t - 67)];
   const float4 f = __ldg(&sp.fld[lm]);
   const int nterms = __float_as_int(f.w);
   const float mk = sp.maskw[p].x;
-
-  // ---- eta = V^{1/2} u, u = s + d2, to the exchange buffer
+  float2 vh[J + 1], vd[J + 1];
+#pragma unroll
+  for (int j = 0; j <= J; ++j) {
+    vd[j] = __ldg(vdp + j * NR);
+    vh[j] = __ldg(vhp + j * NR);
+  }
+  __syncthreads();  // the barrier is initialised
+  {
+    const bool ok = mbar_wait_sleep(&s_bar[0], 0);
+    if (!__syncthreads_and(ok)) {
+      if (t == 0) atomicOr(err, kErrTimeout);
+      if (!ok) mbar_wait_sleep(&s_bar[0], 0);
+      return;
+    }
+  }
+  // ---- eta = V^{1/2} u, u = s + d2, over this thread's own rows of the state
   if (nterms > 0) {
-    float2 vh[J + 1];
 #pragma unroll
-    for (int j = 0; j <= J; ++j) vh[j] = __ldg(vhp + j * NR);
-#pragma unroll
-    for (int c = 0; c < NROT; ++c) Xo[c * NR] = cmul(vh[j_of_c(c)], sa[c] + da[c]);
+    for (int c = 0; c < NROT; ++c) Xo[c * NR] = cmul(vh[j_of_c(c)], Xo[c * NR] + Do[c * NR]);
   }
   __syncthreads();
   // ---- coupling series: S = sum_n (i theta M sigma_x)^n eta / n!
@@ -1275,29 +1290,20 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
   // ---- d1 = (V - 1) u + V^{1/2} S ; mask ; s' = s + (d2 + d1)
   float sn2 = 0.f, absd = 0.f;
   {
-    float2 vh[J + 1], vd[J + 1];
-#pragma unroll
-    for (int j = 0; j <= J; ++j) {
-      vd[j] = __ldg(vdp + j * NR);
-      vh[j] = __ldg(vhp + j * NR);
-    }
-    // s and d2 again (from L2), in two batches each requested in full first
+    // s again (from L2), in two batches each requested in full first; d2 from shared memory
     constexpr int NB = (NROT + 1) / 2;
-    float2 sb[NB], db[NB];
+    float2 sb[NB];
     auto fetch = [&](int c0) {
 #pragma unroll
       for (int k = 0; k < NB; ++k)
-        if (c0 + k < NROT) {
-          sb[k] = __ldcs(gs + (c0 + k) * NR);
-          db[k] = __ldcs(gd + (c0 + k) * NR);
-        }
+        if (c0 + k < NROT) sb[k] = __ldcs(gs + (c0 + k) * NR);
     };
     fetch(0);
 #pragma unroll
     for (int c = 0; c < NROT; ++c) {
       if (c == NB) fetch(NB);
       const int j = j_of_c(c);
-      const float2 sv = sb[c % NB], dv = db[c % NB];
+      const float2 sv = sb[c % NB], dv = Do[c * NR];
       const float2 u = sv + dv;
       float2 d1 = cmul(vd[j], u);
       if (nterms > 0) d1 = d1 + cmul(vh[j], sacc[c]);
@@ -1382,7 +1388,7 @@ template <int J, int NR>
 static void launch_rpoint_jn(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
                              cudaStream_t s) {
   constexpr int NROT = (J + 1) * (J + 1);
-  const size_t smem = (size_t)2 * NROT * NR * sizeof(float2);
+  const size_t smem = (size_t)4 * NROT * NR * sizeof(float2);
   mol_field_kernel<<<(sp.nmol + 127) / 128, 128, 0, s>>>(sp, md, g, prescribed, err);
   auto k = mol_rpoint_kernel<J, NR>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
