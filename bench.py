@@ -252,15 +252,35 @@ def main():
     value = world * wl.n_molecules * a.steps / sec
     cells_rate = world * wl.cells * a.steps / sec
     sp = wl.species[0]
-    mol_bytes = 2 * 2 * sp.nrot * sp.nr * 8 + 12 + 80   # state read+write + field + records
-    bytes_launch = mol_bytes * wl.n_molecules
-    mol_ms = phases[1] / max(nsteps, 1)
-    achieved = bytes_launch / (mol_ms / 1e3) / 1e9
+    state = 16 * sp.nr * sp.nrot                       # FP32 state of one molecule (bytes)
+    per_step = lambda k: phases[k] / max(nsteps, 1)    # ms per step of one timed phase
     peak, peak_src = _peaks()
-    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": _kernel_traffic("mol_step_kernel"), "kernel": f"mol_step_kernel<{sp.nr}>",
-            "bytes_per_launch": bytes_launch, "peak_source": peak_src,
-            "note": "algorithmic bytes = FP32 wavepacket state read + written once per molecule-step"}
+    # dominant kernel: the R-space pass (stage 2), one launch per step; its own
+    # minimum traffic in the streaming form is s and d2 read, s' written, plus
+    # the per-molecule records (field 16 B, rotation 36 B, dipole 3x8 read +
+    # 2x3x8 written, populations 16, absorbed norm 2x16)
+    rs_bytes = (3 * state + 168) * wl.n_molecules
+    rs_ms = per_step(5)
+    kernel = f"mol_rpoint_kernel<{sp.jmax},{sp.nr}>" if sp.jmax <= 4 else f"R-space pass <{sp.nr}>"
+    roof = {"bound": "hbm", "achieved": rs_bytes / (rs_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": rs_bytes / (rs_ms / 1e3) / 1e9 / peak,
+            "traffic": _kernel_traffic("mol_rpoint_kernel"), "kernel": kernel,
+            "bytes_per_launch": rs_bytes, "ms_per_launch": rs_ms, "peak_source": peak_src,
+            "note": "algorithmic bytes of the R-space kernel: state and d2 read, new state written, "
+                    "168 B of per-molecule records"}
+    # the kinetic pass (stage 1: field records + kinetic kernel): s read, d2 written
+    kin_bytes = (2 * state + 16) * wl.n_molecules
+    kin_ms = per_step(4)
+    roof_kin = {"bound": "hbm", "achieved": kin_bytes / (kin_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                "frac": kin_bytes / (kin_ms / 1e3) / 1e9 / peak, "kernel": f"mol_kinetic_kernel<{sp.nr}>",
+                "bytes_per_launch": kin_bytes, "ms_per_launch": kin_ms}
+    # the whole molecular step against the method's minimum: the state read
+    # and written once per step plus about 40 B of field and observables
+    step_bytes = (2 * state + 40) * wl.n_molecules
+    roof_step = {"bound": "hbm", "achieved": step_bytes / (per_step(1) / 1e3) / 1e9, "peak": peak,
+                 "unit": "GB/s", "frac": step_bytes / (per_step(1) / 1e3) / 1e9 / peak,
+                 "bytes_per_step": step_bytes, "ms_per_step": per_step(1),
+                 "note": "molecular step (all its kernels) vs one read and one write of the FP32 state"}
 
     e2e = None
     if not a.no_e2e:
@@ -292,8 +312,10 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": _config(wl), "cell_updates_per_s": cells_rate,
                 "phases_ms_per_step": {"h": phases[0] / nsteps, "molecules": phases[1] / nsteps,
-                                       "e": phases[2] / nsteps},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
+                                       "e": phases[2] / nsteps, "molecules_stage1": phases[4] / nsteps,
+                                       "molecules_stage2": phases[5] / nsteps},
+                "roofline": roof, "roofline_kinetic": roof_kin, "roofline_molecular_step": roof_step,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
                 "clocks": cl, "norm_bookkeeping_max_err": norm_err,
                 "forms": {"plain_fp32": value, "mixed_bf16x3": None}}
         print(json.dumps(line), flush=True)

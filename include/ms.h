@@ -218,13 +218,16 @@ ms_status ms_set_prescribed_field(ms_sim* sim, const float* amp, const float* wa
 
 /* Phase timing with CUDA events on the handle's stream.  Between
  * ms_timing_begin and ms_timing_end every ms_step records events around its
- * three phases; ms_timing_end synchronises and writes the summed durations
- * in milliseconds: out[0] H half step (H update and incident line),
- * out[1] molecular step (all species), out[2] E half step (E update,
- * incident line, step counter), out[3] their sum; *steps receives the
- * number of steps timed and *launches the number of kernels launched. */
+ * phases; ms_timing_end synchronises and writes the summed durations in
+ * milliseconds: out[0] H half step (H update and incident line), out[1]
+ * molecular step (all species), out[2] E half step (E update, incident
+ * line, step counter), out[3] their sum, out[4] the molecular step's first
+ * stage (streaming form: field records and kinetic pass), out[5] its second
+ * stage (streaming form: R-space pass; fused form: the whole step); *steps
+ * receives the number of steps timed and *launches the number of kernels
+ * launched. */
 ms_status ms_timing_begin(ms_sim* sim);
-ms_status ms_timing_end(ms_sim* sim, double out[4], int64_t* steps, int64_t* launches);
+ms_status ms_timing_end(ms_sim* sim, double out[6], int64_t* steps, int64_t* launches);
 
 /* Device memory held by the simulation, in bytes. */
 size_t ms_device_bytes(const ms_sim* sim);

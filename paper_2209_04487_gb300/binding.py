@@ -255,8 +255,9 @@ class Simulation:
         _check(LIB.ms_timing_begin(self.h), "ms_timing_begin")
 
     def timing_end(self):
-        """(ms per phase [H, molecules, E, total], steps timed, kernels launched)"""
-        out = (C.c_double * 4)()
+        """(ms per phase [H, molecules, E, total, molecule stage 1, molecule stage 2],
+        steps timed, kernels launched)"""
+        out = (C.c_double * 6)()
         st = C.c_int64()
         ln = C.c_int64()
         _check(LIB.ms_timing_end(self.h, out, C.byref(st), C.byref(ln)), "ms_timing_end")

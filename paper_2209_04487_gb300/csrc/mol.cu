@@ -1385,11 +1385,9 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
 }
 
 template <int J, int NR>
-static void launch_rpoint_jn(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
-                             cudaStream_t s) {
+static void launch_rpoint_jn(const SpeciesDev& sp, const MolDev& md, int* err, cudaStream_t s) {
   constexpr int NROT = (J + 1) * (J + 1);
   const size_t smem = (size_t)4 * NROT * NR * sizeof(float2);
-  mol_field_kernel<<<(sp.nmol + 127) / 128, 128, 0, s>>>(sp, md, g, prescribed, err);
   auto k = mol_rpoint_kernel<J, NR>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -1397,14 +1395,13 @@ static void launch_rpoint_jn(const SpeciesDev& sp, const MolDev& md, const Grid&
 }
 
 template <int NR>
-static void launch_rpoint_n(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
-                            cudaStream_t s) {
+static void launch_rpoint_n(const SpeciesDev& sp, const MolDev& md, int* err, cudaStream_t s) {
   switch (sp.jmax) {
-    case 0: launch_rpoint_jn<0, NR>(sp, md, g, prescribed, err, s); break;
-    case 1: launch_rpoint_jn<1, NR>(sp, md, g, prescribed, err, s); break;
-    case 2: launch_rpoint_jn<2, NR>(sp, md, g, prescribed, err, s); break;
-    case 3: launch_rpoint_jn<3, NR>(sp, md, g, prescribed, err, s); break;
-    case 4: launch_rpoint_jn<4, NR>(sp, md, g, prescribed, err, s); break;
+    case 0: launch_rpoint_jn<0, NR>(sp, md, err, s); break;
+    case 1: launch_rpoint_jn<1, NR>(sp, md, err, s); break;
+    case 2: launch_rpoint_jn<2, NR>(sp, md, err, s); break;
+    case 3: launch_rpoint_jn<3, NR>(sp, md, err, s); break;
+    case 4: launch_rpoint_jn<4, NR>(sp, md, err, s); break;
   }
 }
 }  // namespace ms
@@ -1678,14 +1675,18 @@ static void launch_step_tt(const SpeciesDev& sp, const MolDev& md, const Grid& g
   k<<<sp.nmol, FFTShape<NR>::THREADS, sh.smem, s>>>(sp, md, g, prescribed, sh.ch, err);
 }
 
+// Stage 1 of a species' step: in the streaming form the per-molecule field
+// records (point-resident R-space kernel only) and the kinetic pass d2 = (T - 1) s.
+// Stage 2: the R-space pass (streaming form) or the whole fused step.
+// Each returns the number of kernels it launched.
 template <int NR>
-static void launch_step_t(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed,
-                          int* err, cudaStream_t s) {
-  const bool fused = sp.path == MS_MOL_FUSED;
-  const StepShape sh = step_shape(NR, sp.nrot, fused);
-  if (fused) {
-    launch_step_tt<NR, true, 12>(sp, md, g, prescribed, err, sh, s);
-    return;
+static int launch_stage1_t(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                           cudaStream_t s) {
+  if (sp.path == MS_MOL_FUSED) return 0;
+  int n = 0;
+  if (sp.jmax <= 4) {
+    mol_field_kernel<<<(sp.nmol + 127) / 128, 128, 0, s>>>(sp, md, g, prescribed, err);
+    ++n;
   }
   const long long rows_total = (long long)sp.nmol * 2 * sp.nrot;
   const int RB = kinetic_rows(NR);
@@ -1693,28 +1694,53 @@ static void launch_step_t(const SpeciesDev& sp, const MolDev& md, const Grid& g,
   cudaFuncSetAttribute(mol_kinetic_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem);
   mol_kinetic_kernel<NR><<<(unsigned)((rows_total + RB - 1) / RB), FFTShape<NR>::THREADS, ksmem, s>>>(
       sp, rows_total, RB, err);
+  return n + 1;
+}
+
+template <int NR>
+static int launch_stage2_t(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                           cudaStream_t s) {
+  const bool fused = sp.path == MS_MOL_FUSED;
+  const StepShape sh = step_shape(NR, sp.nrot, fused);
+  if (fused) {
+    launch_step_tt<NR, true, 12>(sp, md, g, prescribed, err, sh, s);
+    return 1;
+  }
   if (sp.jmax <= 4) {  // point-resident R-space pass
-    launch_rpoint_n<NR>(sp, md, g, prescribed, err, s);
-    return;
+    launch_rpoint_n<NR>(sp, md, err, s);
+    return 1;
   }
   RspaceMaps maps;
   if (rspace_ok(NR, sp.jmax) && rspace_maps(sp, &maps)) {
     launch_rspace(sp, md, g, prescribed, err, maps, s);
-    return;
+    return 1;
   }
   if (sh.maxr == 4) launch_step_tt<NR, false, 4>(sp, md, g, prescribed, err, sh, s);
   else if (sh.maxr == 12) launch_step_tt<NR, false, 12>(sp, md, g, prescribed, err, sh, s);
   else launch_step_tt<NR, false, 24>(sp, md, g, prescribed, err, sh, s);
+  return 1;
 }
 
-void launch_mol_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
-                     cudaStream_t s) {
-  if (sp.nmol == 0) return;
+int launch_mol_stage1(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                      cudaStream_t s) {
+  if (sp.nmol == 0) return 0;
   switch (sp.nr) {
-    case 64: launch_step_t<64>(sp, md, g, prescribed, err, s); break;
-    case 128: launch_step_t<128>(sp, md, g, prescribed, err, s); break;
-    case 256: launch_step_t<256>(sp, md, g, prescribed, err, s); break;
+    case 64: return launch_stage1_t<64>(sp, md, g, prescribed, err, s);
+    case 128: return launch_stage1_t<128>(sp, md, g, prescribed, err, s);
+    case 256: return launch_stage1_t<256>(sp, md, g, prescribed, err, s);
   }
+  return 0;
+}
+
+int launch_mol_stage2(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                      cudaStream_t s) {
+  if (sp.nmol == 0) return 0;
+  switch (sp.nr) {
+    case 64: return launch_stage2_t<64>(sp, md, g, prescribed, err, s);
+    case 128: return launch_stage2_t<128>(sp, md, g, prescribed, err, s);
+    case 256: return launch_stage2_t<256>(sp, md, g, prescribed, err, s);
+  }
+  return 0;
 }
 
 template <int NR>

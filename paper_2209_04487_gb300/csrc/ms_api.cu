@@ -705,35 +705,48 @@ static cudaEvent_t mark(ms_sim* s) {
   return e;
 }
 
+// One coupled step: H half step, the molecules (stage 1: field records and
+// kinetic pass; stage 2: R-space pass, for every species), E half step.
+// `scratch`, when set, replaces the streaming species' d2 buffers.
+static void step_once(ms_sim* s, float2* scratch) {
+  const bool fdtd = s->drive == MS_DRIVE_FDTD;
+  int launched = 0;
+  if (s->timing) mark(s);
+  if (fdtd) {
+    ms::launch_yee_h(s->g, s->stream);
+    ms::launch_aux_h(s->g, s->stream);
+    launched += 1 + (s->g.ks >= 0);
+  }
+  if (s->timing) mark(s);
+  ms::SpeciesDev sp[ms::kMaxSpecies];
+  for (int si = 0; si < s->nspecies; ++si) {
+    sp[si] = s->sp[si];
+    if (scratch && sp[si].path == MS_MOL_STREAMING) sp[si].d2 = scratch;  // rewritten before it is read
+  }
+  for (int si = 0; si < s->nspecies; ++si)
+    launched += ms::launch_mol_stage1(sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
+  if (s->timing) mark(s);
+  for (int si = 0; si < s->nspecies; ++si)
+    launched += ms::launch_mol_stage2(sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
+  if (s->timing) mark(s);
+  if (fdtd) {
+    ms::launch_yee_e(s->g, s->stream);
+    ms::launch_aux_e(s->g, s->stream);
+    launched += 1 + (s->g.ks >= 0);
+  }
+  ms::launch_step_counter(s->d_step, s->stream);
+  ++launched;
+  if (s->timing) {
+    mark(s);
+    s->timed_steps++;
+    s->launches += launched;
+  }
+}
+
 ms_status ms_step(ms_sim* s, int64_t n) {
   if (!s || n < 0) return MS_EINVAL;
   if (s->drive == MS_DRIVE_PRESCRIBED && s->nmol > 0 && s->steps + n > s->nwave) return MS_EINVAL;
-  const bool fdtd = s->drive == MS_DRIVE_FDTD;
-  const bool src = fdtd && s->g.ks >= 0;
-  int per_step = 1;  // step counter
-  if (fdtd) per_step += 2 + (src ? 2 : 0);
-  for (int si = 0; si < s->nspecies; ++si) per_step += s->sp[si].nmol > 0;
-  for (int64_t q = 0; q < n; ++q) {
-    if (s->timing) mark(s);
-    if (fdtd) {
-      ms::launch_yee_h(s->g, s->stream);
-      ms::launch_aux_h(s->g, s->stream);
-    }
-    if (s->timing) mark(s);
-    for (int si = 0; si < s->nspecies; ++si)
-      ms::launch_mol_step(s->sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
-    if (s->timing) mark(s);
-    if (fdtd) {
-      ms::launch_yee_e(s->g, s->stream);
-      ms::launch_aux_e(s->g, s->stream);
-    }
-    ms::launch_step_counter(s->d_step, s->stream);
-    if (s->timing) {
-      mark(s);
-      s->timed_steps++;
-      s->launches += per_step;
-    }
-  }
+  for (int64_t q = 0; q < n; ++q) step_once(s, nullptr);
   s->steps += n;
   return cudaGetLastError() == cudaSuccess ? MS_OK : MS_ECUDA;
 }
@@ -750,23 +763,7 @@ ms_status ms_step_noalloc(ms_sim* s, int64_t n) {
   }
   float2* scratch = nullptr;
   MS_TRY(noalloc_scratch(&scratch));
-  const bool fdtd = s->drive == MS_DRIVE_FDTD;
-  for (int64_t q = 0; q < n; ++q) {
-    if (fdtd) {
-      ms::launch_yee_h(s->g, s->stream);
-      ms::launch_aux_h(s->g, s->stream);
-    }
-    for (int si = 0; si < s->nspecies; ++si) {
-      ms::SpeciesDev sp = s->sp[si];
-      if (sp.path == MS_MOL_STREAMING) sp.d2 = scratch;  // the whole scratch is rewritten before it is read
-      ms::launch_mol_step(sp, s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
-    }
-    if (fdtd) {
-      ms::launch_yee_e(s->g, s->stream);
-      ms::launch_aux_e(s->g, s->stream);
-    }
-    ms::launch_step_counter(s->d_step, s->stream);
-  }
+  for (int64_t q = 0; q < n; ++q) step_once(s, scratch);
   s->steps += n;
   return cudaGetLastError() == cudaSuccess ? MS_OK : MS_ECUDA;
 }
@@ -781,21 +778,23 @@ ms_status ms_timing_begin(ms_sim* s) {
   return MS_OK;
 }
 
-ms_status ms_timing_end(ms_sim* s, double out[4], int64_t* steps, int64_t* launches) {
+ms_status ms_timing_end(ms_sim* s, double out[6], int64_t* steps, int64_t* launches) {
   if (!s || !out) return MS_EINVAL;
   s->timing = false;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
-  double acc[3] = {0, 0, 0};
-  for (size_t b = 0; b + 3 < s->events.size(); b += 4)
-    for (int p = 0; p < 3; ++p) {
+  double acc[4] = {0, 0, 0, 0};  // H, stage 1, stage 2, E
+  for (size_t b = 0; b + 4 < s->events.size(); b += 5)
+    for (int p = 0; p < 4; ++p) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, s->events[b + p], s->events[b + p + 1]) != cudaSuccess) return MS_ECUDA;
       acc[p] += ms;
     }
   out[0] = acc[0];
-  out[1] = acc[1];
-  out[2] = acc[2];
-  out[3] = acc[0] + acc[1] + acc[2];
+  out[1] = acc[1] + acc[2];
+  out[2] = acc[3];
+  out[3] = acc[0] + acc[1] + acc[2] + acc[3];
+  out[4] = acc[1];
+  out[5] = acc[2];
   if (steps) *steps = s->timed_steps;
   if (launches) *launches = s->launches;
   for (cudaEvent_t e : s->events) cudaEventDestroy(e);

@@ -128,8 +128,11 @@ void launch_aux_h(const Grid& g, cudaStream_t s);
 void launch_aux_e(const Grid& g, cudaStream_t s);
 
 // launchers (mol.cu)
-void launch_mol_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed,
-                     int* err, cudaStream_t s);
+// one species' molecular step in two stages (see mol.cu); each returns the kernels it launched
+int launch_mol_stage1(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                      cudaStream_t s);
+int launch_mol_stage2(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                      cudaStream_t s);
 void launch_mol_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s);
 bool mol_step_supported(int nr, int nrot, int path);
 cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip);
