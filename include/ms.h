@@ -55,9 +55,11 @@ typedef enum {
   MS_ECUDA = -3,        /* a CUDA runtime call failed */
   MS_ENUMERIC = -4,     /* latched device condition: non-finite value or
                            a coupling exponential that did not converge */
-  MS_ETIMEOUT = -5,     /* reserved: bounded device wait gave up */
-  MS_EUNSUPPORTED = -6  /* no sm_103 device, or a configuration this build
+  MS_ETIMEOUT = -5,     /* a bounded device wait on an asynchronous copy gave up */
+  MS_EUNSUPPORTED = -6, /* no sm_103 device, or a configuration this build
                            does not support */
+  MS_EIO = -7           /* a checkpoint file could not be written or read,
+                           or is not a checkpoint of this library */
 } ms_status;
 
 enum { MS_BC_PML = 0, MS_BC_PERIODIC = 1 };
@@ -215,6 +217,46 @@ ms_status ms_read_dipoles(ms_sim* sim, int64_t first, int64_t count, double* mu)
  * them. */
 ms_status ms_set_prescribed_field(ms_sim* sim, const float* amp, const float* wave,
                                   int64_t nsteps);
+
+/* Replay drive (MS_DRIVE_PRESCRIBED): molecule k sees the lab field
+ * E[n][k][0..2] (V/m) during step n, for nsteps steps; E is
+ * [nsteps][n_molecules][3] FP32 in the caller's molecule order, copied.
+ * It replaces any amp/wave drive set before, and a later
+ * ms_set_prescribed_field replaces it.  Fields recorded on a coupled run by
+ * ms_record_local_fields replay that run's molecular dynamics exactly
+ * (same arithmetic on the same FP32 inputs).  Errors: MS_EINVAL for a NULL
+ * argument, nsteps <= 0 or an FDTD-driven handle; MS_ENOMEM. */
+ms_status ms_set_replay_field(ms_sim* sim, const float* E, int64_t nsteps);
+
+/* Advances nsteps coupled steps (as ms_step) and records, at every step n,
+ * the lab-frame E^n that drives each listed molecule: the components owned
+ * by its cell (the gather of the coupled step, Eq. 1 grid, in V/m).  dst is
+ * [nsteps][m][3] FP32, caller-owned, written when the call returns
+ * (synchronous).  mol_ids: m molecule indices in the caller's order.
+ * Errors: MS_EINVAL (NULL pointer, m <= 0, nsteps < 0, an index out of
+ * range, or a handle without a field grid), MS_ENOMEM for the temporary
+ * device buffer, and the latched errors of ms_step. */
+ms_status ms_record_local_fields(ms_sim* sim, const int64_t* mol_ids, int64_t m, float* dst,
+                                 int64_t nsteps);
+
+/* Checkpoint / resume (no counterpart in the paper, which runs to completion).
+ * ms_save writes the whole evolving state to the file `path`:
+ *   - the fields E and H;
+ *   - the Drude current;
+ *   - the CPML auxiliaries and the incident line;
+ *   - every species' wavepackets;
+ *   - the molecules' dipoles, populations and absorbed norm;
+ *   - the step counter.
+ * The inputs (geometry, materials, molecules, drive samples) are not saved.
+ * ms_load restores such a file into a handle created from the same
+ * descriptors; the sizes in the file must match (MS_EINVAL otherwise).  A
+ * prescribed or replay drive is set again by the caller.  N steps equal
+ * N/2 steps, save, load into a fresh handle, N/2 steps, bit for bit.  Both
+ * calls are synchronous and stage through a bounded host buffer.  Errors:
+ * MS_EINVAL (NULL argument, size mismatch), MS_EIO (open, short read or
+ * write, wrong magic or version), MS_ECUDA. */
+ms_status ms_save(ms_sim* sim, const char* path);
+ms_status ms_load(ms_sim* sim, const char* path);
 
 /* Phase timing with CUDA events on the handle's stream.  Between
  * ms_timing_begin and ms_timing_end every ms_step records events around its

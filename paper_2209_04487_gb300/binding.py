@@ -16,7 +16,7 @@ import numpy as np
 
 from . import build as _build
 
-MS_OK, MS_EINVAL, MS_ENOMEM, MS_ECUDA, MS_ENUMERIC, MS_ETIMEOUT, MS_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+MS_OK, MS_EINVAL, MS_ENOMEM, MS_ECUDA, MS_ENUMERIC, MS_ETIMEOUT, MS_EUNSUPPORTED, MS_EIO = 0, -1, -2, -3, -4, -5, -6, -7
 MS_BC_PML, MS_BC_PERIODIC = 0, 1
 MS_PREC_FP32, MS_PREC_MIXED_BF16X3 = 0, 1
 MS_DRIVE_FDTD, MS_DRIVE_PRESCRIBED = 0, 1
@@ -79,6 +79,10 @@ def _load() -> C.CDLL:
                                            P(C.c_double), P(C.c_double), P(C.c_double)]),
         "ms_read_dipoles": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, P(C.c_double)]),
         "ms_set_prescribed_field": (C.c_int, [C.c_void_p, P(C.c_float), P(C.c_float), C.c_int64]),
+        "ms_set_replay_field": (C.c_int, [C.c_void_p, P(C.c_float), C.c_int64]),
+        "ms_record_local_fields": (C.c_int, [C.c_void_p, P(C.c_int64), C.c_int64, P(C.c_float), C.c_int64]),
+        "ms_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+        "ms_load": (C.c_int, [C.c_void_p, C.c_char_p]),
         "ms_device_bytes": (C.c_size_t, [C.c_void_p]),
         "ms_timing_begin": (C.c_int, [C.c_void_p]),
         "ms_timing_end": (C.c_int, [C.c_void_p, P(C.c_double), P(C.c_int64), P(C.c_int64)]),
@@ -97,7 +101,8 @@ LIB = _load()
 # every symbol include/ms.h declares
 EXPORTED = ("ms_create", "ms_step", "ms_step_noalloc", "ms_step_count", "ms_read_fields", "ms_write_fields",
             "ms_read_populations", "ms_read_dissociation", "ms_read_dipoles",
-            "ms_set_prescribed_field", "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
+            "ms_set_prescribed_field", "ms_set_replay_field", "ms_record_local_fields", "ms_save", "ms_load",
+            "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
             "ms_destroy", "ms_status_string")
 
 
@@ -244,6 +249,27 @@ class Simulation:
         _check(LIB.ms_read_dissociation(self.h, first, count, _ptr(ag, C.c_double), _ptr(ae, C.c_double),
                                         _ptr(rn, C.c_double), _ptr(rd, C.c_double)), "ms_read_dissociation")
         return np.stack([ag, ae], axis=1), np.stack([rn, rd], axis=1)
+
+    def set_replay(self, E: np.ndarray):
+        """Replay drive: E [nsteps][n_molecules][3] lab field (V/m)."""
+        e = np.ascontiguousarray(E, np.float32)
+        if e.ndim != 3 or e.shape[2] != 3:
+            raise ValueError("replay field must be [nsteps][n_molecules][3]")
+        _check(LIB.ms_set_replay_field(self.h, _ptr(e, C.c_float), e.shape[0]), "ms_set_replay_field")
+
+    def record_local_fields(self, mol_ids, nsteps: int) -> np.ndarray:
+        """Advance nsteps coupled steps; returns E^n at the listed molecules, [nsteps][m][3]."""
+        ids = np.ascontiguousarray(mol_ids, np.int64)
+        out = np.empty((int(nsteps), ids.size, 3), np.float32)
+        _check(LIB.ms_record_local_fields(self.h, _ptr(ids, C.c_int64), ids.size, _ptr(out, C.c_float),
+                                          int(nsteps)), "ms_record_local_fields")
+        return out
+
+    def save(self, path: str):
+        _check(LIB.ms_save(self.h, os.fsencode(path)), "ms_save")
+
+    def load(self, path: str):
+        _check(LIB.ms_load(self.h, os.fsencode(path)), "ms_load")
 
     def dipoles(self, first: int = 0, count: Optional[int] = None) -> np.ndarray:
         count = self.nmol - first if count is None else count

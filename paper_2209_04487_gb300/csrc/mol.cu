@@ -316,6 +316,34 @@ cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip)
   return cudaMemcpyToSymbol(c_dip, dip, sizeof(CouplEntry) * kMaxRot * kMaxCoupl);
 }
 
+// Lab-frame field (V/m) driving molecule m during the current step: the
+// replay samples, the prescribed amp x wave, or the components its cell owns
+// on the grid (E^n, before this step's E update).
+__device__ __forceinline__ void lab_field(const MolDev& md, const Grid& g, int prescribed, int m, float E[3],
+                                          int* err) {
+  const long long n = *g.step;
+  if (prescribed) {
+    const long long nn = n < md.nwave ? n : md.nwave - 1;
+    if (n >= md.nwave) atomicOr(err, kErrPrescribedRange);
+    if (md.replay) {
+      const float* e = md.replay + (nn * md.n + m) * 3;
+      E[0] = e[0];
+      E[1] = e[1];
+      E[2] = e[2];
+    } else {
+      const float wv = md.wave[nn];
+      E[0] = md.amp[3 * (long long)m] * wv;
+      E[1] = md.amp[3 * (long long)m + 1] * wv;
+      E[2] = md.amp[3 * (long long)m + 2] * wv;
+    }
+  } else {
+    const long long c = md.cell[m];
+    E[0] = g.E[0][c];
+    E[1] = g.E[1][c];
+    E[2] = g.E[2][c];
+  }
+}
+
 // Local field at molecule m in its own frame (a.u.): fld = (E_perp, E'_z), the
 // phases e^{i m' phi_E} (ph[m' + J], m' = -J..J) of the frame turned about z
 // so that E'_y = 0, and the number of coupling-series terms, until
@@ -323,20 +351,7 @@ cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip)
 __device__ __noinline__ void molecule_field(const MolDev& md, const Grid& g, int prescribed, int m, int J,
                                             double theta, float* fld, float2* ph, int* nterms, int* err) {
   float E[3];
-  const long long n = *g.step;
-  if (prescribed) {
-    const long long nn = n < md.nwave ? n : md.nwave - 1;
-    if (n >= md.nwave) atomicOr(err, kErrPrescribedRange);
-    const float wv = md.wave[nn];
-    E[0] = md.amp[3 * (long long)m] * wv;
-    E[1] = md.amp[3 * (long long)m + 1] * wv;
-    E[2] = md.amp[3 * (long long)m + 2] * wv;
-  } else {
-    const long long c = md.cell[m];
-    E[0] = g.E[0][c];
-    E[1] = g.E[1][c];
-    E[2] = g.E[2][c];
-  }
+  lab_field(md, g, prescribed, m, E, err);
   const float* O = md.rot + 9 * (long long)m;  // molecule -> lab, row-major
   const float inv_fau = 1.0f / 5.14220674763e11f;
   float Ep[3];
@@ -1100,20 +1115,7 @@ __global__ void mol_field_kernel(SpeciesDev sp, MolDev md, Grid g, int prescribe
   if (lm >= sp.nmol) return;
   const int m = sp.mol[lm];
   float E[3];
-  const long long n = *g.step;
-  if (prescribed) {
-    const long long nn = n < md.nwave ? n : md.nwave - 1;
-    if (n >= md.nwave) atomicOr(err, kErrPrescribedRange);
-    const float wv = md.wave[nn];
-    E[0] = md.amp[3 * (long long)m] * wv;
-    E[1] = md.amp[3 * (long long)m + 1] * wv;
-    E[2] = md.amp[3 * (long long)m + 2] * wv;
-  } else {
-    const long long c = md.cell[m];
-    E[0] = g.E[0][c];
-    E[1] = g.E[1][c];
-    E[2] = g.E[2][c];
-  }
+  lab_field(md, g, prescribed, m, E, err);
   const float* O = md.rot + 9 * (long long)m;  // molecule -> lab, row-major
   const float inv_fau = 1.0f / 5.14220674763e11f;
   float Ep[3];

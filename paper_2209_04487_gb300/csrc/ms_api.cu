@@ -643,6 +643,7 @@ const char* ms_status_string(ms_status s) {
     case MS_ENUMERIC: return "non-finite value or coupling series out of range";
     case MS_ETIMEOUT: return "device wait timed out";
     case MS_EUNSUPPORTED: return "unsupported device or configuration";
+    case MS_EIO: return "checkpoint file error";
   }
   return "unknown status";
 }
@@ -708,7 +709,13 @@ static cudaEvent_t mark(ms_sim* s) {
 // One coupled step: H half step, the molecules (stage 1: field records and
 // kinetic pass; stage 2: R-space pass, for every species), E half step.
 // `scratch`, when set, replaces the streaming species' d2 buffers.
-static void step_once(ms_sim* s, float2* scratch) {
+struct FieldRecorder {  // ms_record_local_fields: E^n of listed molecules, one row per step
+  const long long* ids;
+  int m;
+  float* out;  // [steps][m][3], advanced by the caller
+};
+
+static void step_once(ms_sim* s, float2* scratch, const FieldRecorder* rec = nullptr) {
   const bool fdtd = s->drive == MS_DRIVE_FDTD;
   int launched = 0;
   if (s->timing) mark(s);
@@ -716,6 +723,10 @@ static void step_once(ms_sim* s, float2* scratch) {
     ms::launch_yee_h(s->g, s->stream);
     ms::launch_aux_h(s->g, s->stream);
     launched += 1 + (s->g.ks >= 0);
+  }
+  if (rec) {
+    ms::launch_record_fields(s->g, s->md.cell, rec->ids, rec->m, rec->out, s->stream);
+    ++launched;
   }
   if (s->timing) mark(s);
   ms::SpeciesDev sp[ms::kMaxSpecies];
@@ -884,6 +895,232 @@ ms_status ms_set_prescribed_field(ms_sim* s, const float* amp, const float* wave
   s->md.nwave = nsteps;
   s->nwave = nsteps;
   return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
+}
+
+ms_status ms_set_replay_field(ms_sim* s, const float* E, int64_t nsteps) {
+  if (!s || !E || nsteps <= 0 || s->drive != MS_DRIVE_PRESCRIBED) return MS_EINVAL;
+  float* d = nullptr;
+  MS_TRY(upload(s, &d, E, (size_t)nsteps * 3 * (size_t)(s->nmol > 0 ? s->nmol : 1)));
+  s->md.replay = d;
+  s->md.nwave = nsteps;
+  s->nwave = nsteps;
+  return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
+}
+
+ms_status ms_record_local_fields(ms_sim* s, const int64_t* mol_ids, int64_t m, float* dst, int64_t nsteps) {
+  if (!s || !mol_ids || !dst || m <= 0 || m > INT32_MAX || nsteps < 0 || s->drive != MS_DRIVE_FDTD) return MS_EINVAL;
+  for (int64_t k = 0; k < m; ++k)
+    if (mol_ids[k] < 0 || mol_ids[k] >= s->nmol) return MS_EINVAL;
+  if (nsteps == 0) return latched(s);
+  // temporary device buffers: ids and [nsteps][m][3] samples, released before returning
+  const size_t nid = (size_t)m * sizeof(long long), nout = (size_t)nsteps * m * 3 * sizeof(float);
+  void *d_ids = nullptr, *d_out = nullptr;
+  auto tmp_free = [&](void* p) {
+    if (!p) return;
+    if (s->al.fr) s->al.fr(p, s->al.ctx);
+    else cudaFree(p);
+  };
+  auto tmp_alloc = [&](size_t n) -> void* {
+    void* p = nullptr;
+    if (s->al.fn) p = s->al.fn(n, s->al.ctx);
+    else if (cudaMalloc(&p, n) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return p;
+  };
+  d_ids = tmp_alloc(nid);
+  d_out = tmp_alloc(nout);
+  ms_status st = MS_OK;
+  if (!d_ids || !d_out) st = MS_ENOMEM;
+  std::vector<long long> ids(mol_ids, mol_ids + m);
+  if (st == MS_OK && cudaMemcpyAsync(d_ids, ids.data(), nid, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+    st = MS_ECUDA;
+  if (st == MS_OK) {
+    FieldRecorder rec{static_cast<const long long*>(d_ids), (int)m, static_cast<float*>(d_out)};
+    for (int64_t q = 0; q < nsteps; ++q) {
+      step_once(s, nullptr, &rec);
+      rec.out += (size_t)m * 3;
+    }
+    s->steps += nsteps;
+    if (cudaGetLastError() != cudaSuccess ||
+        cudaMemcpyAsync(dst, d_out, nout, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+        cudaStreamSynchronize(s->stream) != cudaSuccess)
+      st = MS_ECUDA;
+  }
+  cudaStreamSynchronize(s->stream);
+  tmp_free(d_ids);
+  tmp_free(d_out);
+  return st == MS_OK ? latched(s) : st;
+}
+
+// ---- checkpoint ------------------------------------------------------------
+namespace {
+constexpr char kCkMagic[8] = {'M', 'S', '2', '2', '0', '9', 'C', 'K'};
+constexpr uint32_t kCkVersion = 1;
+
+struct CkHeader {
+  char magic[8];
+  uint32_t version, drive;
+  int64_t steps;
+  int32_t nx, ny, nz, nsim;
+  int64_t nmol;
+  int32_t nspecies, pml, ks, jk0, jk1, aux_len;
+  int32_t species[ms::kMaxSpecies][3];  // nr, jmax, molecules
+  uint64_t nblobs;
+};
+
+struct Blob {
+  void* ptr;
+  size_t bytes;
+};
+
+// The evolving device state of a handle, in a fixed order.
+std::vector<Blob> state_blobs(ms_sim* s) {
+  std::vector<Blob> b;
+  const ms::Grid& g = s->g;
+  if (s->drive == MS_DRIVE_FDTD) {
+    const size_t ncell = (size_t)g.ncell_sim * g.nsim;
+    for (int c = 0; c < 3; ++c) b.push_back({g.E[c], ncell * sizeof(float)});
+    for (int c = 0; c < 3; ++c) b.push_back({g.H[c], ncell * sizeof(float)});
+    const size_t nj = (size_t)g.nsim * (g.jk1 - g.jk0) * g.nx * g.ny;
+    if (nj > 0)
+      for (int c = 0; c < 3; ++c) b.push_back({g.J[c], nj * sizeof(float)});
+    if (g.pml > 0) {
+      const size_t np = (size_t)g.nsim * 2 * g.pml * g.nx * g.ny;
+      for (int c = 0; c < 2; ++c) b.push_back({g.psiE[c], np * sizeof(float)});
+      for (int c = 0; c < 2; ++c) b.push_back({g.psiH[c], np * sizeof(float)});
+    }
+    if (g.ks >= 0) {
+      b.push_back({g.auxE, (size_t)g.nsim * (g.aux_len + 1) * sizeof(float)});
+      b.push_back({g.auxH, (size_t)g.nsim * g.aux_len * sizeof(float)});
+    }
+  }
+  for (int si = 0; si < s->nspecies; ++si) {
+    const ms::SpeciesDev& sp = s->sp[si];
+    b.push_back({sp.psi, (size_t)sp.nmol * 2 * sp.nrot * sp.nr * sizeof(float2)});
+  }
+  if (s->nmol > 0) {
+    const size_t n = (size_t)s->nmol;
+    b.push_back({s->md.mu, 3 * n * sizeof(double)});
+    b.push_back({s->md.dmu, 3 * n * sizeof(double)});
+    b.push_back({s->md.pop, 2 * n * sizeof(double)});
+    b.push_back({s->md.absorbed, 2 * n * sizeof(double)});
+  }
+  return b;
+}
+
+CkHeader make_header(ms_sim* s, uint64_t nblobs) {
+  CkHeader h;
+  std::memset(&h, 0, sizeof(h));
+  std::memcpy(h.magic, kCkMagic, 8);
+  h.version = kCkVersion;
+  h.drive = (uint32_t)s->drive;
+  h.steps = s->steps;
+  h.nx = s->g.nx;
+  h.ny = s->g.ny;
+  h.nz = s->g.nz;
+  h.nsim = s->g.nsim;
+  h.nmol = s->nmol;
+  h.nspecies = s->nspecies;
+  h.pml = s->g.pml;
+  h.ks = s->g.ks;
+  h.jk0 = s->g.jk0;
+  h.jk1 = s->g.jk1;
+  h.aux_len = s->g.aux_len;
+  for (int si = 0; si < s->nspecies; ++si) {
+    h.species[si][0] = s->sp[si].nr;
+    h.species[si][1] = s->sp[si].jmax;
+    h.species[si][2] = s->sp[si].nmol;
+  }
+  h.nblobs = nblobs;
+  return h;
+}
+
+constexpr size_t kCkChunk = 64u << 20;  // host staging buffer
+}  // namespace
+
+ms_status ms_save(ms_sim* s, const char* path) {
+  if (!s || !path) return MS_EINVAL;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
+  const std::vector<Blob> blobs = state_blobs(s);
+  const CkHeader h = make_header(s, blobs.size());
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return MS_EIO;
+  ms_status st = std::fwrite(&h, sizeof(h), 1, f) == 1 ? MS_OK : MS_EIO;
+  std::vector<char> buf;
+  for (size_t k = 0; st == MS_OK && k < blobs.size(); ++k) {
+    const uint64_t nb = blobs[k].bytes;
+    if (std::fwrite(&nb, sizeof(nb), 1, f) != 1) {
+      st = MS_EIO;
+      break;
+    }
+    for (size_t off = 0; off < nb; off += kCkChunk) {
+      const size_t len = std::min(kCkChunk, (size_t)nb - off);
+      buf.resize(len);
+      if (cudaMemcpy(buf.data(), static_cast<char*>(blobs[k].ptr) + off, len, cudaMemcpyDeviceToHost) !=
+          cudaSuccess) {
+        st = MS_ECUDA;
+        break;
+      }
+      if (std::fwrite(buf.data(), 1, len, f) != len) {
+        st = MS_EIO;
+        break;
+      }
+    }
+  }
+  if (std::fclose(f) != 0 && st == MS_OK) st = MS_EIO;
+  return st == MS_OK ? latched(s) : st;
+}
+
+ms_status ms_load(ms_sim* s, const char* path) {
+  if (!s || !path) return MS_EINVAL;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
+  const std::vector<Blob> blobs = state_blobs(s);
+  const CkHeader want = make_header(s, blobs.size());
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return MS_EIO;
+  CkHeader h;
+  ms_status st = MS_OK;
+  if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kCkMagic, 8) != 0 || h.version != kCkVersion)
+    st = MS_EIO;
+  else {
+    CkHeader a = h, b = want;  // compare everything but the step count
+    a.steps = b.steps = 0;
+    if (std::memcmp(&a, &b, sizeof(a)) != 0) st = MS_EINVAL;
+  }
+  std::vector<char> buf;
+  for (size_t k = 0; st == MS_OK && k < blobs.size(); ++k) {
+    uint64_t nb = 0;
+    if (std::fread(&nb, sizeof(nb), 1, f) != 1) {
+      st = MS_EIO;
+      break;
+    }
+    if (nb != blobs[k].bytes) {
+      st = MS_EINVAL;
+      break;
+    }
+    for (size_t off = 0; off < nb; off += kCkChunk) {
+      const size_t len = std::min(kCkChunk, (size_t)nb - off);
+      buf.resize(len);
+      if (std::fread(buf.data(), 1, len, f) != len) {
+        st = MS_EIO;
+        break;
+      }
+      if (cudaMemcpy(static_cast<char*>(blobs[k].ptr) + off, buf.data(), len, cudaMemcpyHostToDevice) !=
+          cudaSuccess) {
+        st = MS_ECUDA;
+        break;
+      }
+    }
+  }
+  std::fclose(f);
+  if (st != MS_OK) return st;
+  // the step counter, host and device
+  const long long step = h.steps;
+  if (cudaMemcpy(s->g.step, &step, sizeof(step), cudaMemcpyHostToDevice) != cudaSuccess) return MS_ECUDA;
+  s->steps = h.steps;
+  return latched(s);
 }
 
 size_t ms_device_bytes(const ms_sim* s) { return s ? s->bytes : 0; }

@@ -119,6 +119,7 @@ struct MolDev {
   const float* amp;         // [n][3]
   const float* wave;        // [nwave]
   long long nwave;
+  const float* replay;      // replay drive [nwave][n][3] (lab V/m), else null
 };
 
 // launchers (yee.cu)
@@ -138,6 +139,9 @@ bool mol_step_supported(int nr, int nrot, int path);
 cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip);
 cudaError_t upload_triplet_tables(const CouplEntry* dip);
 void launch_step_counter(long long* step, cudaStream_t s);
+// E^n at the cells of the listed molecules: out[k][3] for k < m
+void launch_record_fields(const Grid& g, const int* cell, const long long* ids, int m, float* out,
+                          cudaStream_t s);
 cudaError_t launch_broadcast_row(float2* psi, const float2* row, int nr, size_t per, long long nmol,
                                  cudaStream_t s);
 

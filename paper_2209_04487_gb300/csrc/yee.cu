@@ -202,6 +202,19 @@ void launch_aux_h(const Grid& g, cudaStream_t s) {
 void launch_aux_e(const Grid& g, cudaStream_t s) {
   if (g.ks >= 0) aux_e_kernel<<<g.nsim, 512, 0, s>>>(g);
 }
+// E^n at the cells of listed molecules (the coupled step's gather)
+__global__ void record_fields_kernel(Grid g, const int* cell, const long long* ids, int m, float* out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const long long c = cell[ids[k]];
+  out[3 * k] = g.E[0][c];
+  out[3 * k + 1] = g.E[1][c];
+  out[3 * k + 2] = g.E[2][c];
+}
+void launch_record_fields(const Grid& g, const int* cell, const long long* ids, int m, float* out,
+                          cudaStream_t s) {
+  record_fields_kernel<<<(m + 127) / 128, 128, 0, s>>>(g, cell, ids, m, out);
+}
 void launch_step_counter(long long* step, cudaStream_t s) {
   step_counter_kernel<<<1, 1, 0, s>>>(step);
 }

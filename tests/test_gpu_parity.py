@@ -109,6 +109,26 @@ def test_coupled_small_matches_oracle(B, path):
     assert np.abs(mu - o.mu).max() < 1e-3 * np.abs(o.mu).max()
 
 
+def test_three_species_coupled_matches_oracle(B):
+    """Three species of different radial grids and rotational bases in one
+    coupled run (each species' molecules polarize the same field)."""
+    species = [W.species_config0(jmax=1), W.Species(nr=128, jmax=2, A=0.05), W.Species(nr=64, jmax=3)]
+    wl = W.custom("three species", 16, 16, 48, src_k=14, pulses=[[2e10, 1.5498, 2e-15, 2e-15]],
+                  layer=(22, 26), n_per_sim=90, species=species, fractions=[0.4, 0.3, 0.3], seed=13,
+                  nsteps=300)
+    sim = B.Simulation(wl)
+    sim.step(wl.nsteps)
+    E = sim.fields(B.MS_FIELD_E)
+    P = sim.populations()
+    mu = sim.dipoles()
+    o = CoupledOracle(wl).run(wl.nsteps)
+    Eo, _ = _fields_oracle(o)
+    assert _rel(E, Eo) < 1e-4
+    assert np.abs(P - o.populations()).max() < 1e-5
+    assert np.abs(mu - o.mu).max() < 1e-3 * np.abs(o.mu).max()
+    assert set(np.unique(wl.species_id)) == {0, 1, 2}
+
+
 @pytest.mark.parametrize("nr,jmax,E0", [(64, 1, 0.0), (128, 4, 0.0), (128, 4, 1e9)])
 def test_norm_drift_2000_steps(B, nr, jmax, E0):
     """Norm drift of the FP32 wavepackets over 2000 steps (target 1e-6):

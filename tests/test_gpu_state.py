@@ -1,0 +1,152 @@
+"""Determinism, checkpoint/resume and field record/replay, through the C ABI.
+
+The coupled step has no atomics (the polarization scatter is a CSR segmented
+sum, the molecular reductions run in a fixed order), so repeated runs, a
+resumed run and a replayed molecular run are compared bit for bit.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_04487_gb300 import build
+    build.build()
+    from paper_2209_04487_gb300 import binding
+    return binding
+
+
+def _slab(nx, ny, nz):
+    m = np.zeros((nz, ny, nx), np.uint8)
+    m[30:] = W.configs.MAT_GLASS
+    m[27:30, ny // 4:3 * ny // 4, nx // 4:3 * nx // 4] = W.configs.MAT_SILVER
+    return m
+
+
+def _workload(n_per_sim=120, nsim=2):
+    """Two simulations (metal, glass, CPML, TF/SF) with two species."""
+    species = [W.species_config0(jmax=1), W.Species(nr=64, jmax=2, A=0.05)]
+    return W.custom("state", 16, 16, 48, nsim=nsim, src_k=14,
+                    pulses=[[2e10, 1.5498, 2e-15, 2e-15], [1.5e10, 1.2, 2e-15, 2.5e-15]][:nsim],
+                    geometry=_slab, layer=(20, 24), n_per_sim=n_per_sim, species=species,
+                    fractions=[0.6, 0.4], seed=9, nsteps=240)
+
+
+def _snapshot(B, sim, nsim):
+    out = {"P": sim.populations(), "mu": sim.dipoles(), "abs": sim.dissociation()[0]}
+    for s in range(nsim):
+        out[f"E{s}"] = sim.fields(B.MS_FIELD_E, s)
+        out[f"H{s}"] = sim.fields(B.MS_FIELD_H, s)
+    return out
+
+
+def _assert_identical(a, b):
+    assert a.keys() == b.keys()
+    for k in a:
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_two_runs_are_bitwise_identical(B):
+    wl = _workload()
+    runs = []
+    for _ in range(2):
+        sim = B.Simulation(wl)
+        sim.step(160)
+        runs.append(_snapshot(B, sim, wl.nsim))
+        sim.close()
+    _assert_identical(*runs)
+    assert np.abs(runs[0]["mu"]).max() > 0.0  # the pulse reached the molecules
+
+
+def test_checkpoint_resume_is_bitwise(B, tmp_path):
+    wl = _workload()
+    ref = B.Simulation(wl)
+    ref.step(160)
+    want = _snapshot(B, ref, wl.nsim)
+    ref.close()
+
+    first = B.Simulation(wl)
+    first.step(80)
+    path = str(tmp_path / "half.ck")
+    first.save(path)
+    first.close()
+
+    resumed = B.Simulation(wl)
+    resumed.load(path)
+    assert resumed.steps == 80
+    resumed.step(80)
+    assert resumed.steps == 160
+    _assert_identical(want, _snapshot(B, resumed, wl.nsim))
+    resumed.close()
+
+
+def test_checkpoint_rejects_mismatch_and_garbage(B, tmp_path):
+    wl = _workload()
+    sim = B.Simulation(wl)
+    sim.step(3)
+    path = str(tmp_path / "a.ck")
+    sim.save(path)
+    other = B.Simulation(_workload(n_per_sim=100))
+    with pytest.raises(B.MSError) as e:
+        other.load(path)
+    assert e.value.code == B.MS_EINVAL
+    junk = tmp_path / "junk.ck"
+    junk.write_bytes(b"not a checkpoint" * 64)
+    with pytest.raises(B.MSError) as e:
+        sim.load(str(junk))
+    assert e.value.code == B.MS_EIO
+    with pytest.raises(B.MSError) as e:
+        sim.load(str(tmp_path / "missing.ck"))
+    assert e.value.code == B.MS_EIO
+    # a truncated file
+    data = open(path, "rb").read()
+    (tmp_path / "short.ck").write_bytes(data[: len(data) // 2])
+    with pytest.raises(B.MSError) as e:
+        sim.load(str(tmp_path / "short.ck"))
+    assert e.value.code == B.MS_EIO
+    # the handle still works, and its own checkpoint still loads
+    sim.load(path)
+    assert sim.steps == 3
+    sim.step(2)
+    other.close()
+    sim.close()
+
+
+def test_record_and_replay_reproduce_the_coupled_molecules(B):
+    wl = _workload(nsim=1)
+    n = 160
+    coupled = B.Simulation(wl)
+    rec = coupled.record_local_fields(np.arange(wl.n_molecules), n)
+    assert rec.shape == (n, wl.n_molecules, 3)
+    assert np.isfinite(rec).all() and np.abs(rec).max() > 0.0
+    assert coupled.steps == n
+    want = {"P": coupled.populations(), "mu": coupled.dipoles(), "abs": coupled.dissociation()[0]}
+    coupled.close()
+
+    replay = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED)
+    replay.set_replay(rec)
+    replay.step(n)
+    got = {"P": replay.populations(), "mu": replay.dipoles(), "abs": replay.dissociation()[0]}
+    _assert_identical(want, got)
+    # one step beyond the replayed samples is refused
+    with pytest.raises(B.MSError) as e:
+        replay.step(1)
+    assert e.value.code == B.MS_EINVAL
+    replay.close()
+
+
+def test_record_rejects_bad_ids(B):
+    wl = _workload(nsim=1)
+    sim = B.Simulation(wl)
+    with pytest.raises(B.MSError) as e:
+        sim.record_local_fields(np.array([0, wl.n_molecules]), 2)
+    assert e.value.code == B.MS_EINVAL
+    assert sim.steps == 0
+    sim.close()

@@ -106,6 +106,13 @@ def test_invalid_descriptors_are_rejected(B, what):
 
 def test_null_handles(B):
     assert B.LIB.ms_step(None, 1) == B.MS_EINVAL
+    assert B.LIB.ms_step_noalloc(None, 1) == B.MS_EINVAL
     assert B.LIB.ms_read_populations(None, 0, 0, None, None) == B.MS_EINVAL
+    assert B.LIB.ms_set_prescribed_field(None, None, None, 1) == B.MS_EINVAL
+    assert B.LIB.ms_set_replay_field(None, None, 1) == B.MS_EINVAL
+    assert B.LIB.ms_record_local_fields(None, None, 1, None, 1) == B.MS_EINVAL
+    assert B.LIB.ms_save(None, b"unused.ck") == B.MS_EINVAL
+    assert B.LIB.ms_load(None, b"unused.ck") == B.MS_EINVAL
+    assert B.LIB.ms_timing_begin(None) == B.MS_EINVAL
     assert B.LIB.ms_step_count(None) == -1
     B.LIB.ms_destroy(None)

@@ -24,6 +24,7 @@ def test_library_builds_and_exports_header_symbols():
 
 def test_status_strings():
     from paper_2209_04487_gb300 import binding as B
-    for code in (B.MS_OK, B.MS_EINVAL, B.MS_ENOMEM, B.MS_ECUDA, B.MS_ENUMERIC, B.MS_ETIMEOUT,
-                 B.MS_EUNSUPPORTED):
-        assert B.LIB.ms_status_string(code)
+    codes = (B.MS_OK, B.MS_EINVAL, B.MS_ENOMEM, B.MS_ECUDA, B.MS_ENUMERIC, B.MS_ETIMEOUT,
+             B.MS_EUNSUPPORTED, B.MS_EIO)
+    texts = [B.LIB.ms_status_string(code) for code in codes]
+    assert all(texts) and b"unknown status" not in texts and len(set(texts)) == len(codes)
