@@ -108,6 +108,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, dist=None, device="cpu") -> float:
+    """The maximum of x over all ranks (x itself without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def _workload(nmol):
     import workloads as W
     return W.config1(n_molecules=nmol)
@@ -236,11 +251,8 @@ def main():
     torch.cuda.synchronize()
     phases, nsteps, launches = sim.timing_end()
     cl = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     P = sim.populations()
     norm_err = float(np.abs(P.sum(axis=1) + sim.dissociation()[0].sum(axis=1) - 1.0).max())
@@ -249,8 +261,8 @@ def main():
     torch.cuda.empty_cache()
 
     sec = ms / 1e3
-    value = world * wl.n_molecules * a.steps / sec
-    cells_rate = world * wl.cells * a.steps / sec
+    value = job_rate(wl.n_molecules * a.steps, world, sec)
+    cells_rate = job_rate(wl.cells * a.steps, world, sec)
     sp = wl.species[0]
     state = 16 * sp.nr * sp.nrot                       # FP32 state of one molecule (bytes)
     per_step = lambda k: phases[k] / max(nsteps, 1)    # ms per step of one timed phase
@@ -294,7 +306,8 @@ def main():
             s2.populations()
         t1 = time.perf_counter()
         s2.close()
-        e2e = {"value": world * wl.n_molecules * a.steps / (t1 - t0), "unit": UNIT,
+        e2e_s = max_over_ranks(t1 - t0, dist, "cuda")
+        e2e = {"value": job_rate(wl.n_molecules * a.steps, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": host_in / a.steps, "d2h_bytes_per_step": 16 * wl.n_molecules,
                "note": "ms_create from host inputs + per step ms_step(1) and a D2H read of all "
                        "populations, host wall clock"}

@@ -271,6 +271,17 @@ ms_status ms_load(ms_sim* sim, const char* path);
 ms_status ms_timing_begin(ms_sim* sim);
 ms_status ms_timing_end(ms_sim* sim, double out[6], int64_t* steps, int64_t* launches);
 
+/* Diagnostic of the bounded waits (no counterpart in the paper).  The
+ * molecular kernels wait for their bulk copies with a bounded wait: each
+ * try suspends the thread until the copy lands or a time hint expires, and
+ * after the last try the kernel records MS_ETIMEOUT and returns instead of
+ * hanging.  This runs that routine in one CTA on a barrier that nothing
+ * completes, with `tries` (1..100000) tries of up to 10 us, so the wait runs
+ * out.  Expected result: MS_ETIMEOUT, with the device context still usable.
+ * MS_EINVAL for tries out of range, MS_ENOMEM / MS_ECUDA on runtime errors.
+ * Needs no handle; allocates one int of device memory. */
+ms_status ms_check_bounded_wait(int32_t tries);
+
 /* Device memory held by the simulation, in bytes. */
 size_t ms_device_bytes(const ms_sim* sim);
 

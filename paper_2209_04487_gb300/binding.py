@@ -82,6 +82,7 @@ def _load() -> C.CDLL:
         "ms_set_replay_field": (C.c_int, [C.c_void_p, P(C.c_float), C.c_int64]),
         "ms_record_local_fields": (C.c_int, [C.c_void_p, P(C.c_int64), C.c_int64, P(C.c_float), C.c_int64]),
         "ms_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+        "ms_check_bounded_wait": (C.c_int, [C.c_int32]),
         "ms_load": (C.c_int, [C.c_void_p, C.c_char_p]),
         "ms_device_bytes": (C.c_size_t, [C.c_void_p]),
         "ms_timing_begin": (C.c_int, [C.c_void_p]),
@@ -102,7 +103,7 @@ LIB = _load()
 EXPORTED = ("ms_create", "ms_step", "ms_step_noalloc", "ms_step_count", "ms_read_fields", "ms_write_fields",
             "ms_read_populations", "ms_read_dissociation", "ms_read_dipoles",
             "ms_set_prescribed_field", "ms_set_replay_field", "ms_record_local_fields", "ms_save", "ms_load",
-            "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
+            "ms_check_bounded_wait", "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
             "ms_destroy", "ms_status_string")
 
 
@@ -157,7 +158,7 @@ class Simulation:
 
     def __init__(self, wl, *, drive: int = MS_DRIVE_FDTD, precision: int = MS_PREC_FP32,
                  with_molecules: bool = True, use_torch: bool = True, stream=None,
-                 mol_path: int = MS_MOL_AUTO):
+                 mol_path: int = MS_MOL_AUTO, allocator=None):
         self.wl = wl
         self._keep = []
         src = np.ascontiguousarray(wl.src, np.float64) if wl.src_k >= 0 else None
@@ -189,7 +190,7 @@ class Simulation:
         self.stream = None
         if use_torch:
             import torch
-            self._alloc = _TorchAllocator()
+            self._alloc = allocator if allocator is not None else _TorchAllocator()
             opts.alloc = self._alloc.c_alloc
             opts.free = self._alloc.c_free
             # a real (non-legacy-default) stream, so that torch events recorded

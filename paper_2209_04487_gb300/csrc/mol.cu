@@ -370,6 +370,7 @@ __device__ __noinline__ void molecule_field(const MolDev& md, const Grid& g, int
     ph[J - q] = make_float2(pw.x, -pw.y);
   }
   const float x = (float)theta * sqrtf(eperp * eperp + Ep[2] * Ep[2]);
+  if (!isfinite(x)) atomicOr(err, kErrNonFinite);  // a non-finite local field
   int nt = 0;
   if (x > 0.f) {
     nt = 1;
@@ -750,19 +751,39 @@ struct RowT {
 constexpr int kRtCu = (int)offsetof(RowT, cu), kRtCd = (int)offsetof(RowT, cd), kRtDu = (int)offsetof(RowT, du),
               kRtDd = (int)offsetof(RowT, dd), kRtPh = (int)offsetof(RowT, ph);
 
-// Wait for phase `parity`, suspending up to 1 ms per try until it completes;
-// gives up after 2000 tries.
-__device__ __forceinline__ bool mbar_wait_sleep(unsigned long long* bar, unsigned parity) {
-  for (int it = 0; it < 2000; ++it) {
+// Wait for phase `parity`, each try suspending up to hint_ns until the phase
+// completes; gives up after `tries` tries (by default about 2 s in all).
+__device__ __forceinline__ bool mbar_wait_sleep(unsigned long long* bar, unsigned parity, int tries = 2000,
+                                                unsigned hint_ns = 1000000u) {
+  for (int it = 0; it < tries; ++it) {
     unsigned done;
     asm volatile(
         "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
         : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(1000000)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     if (done) return true;
   }
   return false;
+}
+
+// Diagnostic of the bounded wait: one CTA waits on a barrier that nothing
+// completes, gives up after `tries` tries of up to 10 us, and records the
+// timeout as the molecular kernels do.
+__global__ void wait_timeout_probe_kernel(int tries, int* flag) {
+  __shared__ __align__(8) unsigned long long bar[1];
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_sleep(&bar[0], 0, tries, 10000u);
+  if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicOr(flag, kErrTimeout);
+}
+
+cudaError_t launch_wait_timeout_probe(int tries, int* flag, cudaStream_t s) {
+  wait_timeout_probe_kernel<<<1, 32, 0, s>>>(tries, flag);
+  return cudaGetLastError();
 }
 
 // Layout of the R-space kernel for basis size J: NW = 2 (J + 1) warps of
@@ -1123,6 +1144,7 @@ __global__ void mol_field_kernel(SpeciesDev sp, MolDev md, Grid g, int prescribe
   for (int i = 0; i < 3; ++i) Ep[i] = (O[i] * E[0] + O[3 + i] * E[1] + O[6 + i] * E[2]) * inv_fau;
   const float th = (float)sp.theta;
   const float x = th * sqrtf(Ep[0] * Ep[0] + Ep[1] * Ep[1] + Ep[2] * Ep[2]);
+  if (!isfinite(x)) atomicOr(err, kErrNonFinite);  // a non-finite local field
   int nt = 0;
   if (x > 0.f) {
     nt = 1;

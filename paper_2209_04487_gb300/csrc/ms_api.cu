@@ -1123,6 +1123,23 @@ ms_status ms_load(ms_sim* s, const char* path) {
   return latched(s);
 }
 
+ms_status ms_check_bounded_wait(int32_t tries) {
+  if (tries < 1 || tries > 100000) return MS_EINVAL;
+  int* d_flag = nullptr;
+  if (cudaMalloc(&d_flag, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return MS_ENOMEM;
+  }
+  int flag = 0;
+  ms_status st = MS_OK;
+  if (cudaMemset(d_flag, 0, sizeof(int)) != cudaSuccess || ms::launch_wait_timeout_probe(tries, d_flag, 0) != cudaSuccess ||
+      cudaMemcpy(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = MS_ECUDA;
+  cudaFree(d_flag);
+  if (st != MS_OK) return st;
+  return (flag & ms::kErrTimeout) ? MS_ETIMEOUT : MS_OK;
+}
+
 size_t ms_device_bytes(const ms_sim* s) { return s ? s->bytes : 0; }
 
 void ms_destroy(ms_sim* s) {

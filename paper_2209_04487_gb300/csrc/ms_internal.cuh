@@ -138,6 +138,7 @@ void launch_mol_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s);
 bool mol_step_supported(int nr, int nrot, int path);
 cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip);
 cudaError_t upload_triplet_tables(const CouplEntry* dip);
+cudaError_t launch_wait_timeout_probe(int tries, int* flag, cudaStream_t s);
 void launch_step_counter(long long* step, cudaStream_t s);
 // E^n at the cells of the listed molecules: out[k][3] for k < m
 void launch_record_fields(const Grid& g, const int* cell, const long long* ids, int m, float* out,
