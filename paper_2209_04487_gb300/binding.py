@@ -152,6 +152,11 @@ def species_desc(sp) -> SpeciesDesc:
                        sp.beta, sp.rc, sp.dipole, sp.absorber_r, sp.absorber_power)
 
 
+def mixed_supported(wl) -> bool:
+    """Whether every species of the workload can take the mixed kinetic pass."""
+    return all(sp.nr in (64, 128) for sp in wl.species)
+
+
 class Simulation:
     """One coupled simulation on the current CUDA device (workload in the
     layout of ``workloads.Workload``)."""

@@ -23,8 +23,10 @@
 // z that puts E' in the xz plane (a diagonal phase on the correction only),
 // where M is real.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <mutex>
@@ -1699,6 +1701,228 @@ static void launch_step_tt(const SpeciesDev& sp, const MolDev& md, const Grid& g
   k<<<sp.nmol, FFTShape<NR>::THREADS, sh.smem, s>>>(sp, md, g, prescribed, sh.ch, err);
 }
 
+// ----------------------------------------------------------------------------
+// Mixed form of the kinetic pass: d2 = (K - I) s for every row as a tensor-core
+// GEMM on split BF16 operands (x = x_hi + x_lo, three products, FP32
+// accumulation in tensor memory).  K is the N_r x N_r circulant of the
+// kinetic propagator (symmetric).  Transposed so that the accumulator lanes
+// are radial points: D[n][m] = sum_k (K - I)[n][k] s_m[k], A = K - I (resident
+// in shared memory, four planes), B = 64 state rows per tile (four planes,
+// double buffered), D double-buffered in tensor memory: one tile is staged
+// while the previous tile's products run, and written out while the next
+// tile's run.  K - I being circulant, its K-slice j (columns 16 j..16 j + 15)
+// is slice 0 with the rows shifted by 16 j; A is therefore stored once as
+// one 16-column strip of 128 + N_r - 16 rows, and slice j is the window
+// starting 16 j rows higher.
+// ----------------------------------------------------------------------------
+__host__ __device__ inline int tc_kmaj_off(int r, int k, int K) {
+  // K-major, no swizzle: 8-row x 16-byte core matrices, 128 B each, row groups outer
+  return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+int mixed_plane_offset(int row, int k, int nr) { return tc_kmaj_off(row, k, 16); }
+int mixed_strip_rows(int nr) { return 128 + nr - 16; }
+bool mol_mixed_supported(int nr) { return nr == 64 || nr == 128; }
+
+// shared-memory matrix descriptor: start, leading (K-direction) and stride
+// (8-row group) byte offsets, no swizzle
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (unsigned long long)((addr >> 4) & 0x3FFF) | ((unsigned long long)((lbo >> 4) & 0x3FFF) << 16) |
+         ((unsigned long long)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                       int accumulate) {
+  asm volatile(
+      "{ .reg .pred p; setp.ne.b32 p, %4, 0; tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p; }" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void tc_ld32(unsigned taddr, unsigned (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+
+template <int NR>
+struct TcShape {
+  static constexpr int MR = 128;                 // accumulator lanes: radial points (>= NR discarded)
+  static constexpr int TR = 64;                  // state rows per tile (the MMA's N)
+  static constexpr int KS = NR / 16;             // K slices of 16
+  static constexpr int SR = MR + NR - 16;        // rows of the circulant strip
+  static constexpr int APL = SR * 16 * 2;        // bytes of one strip plane
+  static constexpr int BPL = TR * NR * 2;        // bytes of one B plane
+  static constexpr int LOADS = TR * NR / (256 * 2);  // 16-byte loads per thread per tile
+  static constexpr int SMEM = 4 * APL + 2 * 4 * BPL; // strip + two tile buffers
+};
+
+template <int NR>
+__global__ void __launch_bounds__(256, 1) mol_kinetic_tc_kernel(SpeciesDev sp, long long rows, int* err) {
+  using S = TcShape<NR>;
+  constexpr int TR = S::TR, KS = S::KS, APL = S::APL, BPL = S::BPL, LOADS = S::LOADS;
+  constexpr unsigned SBO_A = 2 * 128, SBO_B = (NR / 8) * 128;
+  constexpr unsigned kCols = 4 * TR;  // tensor memory: 2 buffers x (Re, Im) x TR rows
+  extern __shared__ __align__(1024) uint8_t smem_tc[];
+  uint8_t* A = smem_tc;             // (K - I) strip: Re hi, Re lo, Im hi, Im lo
+  uint8_t* Bt = smem_tc + 4 * APL;  // two tile buffers, each Re hi, Re lo, Im hi, Im lo
+  __shared__ __align__(8) unsigned long long bar[2];  // [0] A staged, [1] products done
+  __shared__ unsigned tmem_base;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  const float2* X = sp.psi;
+  float2* Y = sp.d2;
+
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar[0], 4u * APL);
+    bulk_g2s(A, sp.kpl, 4u * APL, &bar[0]);
+  }
+  if (w == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_base;
+  auto release = [&]() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (w == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols));
+  };
+  // a wait on bar[id] phase ph by every thread, uniform outcome; on a timeout
+  // the products in flight get a second bounded wait before tensor memory is freed
+  auto wait_all = [&](int id, unsigned ph) -> bool {
+    const bool ok = mbar_wait_sleep(&bar[id], ph);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__syncthreads_and(ok)) return true;
+    if (t == 0) atomicOr(err, kErrTimeout);
+    if (!ok) mbar_wait_sleep(&bar[id], ph);
+    release();
+    return false;
+  };
+  if (!wait_all(0, 0)) return;
+
+  // load slot u of a tile: rows 8 q + (lane & 7), points 8 kc + 2 (lane >> 3) (+1)
+  auto slot_row = [&](int u) { return 8 * ((w + 8 * u) / (NR / 8)) + (lane & 7); };
+  auto slot_k = [&](int u) { return 8 * ((w + 8 * u) % (NR / 8)) + 2 * (lane >> 3); };
+  float4 pre[LOADS];
+  auto fetch = [&](long long tile) {
+#pragma unroll
+    for (int u = 0; u < LOADS; ++u) {
+      const long long gr = tile * TR + slot_row(u);
+      pre[u] = gr < rows ? __ldcs(reinterpret_cast<const float4*>(X + gr * NR + slot_k(u)))
+                         : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+  auto stage = [&](int buf) {  // the fetched tile -> four bf16 planes of buffer buf
+    uint8_t* B0 = Bt + buf * 4 * BPL;
+#pragma unroll
+    for (int u = 0; u < LOADS; ++u) {
+      const float re[2] = {pre[u].x, pre[u].z}, im[2] = {pre[u].y, pre[u].w};
+      __nv_bfloat16 rh[2], rl[2], ih[2], il[2];
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        rh[e] = __float2bfloat16_rn(re[e]);
+        rl[e] = __float2bfloat16_rn(re[e] - __bfloat162float(rh[e]));
+        ih[e] = __float2bfloat16_rn(im[e]);
+        il[e] = __float2bfloat16_rn(im[e] - __bfloat162float(ih[e]));
+      }
+      const int off = tc_kmaj_off(slot_row(u), slot_k(u), NR);
+      *reinterpret_cast<__nv_bfloat162*>(B0 + 0 * BPL + off) = __halves2bfloat162(rh[0], rh[1]);
+      *reinterpret_cast<__nv_bfloat162*>(B0 + 1 * BPL + off) = __halves2bfloat162(rl[0], rl[1]);
+      *reinterpret_cast<__nv_bfloat162*>(B0 + 2 * BPL + off) = __halves2bfloat162(ih[0], ih[1]);
+      *reinterpret_cast<__nv_bfloat162*>(B0 + 3 * BPL + off) = __halves2bfloat162(il[0], il[1]);
+    }
+  };
+  auto issue = [&](int buf) {  // 2 outputs x 6 split products x KS slices, one thread
+    constexpr unsigned idp =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TR >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+    constexpr unsigned idn = idp | (1u << 14);  // B negated
+    // {A plane, B plane, negate}: Re = Kr Xr - Ki Xi, Im = Kr Xi + Ki Xr, each as hh + hl + lh
+    constexpr int blk[2][6][3] = {{{0, 0, 0}, {0, 1, 0}, {1, 0, 0}, {2, 2, 1}, {2, 3, 1}, {3, 2, 1}},
+                                  {{0, 2, 0}, {0, 3, 0}, {1, 2, 0}, {2, 0, 0}, {2, 1, 0}, {3, 0, 0}}};
+    // slice j: A window starts (NR - 16 - 16 j) rows into the strip, B at column 16 j
+    unsigned long long da[4], db[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      da[p] = tc_desc(smem_u32(A + p * APL) + ((NR - 16) / 8) * SBO_A, 128, SBO_A);
+      db[p] = tc_desc(smem_u32(Bt + (buf * 4 + p) * BPL), 128, SBO_B);
+    }
+#pragma unroll
+    for (int o = 0; o < 2; ++o) {
+      const unsigned d = tmem + (unsigned)(buf * 2 * TR + o * TR);
+#pragma unroll
+      for (int b = 0; b < 6; ++b)
+#pragma unroll
+        for (int j = 0; j < KS; ++j)
+          tc_mma(d, da[blk[o][b][0]] - (unsigned long long)(j * 2 * SBO_A / 16),
+                 db[blk[o][b][1]] + (unsigned long long)(j * 256 / 16), blk[o][b][2] ? idn : idp,
+                 (b | j) != 0);
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(&bar[1]))
+                 : "memory");
+  };
+  auto drain = [&](int buf, long long tile) {  // tensor memory -> d2 rows of the tile
+    constexpr int H = TR / 2;                       // rows per warp half
+    const int n = 32 * (w & 3) + lane, rh = w >> 2;  // radial point, row half
+    static_assert(H == 32, "the write-out loads 32 accumulator columns per warp half");
+    unsigned re[H], im[H];
+    const unsigned ta = tmem + ((unsigned)(32 * (w & 3)) << 16) + (unsigned)(buf * 2 * TR + H * rh);
+    tc_ld32(ta, re);
+    tc_ld32(ta + TR, im);
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (n < NR) {
+#pragma unroll
+      for (int r = 0; r < H; ++r) {
+        const long long gr = tile * TR + H * rh + r;
+        if (gr < rows) __stcs(Y + gr * NR + n, make_float2(__uint_as_float(re[r]), __uint_as_float(im[r])));
+      }
+    }
+  };
+  auto sync_async = [&]() {  // the staged planes are visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  };
+
+  // tile i: staged into buffer i & 1 while the products of tile i - 1 run
+  // (its loads were issued one iteration earlier), issued once those are
+  // done; then tile i - 1 is written out while tile i's products run
+  const long long ntiles = (rows + TR - 1) / TR;
+  long long tile = blockIdx.x;
+  if (tile >= ntiles) {
+    release();
+    return;
+  }
+  fetch(tile);
+  stage(0);
+  sync_async();
+  if (t == 0) issue(0);
+  long long prev = tile;
+  tile += gridDim.x;
+  if (tile < ntiles) fetch(tile);
+  int i = 1;
+  for (; tile < ntiles; tile += gridDim.x, ++i) {
+    stage(i & 1);  // buffer i & 1 was read by the products of tile i - 2, complete
+    if (tile + gridDim.x < ntiles) fetch(tile + gridDim.x);  // in flight until the next stage
+    sync_async();
+    if (!wait_all(1, (unsigned)((i - 1) & 1))) return;  // products of tile i - 1
+    if (t == 0) issue(i & 1);
+    drain((i - 1) & 1, prev);  // overlaps the products of tile i
+    prev = tile;
+  }
+  if (!wait_all(1, (unsigned)((i - 1) & 1))) return;
+  drain((i - 1) & 1, prev);
+  release();
+}
+
 // Stage 1 of a species' step: in the streaming form the per-molecule field
 // records (point-resident R-space kernel only) and the kinetic pass d2 = (T - 1) s.
 // Stage 2: the R-space pass (streaming form) or the whole fused step.
@@ -1713,6 +1937,19 @@ static int launch_stage1_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
     ++n;
   }
   const long long rows_total = (long long)sp.nmol * 2 * sp.nrot;
+  if (sp.mixed) {  // split-BF16 tensor-core GEMM
+    if constexpr (NR == 64 || NR == 128) {
+      using T = TcShape<NR>;
+      int dev = 0, nsm = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      const long long ntiles = (rows_total + T::TR - 1) / T::TR;
+      const int grid = (int)std::min<long long>(ntiles, (long long)(nsm > 0 ? nsm : 1));
+      cudaFuncSetAttribute(mol_kinetic_tc_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, T::SMEM);
+      mol_kinetic_tc_kernel<NR><<<grid, 256, T::SMEM, s>>>(sp, rows_total, err);
+    }
+    return n + 1;
+  }
   const int RB = kinetic_rows(NR);
   const size_t ksmem = 2 * (size_t)NR * sizeof(float2) + (size_t)RB * NR * sizeof(float2);
   cudaFuncSetAttribute(mol_kinetic_kernel<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ksmem);

@@ -242,8 +242,57 @@ ms_status upload_angular_tables() {
   return ms::upload_triplet_tables(dip.data()) == cudaSuccess ? MS_OK : MS_ECUDA;
 }
 
+// bf16 of x, round to nearest even (x finite)
+uint16_t to_bf16(float x) {
+  uint32_t u;
+  std::memcpy(&u, &x, 4);
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+float from_bf16(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float x;
+  std::memcpy(&x, &u, 4);
+  return x;
+}
+
+// (K - I) of the kinetic propagator for the mixed form, (K - I)[a][b] =
+// (1/nr) sum_p (e^{-i k_p^2 dtau / 2 mu} - 1) e^{2 pi i p (a - b) / nr} (FP64),
+// a circulant: stored as one 16-column strip T[i][q] = (K - I)[i - (nr - 16)][q]
+// (indices mod nr) of 128 + nr - 16 rows, in four bf16 planes (Re hi, Re lo,
+// Im hi, Im lo) in the tensor cores' K-major layout.
+std::vector<uint16_t> mixed_kinetic_planes(int nr, double dR, double dtau, double mu) {
+  std::vector<cplx> kd(nr);
+  for (int dlt = 0; dlt < nr; ++dlt) {
+    cplx acc = 0.0;
+    for (int k = 0; k < nr; ++k) {
+      const int p = k < nr / 2 ? k : k - nr;
+      const double kk = 2.0 * kPi * p / (nr * dR);
+      acc += expm1i(-kk * kk * dtau / (2.0 * mu)) * std::polar(1.0, 2.0 * kPi * p * dlt / nr);
+    }
+    kd[dlt] = acc / (double)nr;
+  }
+  const int rows = ms::mixed_strip_rows(nr);
+  const size_t plane = (size_t)rows * 16;  // elements
+  std::vector<uint16_t> out(4 * plane, 0);
+  for (int i = 0; i < rows; ++i)
+    for (int q = 0; q < 16; ++q) {
+      const int dlt = (((i - (nr - 16) - q) % nr) + nr) % nr;
+      const cplx v = kd[dlt];
+      const uint16_t rh = to_bf16((float)v.real()), ih = to_bf16((float)v.imag());
+      const uint16_t rl = to_bf16((float)(v.real() - (double)from_bf16(rh)));
+      const uint16_t il = to_bf16((float)(v.imag() - (double)from_bf16(ih)));
+      const size_t off = (size_t)ms::mixed_plane_offset(i, q, nr) / 2;
+      out[off] = rh;
+      out[plane + off] = rl;
+      out[2 * plane + off] = ih;
+      out[3 * plane + off] = il;
+    }
+  return out;
+}
+
 ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const std::vector<int>& ids,
-                        int path) {
+                        int path, bool mixed) {
   ms::SpeciesDev& sp = s->sp[si];
   const int nr = d.nr, J = d.jmax, nrot = (J + 1) * (J + 1);
   // layout: the streaming form unless the caller asks for the fused one
@@ -252,6 +301,8 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   sp.jmax = J;
   sp.nrot = nrot;
   sp.nmol = (int)ids.size();
+  sp.mixed = mixed ? 1 : 0;
+  sp.kpl = nullptr;
   const double dR = (d.rmax - d.rmin) / (nr - 1);
   const double dtau = dt / kTau;
   const double mu = d.mass_me;
@@ -324,6 +375,10 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   MS_TRY(zeros(s, &sp.psi, per * ids.size()));
   sp.d2 = nullptr;
   sp.fld = nullptr;
+  if (mixed) {
+    const std::vector<uint16_t> kp = mixed_kinetic_planes(nr, dR, dtau, mu);
+    MS_TRY(upload(s, (uint16_t**)&sp.kpl, kp.data(), kp.size()));
+  }
   if (sp.path == MS_MOL_STREAMING) {
     MS_TRY(zeros(s, &sp.d2, per * ids.size()));
     MS_TRY(zeros(s, &sp.fld, ids.size()));
@@ -529,7 +584,8 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
     std::vector<int> ids;
     for (long long q = 0; q < n; ++q)
       if (D->species_id[q] == si) ids.push_back((int)q);
-    MS_TRY(build_species(s, si, D->species[si], dt, ids, O ? O->mol_path : MS_MOL_AUTO));
+    MS_TRY(build_species(s, si, D->species[si], dt, ids, O ? O->mol_path : MS_MOL_AUTO,
+                         O && O->precision == MS_PREC_MIXED_BF16X3));
   }
   return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
 }
@@ -559,7 +615,8 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
     if (M->material_id[c] >= M->n_materials) return MS_EINVAL;
   const int drive = O ? O->drive : MS_DRIVE_FDTD;
   if (drive != MS_DRIVE_FDTD && drive != MS_DRIVE_PRESCRIBED) return MS_EINVAL;
-  if (O && O->precision != MS_PREC_FP32) return MS_EUNSUPPORTED;
+  if (O && O->precision != MS_PREC_FP32 && O->precision != MS_PREC_MIXED_BF16X3) return MS_EINVAL;
+  const bool mixed = O && O->precision == MS_PREC_MIXED_BF16X3;
   if (O && O->mol_substeps != 0 && O->mol_substeps != 1) return MS_EUNSUPPORTED;
   if (O && ((O->alloc == nullptr) != (O->free == nullptr))) return MS_EINVAL;
   if (O && (O->mol_path < MS_MOL_AUTO || O->mol_path > MS_MOL_STREAMING)) return MS_EINVAL;
@@ -579,6 +636,8 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
       if (path == MS_MOL_FUSED ? !ms::mol_step_supported(sp.nr, nrot, MS_MOL_FUSED)
                                : !ms::mol_step_supported(sp.nr, nrot, MS_MOL_STREAMING))
         return MS_EUNSUPPORTED;
+      // the mixed kinetic pass: streaming form, radial grids of 64 or 128 points
+      if (mixed && (path == MS_MOL_FUSED || !ms::mol_mixed_supported(sp.nr))) return MS_EUNSUPPORTED;
     }
     for (long long q = 0; q < D->n_molecules; ++q) {
       const int si = D->species_id[q];

@@ -82,6 +82,8 @@ struct SpeciesDev {
   float2* psi;              // state [nmol][2][nrot][nr], s = T^{-1/2} psi
   float2* d2;               // streaming form: scratch (T - 1) s, same layout
   float4* fld;              // streaming form: per molecule (theta E'_z, theta E'_x/2, theta E'_y/2, terms)
+  int mixed;                // kinetic pass as the split-BF16 tensor-core GEMM (MS_PREC_MIXED_BF16X3)
+  const uint16_t* kpl;      // mixed: (K - I) strip as four bf16 planes (Re hi, Re lo, Im hi, Im lo)
   int path;                 // MS_MOL_FUSED or MS_MOL_STREAMING
   // per (s, j, r): e^{-i V dtau} - 1 and e^{-i V dtau/2}
   const float2* vdelta;     // [2][jmax+1][nr]
@@ -139,6 +141,12 @@ bool mol_step_supported(int nr, int nrot, int path);
 cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip);
 cudaError_t upload_triplet_tables(const CouplEntry* dip);
 cudaError_t launch_wait_timeout_probe(int tries, int* flag, cudaStream_t s);
+// mixed form of the kinetic pass: nr values it supports, the rows of the
+// circulant strip of (K - I) and the byte offset of its element (row, q),
+// q < 16, in the tensor cores' K-major layout
+bool mol_mixed_supported(int nr);
+int mixed_strip_rows(int nr);
+int mixed_plane_offset(int row, int k, int nr);
 void launch_step_counter(long long* step, cudaStream_t s);
 // E^n at the cells of the listed molecules: out[k][3] for k < m
 void launch_record_fields(const Grid& g, const int* cell, const long long* ids, int m, float* out,

@@ -56,9 +56,13 @@ def _wl():
     return W.custom("v", 8, 8, 48, src_k=14, layer=(20, 24), n_per_sim=5, nsteps=10)
 
 
-def test_valid_descriptor_reaches_the_device_check(B):
+@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+def test_valid_descriptor_reaches_the_device_check(B, precision):
     import torch
-    rc = _create(B, _wl())
+
+    def mutate(g, m, d, o, keep):
+        o.precision = B.MS_PREC_MIXED_BF16X3 if precision == "mixed" else B.MS_PREC_FP32
+    rc = _create(B, _wl(), mutate)
     if torch.cuda.is_available():
         assert rc == B.MS_OK
     else:
@@ -66,7 +70,8 @@ def test_valid_descriptor_reaches_the_device_check(B):
 
 
 @pytest.mark.parametrize("what", ["courant", "nx", "pml", "src_in_pml", "material_id", "species_nr",
-                                  "jmax", "position", "quaternion", "precision_mixed", "alloc_half"])
+                                  "jmax", "position", "quaternion", "precision_unknown", "mixed_fused",
+                                  "mixed_nr256", "alloc_half"])
 def test_invalid_descriptors_are_rejected(B, what):
     def mutate(g, m, d, o, keep):
         if what == "courant":
@@ -94,13 +99,19 @@ def test_invalid_descriptors_are_rejected(B, what):
             qz = np.zeros(4 * d.n_molecules)
             keep.append(qz)
             d.orient = qz.ctypes.data_as(C.POINTER(C.c_double))
-        elif what == "precision_mixed":
+        elif what == "precision_unknown":
+            o.precision = 7
+        elif what == "mixed_fused":
             o.precision = B.MS_PREC_MIXED_BF16X3
+            o.mol_path = B.MS_MOL_FUSED
+        elif what == "mixed_nr256":
+            o.precision = B.MS_PREC_MIXED_BF16X3
+            d.species[0].nr = 256
         elif what == "alloc_half":
             o.alloc = B._ALLOC(lambda n, c: None)
     rc = _create(B, _wl(), mutate)
     expect = {"species_nr": B.MS_EUNSUPPORTED, "jmax": B.MS_EUNSUPPORTED,
-              "precision_mixed": B.MS_EUNSUPPORTED}.get(what, B.MS_EINVAL)
+              "mixed_fused": B.MS_EUNSUPPORTED, "mixed_nr256": B.MS_EUNSUPPORTED}.get(what, B.MS_EINVAL)
     assert rc == expect, (what, rc)
 
 
