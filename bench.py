@@ -232,63 +232,65 @@ def main():
 
     wl = _workload(a.molecules)
     path = {"auto": B.MS_MOL_AUTO, "fused": B.MS_MOL_FUSED, "streaming": B.MS_MOL_STREAMING}[a.mol_path]
-    sim = B.Simulation(wl, mol_path=path)
-    # the TF/SF wave needs ~40 steps to reach the molecular layer: before that
-    # the molecules see E' = 0 and skip the coupling work, which is not the
-    # regime the step is measured in
-    sim.step(a.preroll)
-    sim.step(a.warmup)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = Clocks(local)
-    stream = sim.stream          # the stream the library launches on
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    sim.timing_begin()
-    ev0.record(stream)
-    sim.step(a.steps)
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    phases, nsteps, launches = sim.timing_end()
-    cl = clocks.stop()
-    ms = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
-    if dist:
-        dist.barrier()
-    P = sim.populations()
-    norm_err = float(np.abs(P.sum(axis=1) + sim.dissociation()[0].sum(axis=1) - 1.0).max())
-    sim.close()
-    del sim
-    torch.cuda.empty_cache()
 
-    # the mixed form: same workload, same steps, kinetic pass on the tensor cores
-    mixed = None
-    if not a.no_mixed and B.mixed_supported(wl):
-        sm = B.Simulation(wl, mol_path=B.MS_MOL_STREAMING, precision=B.MS_PREC_MIXED_BF16X3)
-        sm.step(a.preroll)
-        sm.step(a.warmup)
+    def time_form(mol_path, precision, clocks=False):
+        """Preroll, warm-up, then a.steps timed steps of one form (CUDA events on
+        the library's stream, max over ranks) and its phase timings."""
+        sim = B.Simulation(wl, mol_path=mol_path, precision=precision)
+        form_path = sim.species_path(0)
+        # the TF/SF wave needs ~40 steps to reach the molecular layer: before that
+        # the molecules see E' = 0 and skip the coupling work, which is not the
+        # regime the step is measured in
+        sim.step(a.preroll)
+        sim.step(a.warmup)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        sm.timing_begin()
-        e0.record(sm.stream)
-        sm.step(a.steps)
-        e1.record(sm.stream)
+        clk = Clocks(local) if clocks else None
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
-        mph, mn, _ = sm.timing_end()
-        mms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
-        Pm = sm.populations()
-        sm.close()
-        del sm
+        sim.timing_begin()
+        ev0.record(sim.stream)   # the stream the library launches on
+        sim.step(a.steps)
+        ev1.record(sim.stream)
+        torch.cuda.synchronize()
+        ph, nst, nlaunch = sim.timing_end()
+        cl = clk.stop() if clk else None
+        ms_ = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+        if dist:
+            dist.barrier()
+        Pf = sim.populations()
+        nerr = float(np.abs(Pf.sum(axis=1) + sim.dissociation()[0].sum(axis=1) - 1.0).max())
+        sim.close()
+        del sim
         torch.cuda.empty_cache()
-        mixed = {"value": job_rate(wl.n_molecules * a.steps, world, mms / 1e3), "unit": UNIT,
-                 "ms_per_step": mms / a.steps, "kinetic_ms_per_step": mph[4] / max(mn, 1),
-                 "populations_max_abs_diff_vs_plain": float(np.abs(Pm - P).max()),
-                 "stated_error_vs_fp64": "populations 6e-6 abs, dipoles 6e-6 rel after 300 strongly driven "
-                                         "steps; norm drift 2.8e-5 in 2000 steps (plain FP32: ~1e-7, 1.9e-6)"}
+        return {"ms": ms_, "phases": ph, "nsteps": nst, "launches": nlaunch, "clocks": cl, "P": Pf,
+                "norm_err": nerr, "path": form_path}
+
+    main_form = time_form(path, B.MS_PREC_FP32, clocks=True)
+    ms, phases, nsteps, launches = main_form["ms"], main_form["phases"], main_form["nsteps"], main_form["launches"]
+    cl, P, norm_err = main_form["clocks"], main_form["P"], main_form["norm_err"]
+    fused = main_form["path"] == B.MS_MOL_FUSED
+
+    def form_entry(f):
+        return {"value": job_rate(wl.n_molecules * a.steps, world, f["ms"] / 1e3), "unit": UNIT,
+                "ms_per_step": f["ms"] / a.steps,
+                "molecular_step_ms": f["phases"][1] / max(f["nsteps"], 1),
+                "layout": "fused" if f["path"] == B.MS_MOL_FUSED else "streaming",
+                "populations_max_abs_diff_vs_default": float(np.abs(f["P"] - P).max())}
+
+    # the other forms of the same workload: the streaming layout (FP32) and the
+    # mixed form (kinetic pass as a split-BF16 tensor-core GEMM, streaming layout)
+    other = {}
+    if not a.no_mixed:
+        if fused:
+            other["plain_fp32_streaming"] = form_entry(time_form(B.MS_MOL_STREAMING, B.MS_PREC_FP32))
+        if B.mixed_supported(wl):
+            mixed = form_entry(time_form(B.MS_MOL_STREAMING, B.MS_PREC_MIXED_BF16X3))
+            mixed["stated_error_vs_fp64"] = ("populations 6e-6 abs, dipoles 6e-6 rel after 300 strongly driven "
+                                             "steps; norm drift 2.8e-5 in 2000 steps (plain FP32: ~1e-7, 1.9e-6)")
+            other["mixed_bf16x3"] = mixed
 
     sec = ms / 1e3
     value = job_rate(wl.n_molecules * a.steps, world, sec)
@@ -297,25 +299,33 @@ def main():
     state = 16 * sp.nr * sp.nrot                       # FP32 state of one molecule (bytes)
     per_step = lambda k: phases[k] / max(nsteps, 1)    # ms per step of one timed phase
     peak, peak_src = _peaks()
-    # dominant kernel: the R-space pass (stage 2), one launch per step; its own
-    # minimum traffic in the streaming form is s and d2 read, s' written, plus
-    # the per-molecule records (field 16 B, rotation 36 B, dipole 3x8 read +
-    # 2x3x8 written, populations 16, absorbed norm 2x16)
-    rs_bytes = (3 * state + 168) * wl.n_molecules
+    records = 168  # per molecule: field 16 B, rotation 36, dipole 3x8 read + 2x3x8 written, populations 16,
+    #                absorbed norm 2x16
+    if fused:
+        # dominant kernel: the fused molecular step (stage 2), one launch per step;
+        # the state read and written once
+        rs_bytes = (2 * state + records) * wl.n_molecules
+        kernel = f"mol_rpoint_kernel<{sp.jmax},{sp.nr},fused>"
+        note = "algorithmic bytes of the fused molecular step: the state read and written once, 168 B of records"
+        roof_kin = None
+    else:
+        # dominant kernel: the R-space pass (stage 2); in the streaming form it reads
+        # s and d2 and writes s'
+        rs_bytes = (3 * state + records) * wl.n_molecules
+        kernel = f"mol_rpoint_kernel<{sp.jmax},{sp.nr}>" if sp.jmax <= 4 else f"R-space pass <{sp.nr}>"
+        note = "algorithmic bytes of the R-space kernel: state and d2 read, new state written, 168 B of records"
+        # the kinetic pass (stage 1: field records + kinetic kernel): s read, d2 written
+        kin_bytes = (2 * state + 16) * wl.n_molecules
+        kin_ms = per_step(4)
+        roof_kin = {"bound": "hbm", "achieved": kin_bytes / (kin_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                    "frac": kin_bytes / (kin_ms / 1e3) / 1e9 / peak, "kernel": f"mol_kinetic_kernel<{sp.nr}>",
+                    "bytes_per_launch": kin_bytes, "ms_per_launch": kin_ms}
     rs_ms = per_step(5)
-    kernel = f"mol_rpoint_kernel<{sp.jmax},{sp.nr}>" if sp.jmax <= 4 else f"R-space pass <{sp.nr}>"
     roof = {"bound": "hbm", "achieved": rs_bytes / (rs_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
             "frac": rs_bytes / (rs_ms / 1e3) / 1e9 / peak,
-            "traffic": _kernel_traffic("mol_rpoint_kernel"), "kernel": kernel,
-            "bytes_per_launch": rs_bytes, "ms_per_launch": rs_ms, "peak_source": peak_src,
-            "note": "algorithmic bytes of the R-space kernel: state and d2 read, new state written, "
-                    "168 B of per-molecule records"}
-    # the kinetic pass (stage 1: field records + kinetic kernel): s read, d2 written
-    kin_bytes = (2 * state + 16) * wl.n_molecules
-    kin_ms = per_step(4)
-    roof_kin = {"bound": "hbm", "achieved": kin_bytes / (kin_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
-                "frac": kin_bytes / (kin_ms / 1e3) / 1e9 / peak, "kernel": f"mol_kinetic_kernel<{sp.nr}>",
-                "bytes_per_launch": kin_bytes, "ms_per_launch": kin_ms}
+            "traffic": _kernel_traffic("mol_rpoint_kernel_fused" if fused else "mol_rpoint_kernel"),
+            "kernel": kernel, "bytes_per_launch": rs_bytes, "ms_per_launch": rs_ms, "peak_source": peak_src,
+            "note": note}
     # the whole molecular step against the method's minimum: the state read
     # and written once per step plus about 40 B of field and observables
     step_bytes = (2 * state + 40) * wl.n_molecules
@@ -361,8 +371,8 @@ def main():
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
                 "clocks": cl, "norm_bookkeeping_max_err": norm_err,
                 "forms": {"plain_fp32": {"value": value, "unit": UNIT, "ms_per_step": ms / a.steps,
-                                         "kinetic_ms_per_step": phases[4] / nsteps},
-                          "mixed_bf16x3": mixed}}
+                                         "molecular_step_ms": phases[1] / nsteps,
+                                         "layout": "fused" if fused else "streaming"}, **other}}
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -66,12 +66,15 @@ enum { MS_BC_PML = 0, MS_BC_PERIODIC = 1 };
 enum { MS_PREC_FP32 = 0, MS_PREC_MIXED_BF16X3 = 1 };
 enum { MS_DRIVE_FDTD = 0, MS_DRIVE_PRESCRIBED = 1 };
 enum { MS_FIELD_E = 0, MS_FIELD_H = 1 };
-/* Molecular kernel layout: MS_MOL_AUTO picks per species; MS_MOL_FUSED keeps
- * each molecule's state in shared memory for the whole step (species whose
- * state fits, up to J = 8 at N_r = 64); MS_MOL_STREAMING runs the kinetic
- * pass over blocks of rows into a device scratch buffer of the state's size
- * and then streams state and scratch through the R-space pass (any species
- * up to J = 16). */
+/* Molecular kernel layout.  MS_MOL_FUSED keeps each molecule's state in
+ * shared memory for the whole step, so the state is read and written once
+ * per step (species whose state fits, up to J = 8 at N_r = 64).
+ * MS_MOL_STREAMING runs the kinetic pass over blocks of rows into a device
+ * scratch buffer of the state's size, then streams state and scratch
+ * through the R-space pass (any species up to J = 16, and the mixed
+ * precision form).  MS_MOL_AUTO picks the fused form for FP32 species with
+ * J <= 4 at N_r = 128 (its point-resident kernel), else the streaming
+ * form. */
 enum { MS_MOL_AUTO = 0, MS_MOL_FUSED = 1, MS_MOL_STREAMING = 2 };
 
 /* Grid and source.  dt must satisfy dt <= dx/(sqrt(3) c) (checked).
@@ -281,6 +284,11 @@ ms_status ms_timing_end(ms_sim* sim, double out[6], int64_t* steps, int64_t* lau
  * MS_EINVAL for tries out of range, MS_ENOMEM / MS_ECUDA on runtime errors.
  * Needs no handle; allocates one int of device memory. */
 ms_status ms_check_bounded_wait(int32_t tries);
+
+/* The molecular kernel layout a species runs in (MS_MOL_FUSED or
+ * MS_MOL_STREAMING, after MS_MOL_AUTO resolved it); MS_EINVAL for a NULL
+ * handle or a species index out of range. */
+int32_t ms_species_path(const ms_sim* sim, int32_t species);
 
 /* Device memory held by the simulation, in bytes. */
 size_t ms_device_bytes(const ms_sim* sim);

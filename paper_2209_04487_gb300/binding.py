@@ -83,6 +83,7 @@ def _load() -> C.CDLL:
         "ms_record_local_fields": (C.c_int, [C.c_void_p, P(C.c_int64), C.c_int64, P(C.c_float), C.c_int64]),
         "ms_save": (C.c_int, [C.c_void_p, C.c_char_p]),
         "ms_check_bounded_wait": (C.c_int, [C.c_int32]),
+        "ms_species_path": (C.c_int32, [C.c_void_p, C.c_int32]),
         "ms_load": (C.c_int, [C.c_void_p, C.c_char_p]),
         "ms_device_bytes": (C.c_size_t, [C.c_void_p]),
         "ms_timing_begin": (C.c_int, [C.c_void_p]),
@@ -103,7 +104,7 @@ LIB = _load()
 EXPORTED = ("ms_create", "ms_step", "ms_step_noalloc", "ms_step_count", "ms_read_fields", "ms_write_fields",
             "ms_read_populations", "ms_read_dissociation", "ms_read_dipoles",
             "ms_set_prescribed_field", "ms_set_replay_field", "ms_record_local_fields", "ms_save", "ms_load",
-            "ms_check_bounded_wait", "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
+            "ms_check_bounded_wait", "ms_species_path", "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
             "ms_destroy", "ms_status_string")
 
 
@@ -294,6 +295,10 @@ class Simulation:
         ln = C.c_int64()
         _check(LIB.ms_timing_end(self.h, out, C.byref(st), C.byref(ln)), "ms_timing_end")
         return list(out), st.value, ln.value
+
+    def species_path(self, species: int = 0) -> int:
+        """MS_MOL_FUSED or MS_MOL_STREAMING: the layout the species runs in."""
+        return int(LIB.ms_species_path(self.h, species))
 
     @property
     def device_bytes(self) -> int:

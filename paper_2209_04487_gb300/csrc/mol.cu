@@ -1233,15 +1233,22 @@ __device__ __forceinline__ void dipole_rows(const V& gv, const V& ev, float2& ac
   }
 }
 
-template <int J, int NR>
+// FUSED: the kinetic pass runs here too (the fused form, N_r = 128): the
+// state is staged once into D and transformed in place into d2 = (T - 1) s by
+// the shared-memory FFT, while a second copy of s (an L2 hit) fills X.
+// Otherwise d2 comes from the kinetic kernel's scratch.
+template <int J, int NR, bool FUSED>
 __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
     mol_rpoint_kernel(SpeciesDev sp, MolDev md, int* err) {
   constexpr int NROT = (J + 1) * (J + 1), NT = 2 * NR, NW = NT / 32;
   constexpr unsigned kStateBytes = 2u * NROT * NR * sizeof(float2);  // one molecule's state
+  static_assert(!FUSED || NT == FFTShape<NR>::THREADS, "the fused form runs the FFT with every thread");
   extern __shared__ __align__(16) float4 smem4[];
   float2* X = reinterpret_cast<float2*>(smem4);  // [2 NROT][NR]: s, then eta and the series terms, then s'
   float2* D = X + 2 * NROT * NR;                 // [2 NROT][NR]: d2
-  __shared__ __align__(8) unsigned long long s_bar[1];
+  float2* s_tw = D + 2 * NROT * NR;              // fused: [N2][N1] FFT twiddles
+  float2* s_kd = s_tw + NR;                      // fused: [NR] kinetic phase deltas
+  __shared__ __align__(8) unsigned long long s_bar[2];
   __shared__ float s_rot[9];
   __shared__ double s_mu[3], s_abs[2];
   __shared__ float s_red[NW][9];
@@ -1259,13 +1266,25 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
   const float2* vdp = sp.vdelta + sf * (J + 1) * NR + p;
   const float2* vhp = sp.vhalf + sf * (J + 1) * NR + p;
 
-  // the molecule's state and d2, one bulk copy each (contiguous in global memory)
+  // the molecule's state (and d2), one bulk copy each (contiguous in global memory)
   if (t == 0) {
     mbar_init(&s_bar[0], 1);
+    mbar_init(&s_bar[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    mbar_expect_tx(&s_bar[0], 2 * kStateBytes);
-    bulk_g2s(X, sp.psi + mol0, kStateBytes, &s_bar[0]);
-    bulk_g2s(D, sp.d2 + mol0, kStateBytes, &s_bar[0]);
+    if (FUSED) {
+      mbar_expect_tx(&s_bar[0], kStateBytes);
+      bulk_g2s(D, sp.psi + mol0, kStateBytes, &s_bar[0]);
+    } else {
+      mbar_expect_tx(&s_bar[0], 2 * kStateBytes);
+      bulk_g2s(X, sp.psi + mol0, kStateBytes, &s_bar[0]);
+      bulk_g2s(D, sp.d2 + mol0, kStateBytes, &s_bar[0]);
+    }
+  }
+  if (FUSED) {
+    for (int q = t; q < NR; q += NT) {
+      s_tw[q] = __ldg(&sp.twiddle[q]);
+      s_kd[q] = __ldg(&sp.kdelta[q]);
+    }
   }
   if (t >= 32 && t < 41) s_rot[t - 32] = md.rot[9 * (long long)m + (t - 32)];
   else if (t >= 64 && t < 67) s_mu[t - 64] = md.mu[3 * (long long)m + (t - 64)];
@@ -1280,13 +1299,21 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
     vh[j] = __ldg(vhp + j * NR);
   }
   __syncthreads();  // the barrier is initialised
-  {
-    const bool ok = mbar_wait_sleep(&s_bar[0], 0);
-    if (!__syncthreads_and(ok)) {
-      if (t == 0) atomicOr(err, kErrTimeout);
-      if (!ok) mbar_wait_sleep(&s_bar[0], 0);
-      return;
+  auto wait_all = [&](int id) -> bool {
+    const bool ok = mbar_wait_sleep(&s_bar[id], 0);
+    if (__syncthreads_and(ok)) return true;
+    if (t == 0) atomicOr(err, kErrTimeout);
+    if (!ok) mbar_wait_sleep(&s_bar[id], 0);
+    return false;
+  };
+  if (!wait_all(0)) return;
+  if (FUSED) {
+    if (t == 0) {  // s again into X (the lines were just read), while the FFT runs on D
+      mbar_expect_tx(&s_bar[1], kStateBytes);
+      bulk_g2s(X, sp.psi + mol0, kStateBytes, &s_bar[1]);
     }
+    kinetic_pass<NR>(D, 2 * NROT, s_kd, s_tw);  // D <- d2 = (T - 1) s
+    if (!wait_all(1)) return;
   }
   // ---- eta = V^{1/2} u, u = s + d2, over this thread's own rows of the state
   if (nterms > 0) {
@@ -1410,26 +1437,29 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
   }
 }
 
-template <int J, int NR>
+template <int J, int NR, bool FUSED>
 static void launch_rpoint_jn(const SpeciesDev& sp, const MolDev& md, int* err, cudaStream_t s) {
   constexpr int NROT = (J + 1) * (J + 1);
-  const size_t smem = (size_t)4 * NROT * NR * sizeof(float2);
-  auto k = mol_rpoint_kernel<J, NR>;
+  const size_t smem = (size_t)4 * NROT * NR * sizeof(float2) + (FUSED ? 2 * NR * sizeof(float2) : 0);
+  auto k = mol_rpoint_kernel<J, NR, FUSED>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   k<<<sp.nmol, 2 * NR, smem, s>>>(sp, md, err);
 }
 
-template <int NR>
+template <int NR, bool FUSED = false>
 static void launch_rpoint_n(const SpeciesDev& sp, const MolDev& md, int* err, cudaStream_t s) {
   switch (sp.jmax) {
-    case 0: launch_rpoint_jn<0, NR>(sp, md, err, s); break;
-    case 1: launch_rpoint_jn<1, NR>(sp, md, err, s); break;
-    case 2: launch_rpoint_jn<2, NR>(sp, md, err, s); break;
-    case 3: launch_rpoint_jn<3, NR>(sp, md, err, s); break;
-    case 4: launch_rpoint_jn<4, NR>(sp, md, err, s); break;
+    case 0: launch_rpoint_jn<0, NR, FUSED>(sp, md, err, s); break;
+    case 1: launch_rpoint_jn<1, NR, FUSED>(sp, md, err, s); break;
+    case 2: launch_rpoint_jn<2, NR, FUSED>(sp, md, err, s); break;
+    case 3: launch_rpoint_jn<3, NR, FUSED>(sp, md, err, s); break;
+    case 4: launch_rpoint_jn<4, NR, FUSED>(sp, md, err, s); break;
   }
 }
+
+// The fused form of a species runs the point-resident kernel when it applies
+static bool fused_point(const SpeciesDev& sp) { return sp.path == MS_MOL_FUSED && sp.jmax <= 4 && sp.nr == 128; }
 }  // namespace ms
 
 // ----------------------------------------------------------------------------
@@ -1930,7 +1960,11 @@ __global__ void __launch_bounds__(256, 1) mol_kinetic_tc_kernel(SpeciesDev sp, l
 template <int NR>
 static int launch_stage1_t(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
                            cudaStream_t s) {
-  if (sp.path == MS_MOL_FUSED) return 0;
+  if (sp.path == MS_MOL_FUSED) {
+    if (!fused_point(sp)) return 0;
+    mol_field_kernel<<<(sp.nmol + 127) / 128, 128, 0, s>>>(sp, md, g, prescribed, err);
+    return 1;
+  }
   int n = 0;
   if (sp.jmax <= 4) {
     mol_field_kernel<<<(sp.nmol + 127) / 128, 128, 0, s>>>(sp, md, g, prescribed, err);
@@ -1964,6 +1998,12 @@ static int launch_stage2_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
   const bool fused = sp.path == MS_MOL_FUSED;
   const StepShape sh = step_shape(NR, sp.nrot, fused);
   if (fused) {
+    if constexpr (NR == 128) {
+      if (fused_point(sp)) {
+        launch_rpoint_n<NR, true>(sp, md, err, s);
+        return 1;
+      }
+    }
     launch_step_tt<NR, true, 12>(sp, md, g, prescribed, err, sh, s);
     return 1;
   }

@@ -296,7 +296,11 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   ms::SpeciesDev& sp = s->sp[si];
   const int nr = d.nr, J = d.jmax, nrot = (J + 1) * (J + 1);
   // layout: the streaming form unless the caller asks for the fused one
-  sp.path = path == MS_MOL_FUSED ? MS_MOL_FUSED : MS_MOL_STREAMING;
+  // MS_MOL_AUTO: the fused form where its point-resident kernel applies (FP32,
+  // J <= 4, N_r = 128: one read and one write of the state per step), else
+  // the streaming form
+  const bool auto_fused = path == MS_MOL_AUTO && !mixed && d.jmax <= 4 && d.nr == 128;
+  sp.path = (path == MS_MOL_FUSED || auto_fused) ? MS_MOL_FUSED : MS_MOL_STREAMING;
   sp.nr = nr;
   sp.jmax = J;
   sp.nrot = nrot;
@@ -374,15 +378,12 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   for (int a = 0; a < nr; ++a) row0[a] = make_float2((float)phi0[a].real(), (float)phi0[a].imag());
   MS_TRY(zeros(s, &sp.psi, per * ids.size()));
   sp.d2 = nullptr;
-  sp.fld = nullptr;
+  MS_TRY(zeros(s, &sp.fld, ids.size()));  // per-molecule frame-field records
   if (mixed) {
     const std::vector<uint16_t> kp = mixed_kinetic_planes(nr, dR, dtau, mu);
     MS_TRY(upload(s, (uint16_t**)&sp.kpl, kp.data(), kp.size()));
   }
-  if (sp.path == MS_MOL_STREAMING) {
-    MS_TRY(zeros(s, &sp.d2, per * ids.size()));
-    MS_TRY(zeros(s, &sp.fld, ids.size()));
-  }
+  if (sp.path == MS_MOL_STREAMING) MS_TRY(zeros(s, &sp.d2, per * ids.size()));
   float2* d_row0 = nullptr;
   MS_TRY(upload(s, &d_row0, row0.data(), row0.size()));
   if (ms::launch_broadcast_row(sp.psi, d_row0, nr, per, (long long)ids.size(), s->stream) != cudaSuccess)
@@ -1197,6 +1198,11 @@ ms_status ms_check_bounded_wait(int32_t tries) {
   cudaFree(d_flag);
   if (st != MS_OK) return st;
   return (flag & ms::kErrTimeout) ? MS_ETIMEOUT : MS_OK;
+}
+
+int32_t ms_species_path(const ms_sim* s, int32_t species) {
+  if (!s || species < 0 || species >= s->nspecies) return MS_EINVAL;
+  return s->sp[species].path;
 }
 
 size_t ms_device_bytes(const ms_sim* s) { return s ? s->bytes : 0; }
