@@ -233,10 +233,10 @@ def main():
     wl = _workload(a.molecules)
     path = {"auto": B.MS_MOL_AUTO, "fused": B.MS_MOL_FUSED, "streaming": B.MS_MOL_STREAMING}[a.mol_path]
 
-    def time_form(mol_path, precision, clocks=False):
+    def time_form(mol_path, precision, clocks=False, state_form=0):
         """Preroll, warm-up, then a.steps timed steps of one form (CUDA events on
         the library's stream, max over ranks) and its phase timings."""
-        sim = B.Simulation(wl, mol_path=mol_path, precision=precision)
+        sim = B.Simulation(wl, mol_path=mol_path, precision=precision, state_form=state_form)
         form_path = sim.species_path(0)
         # the TF/SF wave needs ~40 steps to reach the molecular layer: before that
         # the molecules see E' = 0 and skip the coupling work, which is not the
@@ -286,6 +286,11 @@ def main():
     if not a.no_mixed:
         if fused:
             other["plain_fp32_streaming"] = form_entry(time_form(B.MS_MOL_STREAMING, B.MS_PREC_FP32))
+        if all(sp_.jmax <= 4 for sp_ in wl.species):
+            par = form_entry(time_form(path, B.MS_PREC_FP32, state_form=B.MS_STATE_PARITY))
+            par["note"] = ("parity-reduced state: only (ground, even j) and (excited, odd j) rows, the rows the "
+                           "j = 0 start populates; same results as the full state")
+            other["plain_fp32_parity_reduced"] = par
         if B.mixed_supported(wl):
             mixed = form_entry(time_form(B.MS_MOL_STREAMING, B.MS_PREC_MIXED_BF16X3))
             mixed["stated_error_vs_fp64"] = ("populations 6e-6 abs, dipoles 6e-6 rel after 300 strongly driven "

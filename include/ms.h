@@ -76,6 +76,14 @@ enum { MS_FIELD_E = 0, MS_FIELD_H = 1 };
  * J <= 4 at N_r = 128 (its point-resident kernel), else the streaming
  * form. */
 enum { MS_MOL_AUTO = 0, MS_MOL_FUSED = 1, MS_MOL_STREAMING = 2 };
+/* Stored rows of each molecule's state.  MS_STATE_FULL: both surfaces carry
+ * every channel (j, m), j <= J.  MS_STATE_PARITY: only (ground, even j) and
+ * (excited, odd j), the only rows the dynamics populate from the j = 0
+ * ground-state start (each coupling changes j by one and swaps the
+ * surfaces), which halves the state and the work.  Results are those of the
+ * full state.  Parity-reduced species need J <= 4, and the fused layout
+ * only at N_r = 128 (MS_EUNSUPPORTED otherwise). */
+enum { MS_STATE_FULL = 0, MS_STATE_PARITY = 1 };
 
 /* Grid and source.  dt must satisfy dt <= dx/(sqrt(3) c) (checked).
  * src_plane_z: absolute z index of the TF/SF plane (total field for
@@ -147,6 +155,7 @@ typedef struct {
   void* alloc_ctx;
   void* stream;
   int32_t mol_path;     /* MS_MOL_AUTO, MS_MOL_FUSED or MS_MOL_STREAMING */
+  int32_t state_form;   /* MS_STATE_FULL or MS_STATE_PARITY */
 } ms_options;
 
 /* Create a simulation: validates the descriptors, builds the species

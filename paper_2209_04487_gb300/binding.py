@@ -21,6 +21,7 @@ MS_BC_PML, MS_BC_PERIODIC = 0, 1
 MS_PREC_FP32, MS_PREC_MIXED_BF16X3 = 0, 1
 MS_DRIVE_FDTD, MS_DRIVE_PRESCRIBED = 0, 1
 MS_FIELD_E, MS_FIELD_H = 0, 1
+MS_STATE_FULL, MS_STATE_PARITY = 0, 1
 MS_MOL_AUTO, MS_MOL_FUSED, MS_MOL_STREAMING = 0, 1, 2
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -57,7 +58,7 @@ class MoleculesDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mol_substeps", C.c_int32), ("drive", C.c_int32),
                 ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p),
-                ("mol_path", C.c_int32)]
+                ("mol_path", C.c_int32), ("state_form", C.c_int32)]
 
 
 def _load() -> C.CDLL:
@@ -164,7 +165,7 @@ class Simulation:
 
     def __init__(self, wl, *, drive: int = MS_DRIVE_FDTD, precision: int = MS_PREC_FP32,
                  with_molecules: bool = True, use_torch: bool = True, stream=None,
-                 mol_path: int = MS_MOL_AUTO, allocator=None):
+                 mol_path: int = MS_MOL_AUTO, allocator=None, state_form: int = 0):
         self.wl = wl
         self._keep = []
         src = np.ascontiguousarray(wl.src, np.float64) if wl.src_k >= 0 else None
@@ -193,6 +194,7 @@ class Simulation:
         opts.mol_substeps = 1
         opts.drive = drive
         opts.mol_path = mol_path
+        opts.state_form = state_form
         self.stream = None
         if use_torch:
             import torch

@@ -1162,13 +1162,53 @@ __global__ void mol_field_kernel(SpeciesDev sp, MolDev md, Grid g, int prescribe
   sp.fld[lm] = make_float4(th * Ep[2], 0.5f * th * Ep[0], 0.5f * th * Ep[1], __int_as_float(nt));
 }
 
-// i (theta/n) (M in)_c for channel c = (j, m) of a basis of size J, M = E'_z Z +
-// (E'_x - i E'_y)/2 S+ + (E'_x + i E'_y)/2 S- (the molecule-frame coupling);
-// f = (theta E'_z, theta E'_x/2, theta E'_y/2)
-template <int J, int C, class V>
+// Row layout of a molecule's state.  Full: both surfaces carry every channel
+// c = j^2 + j + m, c < (J+1)^2, in channel order.  Parity-reduced: starting
+// from j = 0 on the ground surface, the couplings (j -> j +- 1, surfaces
+// swapped) only ever populate (ground, even j) and (excited, odd j), so only
+// those rows are stored: ground rows are the even-j channels, excited rows
+// the odd-j channels, each in channel order.
+template <int J, bool PAR>
+struct Rows {
+  static constexpr int NROT = (J + 1) * (J + 1);
+  static constexpr int count(int q) {  // channels of j parity q up to J
+    int n = 0;
+    for (int j = q; j <= J; j += 2) n += 2 * j + 1;
+    return n;
+  }
+  static constexpr int NG = PAR ? count(0) : NROT;  // ground rows
+  static constexpr int NE = PAR ? count(1) : NROT;  // excited rows
+  static constexpr int ROWS = NG + NE;
+  static constexpr int N(int sf) { return sf ? NE : NG; }
+  static constexpr int base(int sf) { return sf ? NG : 0; }  // first row of surface sf
+  // channel stored in row r of surface sf
+  static constexpr int chan(int sf, int r) {
+    if (!PAR) return r;
+    for (int j = sf; j <= J; j += 2) {
+      if (r < 2 * j + 1) return j * j + r;
+      r -= 2 * j + 1;
+    }
+    return -1;
+  }
+  // row of surface sf holding channel c (-1: c outside the basis or not stored)
+  static constexpr int row(int sf, int c) {
+    if (c < 0) return -1;
+    if (!PAR) return c;
+    const int j = ch_j(c);
+    if ((j & 1) != sf) return -1;
+    int r = 0;
+    for (int jj = sf; jj < j; jj += 2) r += 2 * jj + 1;
+    return r + (c - j * j);
+  }
+};
+
+// i (theta/n) (M in) for row R of surface SF, M = E'_z Z + (E'_x - i E'_y)/2 S+
+// + (E'_x + i E'_y)/2 S- (the molecule-frame coupling), `in` the other
+// surface's rows; f = (theta E'_z, theta E'_x/2, theta E'_y/2)
+template <int J, bool PAR, int SF, int R, class V>
 __device__ __forceinline__ float2 coupling_row(const V& in, float fz, float fx, float fy, float cn) {
-  constexpr int j = ch_j(C), mm = ch_m(C);
-  constexpr bool up = j < J;
+  using L = Rows<J, PAR>;
+  constexpr int C = L::chan(SF, R), j = ch_j(C), mm = ch_m(C);
   float2 az = make_float2(0.f, 0.f), ap = az, am = az;
   auto mac = [&](float2& a, float cf, auto ni) {
     constexpr int q = decltype(ni)::value;
@@ -1177,15 +1217,17 @@ __device__ __forceinline__ float2 coupling_row(const V& in, float fz, float fx, 
       a.y = fmaf(cf, in[q].y, a.y);
     }
   };
-  if constexpr (up) {
-    mac(az, c_zu(j, mm), std::integral_constant<int, ch_of(j + 1, mm, J)>());
-    mac(ap, c_pu(j, mm), std::integral_constant<int, ch_of(j + 1, mm - 1, J)>());
-    mac(am, c_mu(j, mm), std::integral_constant<int, ch_of(j + 1, mm + 1, J)>());
+  if constexpr (j < J) {
+    mac(az, c_zu(j, mm), std::integral_constant<int, L::row(1 - SF, ch_of(j + 1, mm, J))>());
+    mac(ap, c_pu(j, mm), std::integral_constant<int, L::row(1 - SF, ch_of(j + 1, mm - 1, J))>());
+    mac(am, c_mu(j, mm), std::integral_constant<int, L::row(1 - SF, ch_of(j + 1, mm + 1, J))>());
   }
   if constexpr (j > 0) {
-    mac(az, c_zd(j, mm), std::integral_constant<int, c_zd(j, mm) != 0.f ? ch_of(j - 1, mm, J) : -1>());
-    mac(ap, c_pd(j, mm), std::integral_constant<int, c_pd(j, mm) != 0.f ? ch_of(j - 1, mm - 1, J) : -1>());
-    mac(am, c_md(j, mm), std::integral_constant<int, c_md(j, mm) != 0.f ? ch_of(j - 1, mm + 1, J) : -1>());
+    mac(az, c_zd(j, mm), std::integral_constant<int, c_zd(j, mm) != 0.f ? L::row(1 - SF, ch_of(j - 1, mm, J)) : -1>());
+    mac(ap, c_pd(j, mm),
+        std::integral_constant<int, c_pd(j, mm) != 0.f ? L::row(1 - SF, ch_of(j - 1, mm - 1, J)) : -1>());
+    mac(am, c_md(j, mm),
+        std::integral_constant<int, c_md(j, mm) != 0.f ? L::row(1 - SF, ch_of(j - 1, mm + 1, J)) : -1>());
   }
   // a = fz Z-part + fx (S+ + S-) - i fy (S+ - S-)
   const float bx = ap.x + am.x, by = ap.y + am.y, cx = ap.x - am.x, cy = ap.y - am.y;
@@ -1194,11 +1236,12 @@ __device__ __forceinline__ float2 coupling_row(const V& in, float fz, float fx, 
   return make_float2(-cn * ay, cn * ax);
 }
 
-// Dipole sums over rows [C0, C1): sum_c conj(g_c) (A e)_c for A = S+, S-, Z
-// (g the ground vector, e the excited one at one radial point)
-template <int J, int C, class V>
-__device__ __forceinline__ void dipole_row(const V& gv, const V& ev, float2& accP, float2& accM, float2& accZ) {
-  constexpr int j = ch_j(C), mm = ch_m(C);
+// Dipole sums of ground rows [R0, R1): sum_c conj(g_c) (A e)_c for A = S+, S-,
+// Z (g the ground rows, e the excited rows at one radial point)
+template <int J, bool PAR, int R, class V, class W>
+__device__ __forceinline__ void dipole_row(const V& gv, const W& ev, float2& accP, float2& accM, float2& accZ) {
+  using L = Rows<J, PAR>;
+  constexpr int C = L::chan(0, R), j = ch_j(C), mm = ch_m(C);
   float2 wP = make_float2(0.f, 0.f), wZ = wP, wM = wP;
   auto mac = [&](float2& a, float cf, auto ni) {
     constexpr int q = decltype(ni)::value;
@@ -1208,16 +1251,16 @@ __device__ __forceinline__ void dipole_row(const V& gv, const V& ev, float2& acc
     }
   };
   if constexpr (j < J) {
-    mac(wZ, c_zu(j, mm), std::integral_constant<int, ch_of(j + 1, mm, J)>());
-    mac(wP, c_pu(j, mm), std::integral_constant<int, ch_of(j + 1, mm - 1, J)>());
-    mac(wM, c_mu(j, mm), std::integral_constant<int, ch_of(j + 1, mm + 1, J)>());
+    mac(wZ, c_zu(j, mm), std::integral_constant<int, L::row(1, ch_of(j + 1, mm, J))>());
+    mac(wP, c_pu(j, mm), std::integral_constant<int, L::row(1, ch_of(j + 1, mm - 1, J))>());
+    mac(wM, c_mu(j, mm), std::integral_constant<int, L::row(1, ch_of(j + 1, mm + 1, J))>());
   }
   if constexpr (j > 0) {
-    mac(wZ, c_zd(j, mm), std::integral_constant<int, c_zd(j, mm) != 0.f ? ch_of(j - 1, mm, J) : -1>());
-    mac(wP, c_pd(j, mm), std::integral_constant<int, c_pd(j, mm) != 0.f ? ch_of(j - 1, mm - 1, J) : -1>());
-    mac(wM, c_md(j, mm), std::integral_constant<int, c_md(j, mm) != 0.f ? ch_of(j - 1, mm + 1, J) : -1>());
+    mac(wZ, c_zd(j, mm), std::integral_constant<int, c_zd(j, mm) != 0.f ? L::row(1, ch_of(j - 1, mm, J)) : -1>());
+    mac(wP, c_pd(j, mm), std::integral_constant<int, c_pd(j, mm) != 0.f ? L::row(1, ch_of(j - 1, mm - 1, J)) : -1>());
+    mac(wM, c_md(j, mm), std::integral_constant<int, c_md(j, mm) != 0.f ? L::row(1, ch_of(j - 1, mm + 1, J)) : -1>());
   }
-  const float2 gc = gv[C];
+  const float2 gc = gv[R];
   accZ.x += fmaf(gc.x, wZ.x, gc.y * wZ.y);
   accZ.y += fmaf(gc.x, wZ.y, -gc.y * wZ.x);
   accP.x += fmaf(gc.x, wP.x, gc.y * wP.y);
@@ -1225,28 +1268,34 @@ __device__ __forceinline__ void dipole_row(const V& gv, const V& ev, float2& acc
   accM.x += fmaf(gc.x, wM.x, gc.y * wM.y);
   accM.y += fmaf(gc.x, wM.y, -gc.y * wM.x);
 }
-template <int J, int C0, int C1, class V>
-__device__ __forceinline__ void dipole_rows(const V& gv, const V& ev, float2& accP, float2& accM, float2& accZ) {
-  if constexpr (C0 < C1) {
-    dipole_row<J, C0>(gv, ev, accP, accM, accZ);
-    dipole_rows<J, C0 + 1, C1>(gv, ev, accP, accM, accZ);
+template <int J, bool PAR, int R0, int R1, class V, class W>
+__device__ __forceinline__ void dipole_rows(const V& gv, const W& ev, float2& accP, float2& accM, float2& accZ) {
+  if constexpr (R0 < R1) {
+    dipole_row<J, PAR, R0>(gv, ev, accP, accM, accZ);
+    dipole_rows<J, PAR, R0 + 1, R1>(gv, ev, accP, accM, accZ);
   }
 }
 
-// FUSED: the kinetic pass runs here too (the fused form, N_r = 128): the
-// state is staged once into D and transformed in place into d2 = (T - 1) s by
-// the shared-memory FFT, while a second copy of s (an L2 hit) fills X.
-// Otherwise d2 comes from the kinetic kernel's scratch.
-template <int J, int NR, bool FUSED>
-__global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
+// Point-resident R-space pass (and, FUSED, the kinetic pass): one CTA of 2 N_r
+// threads per molecule, thread = (radial point, surface); PAR: parity-reduced
+// rows.  FUSED (N_r = 128): the state is staged once into D and turned in
+// place into d2 = (T - 1) s by the shared-memory FFT, while a second copy of
+// s (an L2 hit) fills X.  Otherwise d2 comes from the kinetic kernel's
+// scratch.  Every CTA barrier sits in code all threads run; the per-surface
+// work between them is compiled once per surface (row counts differ when
+// PAR).
+template <int J, int NR, bool FUSED, bool PAR>
+__global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 : 2) : 1))
     mol_rpoint_kernel(SpeciesDev sp, MolDev md, int* err) {
-  constexpr int NROT = (J + 1) * (J + 1), NT = 2 * NR, NW = NT / 32;
-  constexpr unsigned kStateBytes = 2u * NROT * NR * sizeof(float2);  // one molecule's state
+  using L = Rows<J, PAR>;
+  constexpr int ROWS = L::ROWS, NG = L::NG, NT = 2 * NR, NW = NT / 32;
+  constexpr int RMAX = L::NG > L::NE ? L::NG : L::NE;
+  constexpr unsigned kStateBytes = (unsigned)ROWS * NR * sizeof(float2);  // one molecule's state
   static_assert(!FUSED || NT == FFTShape<NR>::THREADS, "the fused form runs the FFT with every thread");
   extern __shared__ __align__(16) float4 smem4[];
-  float2* X = reinterpret_cast<float2*>(smem4);  // [2 NROT][NR]: s, then eta and the series terms, then s'
-  float2* D = X + 2 * NROT * NR;                 // [2 NROT][NR]: d2
-  float2* s_tw = D + 2 * NROT * NR;              // fused: [N2][N1] FFT twiddles
+  float2* X = reinterpret_cast<float2*>(smem4);  // [ROWS][NR]: s, then eta and the series terms, then s'
+  float2* D = X + ROWS * NR;                     // [ROWS][NR]: d2
+  float2* s_tw = D + ROWS * NR;                  // fused: [N2][N1] FFT twiddles
   float2* s_kd = s_tw + NR;                      // fused: [NR] kinetic phase deltas
   __shared__ __align__(8) unsigned long long s_bar[2];
   __shared__ float s_rot[9];
@@ -1258,11 +1307,12 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
   const int sf = t >= NR, p = t - sf * NR;  // surface (warp-uniform) and radial point
   const int lm = blockIdx.x;
   const int m = sp.mol[lm];
-  const long long mol0 = (long long)lm * 2 * NROT * NR;  // first element of this molecule
-  float2* gs = sp.psi + mol0 + sf * NROT * NR + p;
-  float2* Xo = X + sf * NROT * NR + p;              // own vector
-  const float2* Xt = X + (1 - sf) * NROT * NR + p;  // the other surface's
-  const float2* Do = D + sf * NROT * NR + p;
+  const long long mol0 = (long long)lm * ROWS * NR;  // first element of this molecule
+  const int own0 = sf ? NG : 0, oth0 = sf ? 0 : NG;   // first rows of this and the other surface
+  float2* gs = sp.psi + mol0 + (long long)own0 * NR + p;
+  float2* Xo = X + own0 * NR + p;        // own rows
+  const float2* Xt = X + oth0 * NR + p;  // the other surface's rows
+  const float2* Do = D + own0 * NR + p;
   const float2* vdp = sp.vdelta + sf * (J + 1) * NR + p;
   const float2* vhp = sp.vhalf + sf * (J + 1) * NR + p;
 
@@ -1312,54 +1362,73 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
       mbar_expect_tx(&s_bar[1], kStateBytes);
       bulk_g2s(X, sp.psi + mol0, kStateBytes, &s_bar[1]);
     }
-    kinetic_pass<NR>(D, 2 * NROT, s_kd, s_tw);  // D <- d2 = (T - 1) s
+    kinetic_pass<NR>(D, ROWS, s_kd, s_tw);  // D <- d2 = (T - 1) s
     if (!wait_all(1)) return;
   }
+  // per-surface work: both surfaces share one row list in the full layout
+  auto per_surface = [&](auto&& fn) {
+    if constexpr (PAR) {
+      if (sf == 0) fn(std::integral_constant<int, 0>());
+      else fn(std::integral_constant<int, 1>());
+    } else {
+      fn(std::integral_constant<int, 0>());
+    }
+  };
   // ---- eta = V^{1/2} u, u = s + d2, over this thread's own rows of the state
-  if (nterms > 0) {
-#pragma unroll
-    for (int c = 0; c < NROT; ++c) Xo[c * NR] = cmul(vh[j_of_c(c)], Xo[c * NR] + Do[c * NR]);
-  }
+  auto eta = [&](auto sfc) {
+    constexpr int SF = decltype(sfc)::value;
+    static_for<0, L::N(SF)>([&](auto ri) {
+      constexpr int r = decltype(ri)::value, j = ch_j(L::chan(SF, r));
+      Xo[r * NR] = cmul(vh[j], Xo[r * NR] + Do[r * NR]);
+    });
+  };
+  if (nterms > 0) per_surface(eta);
   __syncthreads();
   // ---- coupling series: S = sum_n (i theta M sigma_x)^n eta / n!
-  float2 sacc[NROT], in[NROT];
+  float2 sacc[RMAX], in[RMAX];
 #pragma unroll
-  for (int c = 0; c < NROT; ++c) sacc[c] = make_float2(0.f, 0.f);
+  for (int r = 0; r < RMAX; ++r) sacc[r] = make_float2(0.f, 0.f);
+  auto term = [&](auto sfc, float cn, bool store) {
+    constexpr int SF = decltype(sfc)::value;
+    static_for<0, L::N(SF)>([&](auto ri) {
+      constexpr int r = decltype(ri)::value;
+      const float2 o = coupling_row<J, PAR, SF, r>(in, f.x, f.y, f.z, cn);
+      sacc[r].x += o.x;
+      sacc[r].y += o.y;
+      if (store) Xo[r * NR] = o;
+    });
+  };
+  const int n_oth = PAR ? (sf ? L::NG : L::NE) : L::NROT;
   for (int n = 1; n <= nterms; ++n) {
 #pragma unroll
-    for (int c = 0; c < NROT; ++c) in[c] = Xt[c * NR];
+    for (int r = 0; r < RMAX; ++r)
+      if (r < n_oth) in[r] = Xt[r * NR];
     __syncthreads();  // every thread has its input: the buffer may be overwritten
     const float cn = 1.f / (float)n;
     const bool store = n < nterms;
-    static_for<0, NROT>([&](auto ci) {
-      constexpr int c = decltype(ci)::value;
-      const float2 o = coupling_row<J, c>(in, f.x, f.y, f.z, cn);
-      sacc[c].x += o.x;
-      sacc[c].y += o.y;
-      if (store) Xo[c * NR] = o;
-    });
+    per_surface([&](auto sfc) { term(sfc, cn, store); });
     if (store) __syncthreads();
   }
   // ---- d1 = (V - 1) u + V^{1/2} S ; mask ; s' = s + (d2 + d1)
   float sn2 = 0.f, absd = 0.f;
-  {
+  auto update = [&](auto sfc) {
+    constexpr int SF = decltype(sfc)::value, NO = L::N(SF);
     // s again (from L2), in two batches each requested in full first; d2 from shared memory
-    constexpr int NB = (NROT + 1) / 2;
+    constexpr int NB = NO > 1 ? (NO + 1) / 2 : 1;
     float2 sb[NB];
-    auto fetch = [&](int c0) {
+    auto fetch = [&](int r0) {
 #pragma unroll
       for (int k = 0; k < NB; ++k)
-        if (c0 + k < NROT) sb[k] = __ldcs(gs + (c0 + k) * NR);
+        if (r0 + k < NO) sb[k] = __ldcs(gs + (r0 + k) * NR);
     };
     fetch(0);
-#pragma unroll
-    for (int c = 0; c < NROT; ++c) {
-      if (c == NB) fetch(NB);
-      const int j = j_of_c(c);
-      const float2 sv = sb[c % NB], dv = Do[c * NR];
+    static_for<0, NO>([&](auto ri) {
+      constexpr int r = decltype(ri)::value, j = ch_j(L::chan(SF, r));
+      if constexpr (r == NB) fetch(NB);
+      const float2 sv = sb[r % NB], dv = Do[r * NR];
       const float2 u = sv + dv;
       float2 d1 = cmul(vd[j], u);
-      if (nterms > 0) d1 = d1 + cmul(vh[j], sacc[c]);
+      if (nterms > 0) d1 = d1 + cmul(vh[j], sacc[r]);
       if (mk < 1.f) {
         const float px = u.x + d1.x, py = u.y + d1.y;
         d1.x = fmaf(mk - 1.f, u.x, mk * d1.x);
@@ -1367,23 +1436,26 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
         absd += (1.f - mk * mk) * fmaf(px, px, py * py);
       }
       const float2 s1 = sv + (dv + d1);
-      __stcs(gs + c * NR, s1);
+      __stcs(gs + r * NR, s1);
       sn2 += fmaf(s1.x, s1.x, s1.y * s1.y);
-      sacc[c] = s1;  // the new state of this surface, kept for the dipole
-      Xo[c * NR] = s1;
-    }
-  }
+      sacc[r] = s1;  // the new state of this surface, kept for the dipole
+      Xo[r * NR] = s1;
+    });
+  };
+  per_surface(update);
   __syncthreads();
-  // ---- dipole in the molecule frame: sum_c conj(g_c) (A e)_c for A = Z, S+, S-;
-  // rows c < NH on the ground-surface threads, the rest on the excited ones
+  // ---- dipole in the molecule frame: sum over ground rows of conj(g_c) (A e)_c
+  // for A = Z, S+, S-; ground rows [0, NH) on the ground-surface threads, the
+  // rest on the excited ones
   float dP = 0.f, dQ = 0.f, dZ = 0.f;
   {
-    constexpr int NH = (NROT + 1) / 2;
+    constexpr int NH = (NG + 1) / 2;
 #pragma unroll
-    for (int c = 0; c < NROT; ++c) in[c] = Xt[c * NR];
+    for (int r = 0; r < RMAX; ++r)
+      if (r < n_oth) in[r] = Xt[r * NR];
     float2 accP = make_float2(0.f, 0.f), accM = accP, accZ = accP;
-    if (sf == 0) dipole_rows<J, 0, NH>(sacc, in, accP, accM, accZ);
-    else dipole_rows<J, NH, NROT>(in, sacc, accP, accM, accZ);
+    if (sf == 0) dipole_rows<J, PAR, 0, NH>(sacc, in, accP, accM, accZ);
+    else dipole_rows<J, PAR, NH, NG>(in, sacc, accP, accM, accZ);
     dP = accP.x + accM.x;
     dQ = accP.y - accM.y;
     dZ = 2.f * accZ.x;
@@ -1437,14 +1509,19 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? 2 : 1))
   }
 }
 
-template <int J, int NR, bool FUSED>
-static void launch_rpoint_jn(const SpeciesDev& sp, const MolDev& md, int* err, cudaStream_t s) {
-  constexpr int NROT = (J + 1) * (J + 1);
-  const size_t smem = (size_t)4 * NROT * NR * sizeof(float2) + (FUSED ? 2 * NR * sizeof(float2) : 0);
-  auto k = mol_rpoint_kernel<J, NR, FUSED>;
+template <int J, int NR, bool FUSED, bool PAR>
+static void launch_rpoint_jnp(const SpeciesDev& sp, const MolDev& md, int* err, cudaStream_t s) {
+  constexpr int ROWS = Rows<J, PAR>::ROWS;
+  const size_t smem = (size_t)2 * ROWS * NR * sizeof(float2) + (FUSED ? 2 * NR * sizeof(float2) : 0);
+  auto k = mol_rpoint_kernel<J, NR, FUSED, PAR>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   k<<<sp.nmol, 2 * NR, smem, s>>>(sp, md, err);
+}
+template <int J, int NR, bool FUSED>
+static void launch_rpoint_jn(const SpeciesDev& sp, const MolDev& md, int* err, cudaStream_t s) {
+  if (sp.par) launch_rpoint_jnp<J, NR, FUSED, true>(sp, md, err, s);
+  else launch_rpoint_jnp<J, NR, FUSED, false>(sp, md, err, s);
 }
 
 template <int NR, bool FUSED = false>
@@ -1477,17 +1554,17 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS)
   float2* s_kh = s_tw + NR;
   float2* st = s_kh + NR;
   __shared__ double s_red[8][2];
-  const int nrot = sp.nrot;
   const int lm = blockIdx.x;
   const int m = sp.mol[lm];
   for (int q = threadIdx.x; q < NR; q += blockDim.x) {
     s_tw[q] = __ldg(&sp.twiddle[q]);
     s_kh[q] = __ldg(&sp.khalf[q]);
   }
-  const float2* ge = sp.psi + ((long long)lm * 2 + 1) * nrot * NR;  // excited rows
+  const int ne = sp.rows - sp.rows_g;  // excited rows
+  const float2* ge = sp.psi + ((long long)lm * sp.rows + sp.rows_g) * NR;
   double num = 0.0, den = 0.0;
-  for (int b0 = 0; b0 < nrot; b0 += RB) {  // blocks of RB rows
-    const int nb = min(RB, nrot - b0);
+  for (int b0 = 0; b0 < ne; b0 += RB) {  // blocks of RB rows
+    const int nb = min(RB, ne - b0);
     __syncthreads();
     load_state(st, ge + (long long)b0 * NR, nb, NR, NRP);
     __syncthreads();
@@ -1970,7 +2047,7 @@ static int launch_stage1_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
     mol_field_kernel<<<(sp.nmol + 127) / 128, 128, 0, s>>>(sp, md, g, prescribed, err);
     ++n;
   }
-  const long long rows_total = (long long)sp.nmol * 2 * sp.nrot;
+  const long long rows_total = (long long)sp.nmol * sp.rows;
   if (sp.mixed) {  // split-BF16 tensor-core GEMM
     if constexpr (NR == 64 || NR == 128) {
       using T = TcShape<NR>;

@@ -292,7 +292,7 @@ std::vector<uint16_t> mixed_kinetic_planes(int nr, double dR, double dtau, doubl
 }
 
 ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const std::vector<int>& ids,
-                        int path, bool mixed) {
+                        int path, bool mixed, bool par) {
   ms::SpeciesDev& sp = s->sp[si];
   const int nr = d.nr, J = d.jmax, nrot = (J + 1) * (J + 1);
   // layout: the streaming form unless the caller asks for the fused one
@@ -305,6 +305,18 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   sp.jmax = J;
   sp.nrot = nrot;
   sp.nmol = (int)ids.size();
+  sp.par = par ? 1 : 0;
+  if (par) {  // ground rows: channels of even j; excited rows: odd j
+    sp.rows_g = 0;
+    sp.rows = 0;
+    for (int j = 0; j <= J; ++j) {
+      sp.rows += 2 * j + 1;
+      if (j % 2 == 0) sp.rows_g += 2 * j + 1;
+    }
+  } else {
+    sp.rows_g = nrot;
+    sp.rows = 2 * nrot;
+  }
   sp.mixed = mixed ? 1 : 0;
   sp.kpl = nullptr;
   const double dR = (d.rmax - d.rmin) / (nr - 1);
@@ -373,7 +385,7 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
     }
     phi0[a] = acc / (double)nr;
   }
-  const size_t per = (size_t)2 * nrot * nr;
+  const size_t per = (size_t)sp.rows * nr;
   std::vector<float2> row0(nr);
   for (int a = 0; a < nr; ++a) row0[a] = make_float2((float)phi0[a].real(), (float)phi0[a].imag());
   MS_TRY(zeros(s, &sp.psi, per * ids.size()));
@@ -586,7 +598,7 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
     for (long long q = 0; q < n; ++q)
       if (D->species_id[q] == si) ids.push_back((int)q);
     MS_TRY(build_species(s, si, D->species[si], dt, ids, O ? O->mol_path : MS_MOL_AUTO,
-                         O && O->precision == MS_PREC_MIXED_BF16X3));
+                         O && O->precision == MS_PREC_MIXED_BF16X3, O && O->state_form == MS_STATE_PARITY));
   }
   return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
 }
@@ -621,6 +633,8 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
   if (O && O->mol_substeps != 0 && O->mol_substeps != 1) return MS_EUNSUPPORTED;
   if (O && ((O->alloc == nullptr) != (O->free == nullptr))) return MS_EINVAL;
   if (O && (O->mol_path < MS_MOL_AUTO || O->mol_path > MS_MOL_STREAMING)) return MS_EINVAL;
+  if (O && O->state_form != MS_STATE_FULL && O->state_form != MS_STATE_PARITY) return MS_EINVAL;
+  const bool par = O && O->state_form == MS_STATE_PARITY;
   if (D && D->n_molecules > 0) {
     if (D->n_species <= 0 || D->n_species > ms::kMaxSpecies || !D->species || !D->species_id ||
         !D->pos_m || !D->orient)
@@ -639,6 +653,8 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
         return MS_EUNSUPPORTED;
       // the mixed kinetic pass: streaming form, radial grids of 64 or 128 points
       if (mixed && (path == MS_MOL_FUSED || !ms::mol_mixed_supported(sp.nr))) return MS_EUNSUPPORTED;
+      // parity-reduced rows: the point-resident kernels (J <= 4; fused only at N_r = 128)
+      if (par && (sp.jmax > 4 || (path == MS_MOL_FUSED && sp.nr != 128))) return MS_EUNSUPPORTED;
     }
     for (long long q = 0; q < D->n_molecules; ++q) {
       const int si = D->species_id[q];
@@ -829,7 +845,7 @@ ms_status ms_step_noalloc(ms_sim* s, int64_t n) {
   for (int si = 0; si < s->nspecies; ++si) {
     const ms::SpeciesDev& sp = s->sp[si];
     if (sp.path == MS_MOL_STREAMING &&
-        (size_t)sp.nmol * 2 * sp.nrot * sp.nr * sizeof(float2) > kNoAllocScratchBytes)
+        (size_t)sp.nmol * sp.rows * sp.nr * sizeof(float2) > kNoAllocScratchBytes)
       return MS_EINVAL;
   }
   float2* scratch = nullptr;
@@ -1058,7 +1074,7 @@ std::vector<Blob> state_blobs(ms_sim* s) {
   }
   for (int si = 0; si < s->nspecies; ++si) {
     const ms::SpeciesDev& sp = s->sp[si];
-    b.push_back({sp.psi, (size_t)sp.nmol * 2 * sp.nrot * sp.nr * sizeof(float2)});
+    b.push_back({sp.psi, (size_t)sp.nmol * sp.rows * sp.nr * sizeof(float2)});
   }
   if (s->nmol > 0) {
     const size_t n = (size_t)s->nmol;

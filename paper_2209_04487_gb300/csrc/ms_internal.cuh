@@ -77,9 +77,11 @@ struct Grid {
 // One species' device tables (all built on the host in FP64).
 struct SpeciesDev {
   int nr, jmax, nrot;
+  int par;                  // parity-reduced rows: ground even j, excited odd j
+  int rows, rows_g;         // state rows per molecule, of which ground rows
   int nmol;                 // molecules of this species
   const int* mol;           // their global ids (sorted by species, then by id)
-  float2* psi;              // state [nmol][2][nrot][nr], s = T^{-1/2} psi
+  float2* psi;              // state [nmol][rows][nr] (ground rows first), s = T^{-1/2} psi
   float2* d2;               // streaming form: scratch (T - 1) s, same layout
   float4* fld;              // streaming form: per molecule (theta E'_z, theta E'_x/2, theta E'_y/2, terms)
   int mixed;                // kinetic pass as the split-BF16 tensor-core GEMM (MS_PREC_MIXED_BF16X3)

@@ -92,6 +92,58 @@ def test_prescribed_molecules_match_oracle(B, nr, jmax, nmol, path):
     assert np.abs(tot - 1).max() < 2e-5
 
 
+# Parity-reduced state: only (ground, even j) and (excited, odd j) rows are
+# stored.  The oracle keeps the full state, so these runs check that the
+# dropped rows stay exactly empty and that the reduced layout computes the
+# same dynamics, at the plain FP32 tolerances.
+@pytest.mark.parametrize("nr,jmax,nmol,path", [
+    (128, 4, 19, "fused"), (128, 4, 19, "streaming"), (64, 1, 37, "streaming"), (128, 2, 7, "fused"),
+    (64, 3, 11, "streaming"), (256, 2, 5, "streaming"),
+])
+def test_parity_reduced_matches_oracle(B, nr, jmax, nmol, path):
+    sp = W.Species(nr=nr, jmax=jmax, A=0.05)
+    wl = W.custom("prescribed parity", 8, 8, 48, n_per_sim=nmol, species=[sp], layer=(20, 24),
+                  seed=nr + jmax, nsteps=300)
+    amp, wave = W.prescribed_drive(nmol, 300, wl.dt, E0=3e10, carrier_ev=6.0, fwhm=0.5e-15,
+                                   t0=0.5e-15)
+    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, state_form=B.MS_STATE_PARITY,
+                       mol_path=B.MS_MOL_FUSED if path == "fused" else B.MS_MOL_STREAMING)
+    sim.set_prescribed(amp, wave)
+    sim.step(300)
+    P = sim.populations()
+    mu = sim.dipoles()
+    absb, Rr = sim.dissociation()
+    o = PrescribedOracle(wl, amp, wave).run(300)
+    Po = o.populations()
+    assert np.abs(P - Po).max() < 1e-5
+    sel = Po[:, 1] > 1e-10
+    assert sel.any() and Po[:, 1].max() > 1e-6
+    assert np.max(np.abs(P[sel, 1] - Po[sel, 1]) / Po[sel, 1]) < 1e-3
+    assert np.abs(mu - o.mu).max() < 1e-4 * np.abs(o.mu).max()
+    assert np.abs(absb - o.absorbed()).max() < 1e-6
+    Ro = o.excited_R()
+    assert np.abs(Rr[:, 1] - Ro[:, 1]).max() < 1e-3 * Ro[:, 1].max() + 1e-12
+    tot = P.sum(axis=1) + absb.sum(axis=1)
+    assert np.abs(tot - 1).max() < 2e-5
+
+
+def test_parity_reduced_coupled_matches_oracle(B):
+    wl = W.custom("coupled parity", 16, 16, 48, src_k=14, pulses=[[2e10, 1.5498, 2e-15, 2e-15]],
+                  layer=(22, 26), n_per_sim=60, species=[W.Species(nr=128, jmax=4, A=0.05)], seed=5,
+                  nsteps=300)
+    sim = B.Simulation(wl, state_form=B.MS_STATE_PARITY)
+    assert sim.species_path(0) == B.MS_MOL_FUSED
+    sim.step(wl.nsteps)
+    E = sim.fields(B.MS_FIELD_E)
+    P = sim.populations()
+    mu = sim.dipoles()
+    o = CoupledOracle(wl).run(wl.nsteps)
+    Eo, _ = _fields_oracle(o)
+    assert _rel(E, Eo) < 1e-4
+    assert np.abs(P - o.populations()).max() < 1e-5
+    assert np.abs(mu - o.mu).max() < 1e-3 * np.abs(o.mu).max()
+
+
 # Mixed form (kinetic pass as a split-BF16 tensor-core GEMM): its stated
 # error.  bf16 hi + lo keeps ~17 bits of each operand, so the kinetic
 # correction carries a ~5e-6 relative error per step.  Over 300 steps of the
