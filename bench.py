@@ -233,10 +233,12 @@ def main():
     wl = _workload(a.molecules)
     path = {"auto": B.MS_MOL_AUTO, "fused": B.MS_MOL_FUSED, "streaming": B.MS_MOL_STREAMING}[a.mol_path]
 
-    def time_form(mol_path, precision, clocks=False, state_form=0):
+    def time_form(mol_path, precision, clocks=False, state_form=0, detectors=None):
         """Preroll, warm-up, then a.steps timed steps of one form (CUDA events on
         the library's stream, max over ranks) and its phase timings."""
         sim = B.Simulation(wl, mol_path=mol_path, precision=precision, state_form=state_form)
+        if detectors is not None:
+            sim.set_detectors(*detectors)
         form_path = sim.species_path(0)
         # the TF/SF wave needs ~40 steps to reach the molecular layer: before that
         # the molecules see E' = 0 and skip the coupling work, which is not the
@@ -286,6 +288,13 @@ def main():
     if not a.no_mixed:
         if fused:
             other["plain_fp32_streaming"] = form_entry(time_form(B.MS_MOL_STREAMING, B.MS_PREC_FP32))
+        # spectral detection: transmission plane in the glass, reflection plane
+        # below the source, 64 frequencies over 1.0 .. 2.5 eV
+        spec_planes = [wl.src_k - 4, wl.nz - wl.pml - 2]
+        spec_omega = np.linspace(1.0, 2.5, 64) / 6.582119569e-16
+        spec = form_entry(time_form(path, B.MS_PREC_FP32, detectors=(spec_planes, spec_omega)))
+        spec["note"] = f"running DFTs on z-planes {spec_planes}, 64 frequencies, flux spectra (FP64 accumulators)"
+        other["plain_fp32_with_spectra"] = spec
         if all(sp_.jmax <= 4 for sp_ in wl.species):
             par = form_entry(time_form(path, B.MS_PREC_FP32, state_form=B.MS_STATE_PARITY))
             par["note"] = ("parity-reduced state: only (ground, even j) and (excited, odd j) rows, the rows the "

@@ -251,6 +251,35 @@ ms_status ms_set_replay_field(ms_sim* sim, const float* E, int64_t nsteps);
 ms_status ms_record_local_fields(ms_sim* sim, const int64_t* mol_ids, int64_t m, float* dst,
                                  int64_t nsteps);
 
+/* Spectral detection (the transmission / reflection spectra of Figs. 2, 4
+ * and 6a): running discrete Fourier transforms of the tangential fields on
+ * z-planes, accumulated every step from the next ms_step on.
+ *   - Accumulator: F^(omega) = dt sum_n F(t_n) e^{i omega t_n}, FP64, per
+ *     cell, with Ex, Ey on plane k at t_{n+1} and Hx, Hy averaged over the
+ *     planes k -+ 1/2 at t_{n+1/2}; so Ex with Hy and Ey with Hx share their
+ *     in-plane positions.
+ *   - planes_z: nplanes (1..16) absolute z indices in [1, nz - 1).
+ *   - omega: nfreq (1..512) angular frequencies in rad/s.
+ * A call replaces the detectors set before and zeroes the accumulators;
+ * each call allocates their device memory (nsim * nplanes * nfreq * 4 * nx
+ * * ny * 16 bytes) until ms_destroy.  FDTD-driven handles only.  Errors:
+ * MS_EINVAL, MS_ENOMEM. */
+ms_status ms_set_detectors(ms_sim* sim, const int32_t* planes_z, int32_t nplanes, const double* omega,
+                           int32_t nfreq);
+
+/* Poynting flux spectrum through detector plane `plane` (in +z):
+ * flux[s][f] = Re sum_cells (Ex^ conj(Hy^) - Ey^ conj(Hx^)) dx^2 for
+ * simulation s and frequency f ([nsim][nfreq], FP64, in J s: the
+ * accumulators carry dt).  The energy through the plane is
+ * (1/pi) integral_0^inf flux d omega.  Synchronous. */
+ms_status ms_read_flux(ms_sim* sim, int32_t plane, double* flux);
+
+/* Raw accumulator of plane `plane`, simulation `sim`, component (0 Ex, 1 Ey,
+ * 2 Hx, 3 Hy) and frequency index `freq`: [ny][nx] complex FP64 as
+ * (re, im) pairs into dst (2 ny nx doubles).  Synchronous. */
+ms_status ms_read_dft(ms_sim* sim, int32_t plane, int32_t sim_index, int32_t component, int32_t freq,
+                      double* dst);
+
 /* Checkpoint / resume (no counterpart in the paper, which runs to completion).
  * ms_save writes the whole evolving state to the file `path`:
  *   - the fields E and H;
@@ -258,6 +287,7 @@ ms_status ms_record_local_fields(ms_sim* sim, const int64_t* mol_ids, int64_t m,
  *   - the CPML auxiliaries and the incident line;
  *   - every species' wavepackets;
  *   - the molecules' dipoles, populations and absorbed norm;
+ *   - the detectors' running Fourier transforms (when set);
  *   - the step counter.
  * The inputs (geometry, materials, molecules, drive samples) are not saved.
  * ms_load restores such a file into a handle created from the same

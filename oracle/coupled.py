@@ -21,6 +21,7 @@ import numpy as np
 from .constants import EA0
 from .fdtd import YeeOracle
 from .molecule import SpeciesEnsemble, dtau_au
+from .spectra import FluxDFT
 
 
 def molecule_cells(wl):
@@ -31,7 +32,7 @@ def molecule_cells(wl):
 
 
 class CoupledOracle:
-    def __init__(self, wl, *, aux_len=None, with_molecules=True):
+    def __init__(self, wl, *, aux_len=None, with_molecules=True, detectors=None):
         self.wl = wl
         if aux_len is None:
             aux_len = max(4096, wl.nsteps // 2 + 64)
@@ -48,6 +49,8 @@ class CoupledOracle:
                 if idx.size:
                     self.groups.append((idx, SpeciesEnsemble(sp, wl.quat[idx], self.dtau)))
         self.mu = np.zeros((self.nmol, 3))
+        # detectors = (planes_z, omega): running DFTs after every E half step
+        self.dft = FluxDFT(self.f, *detectors) if detectors is not None else None
 
     def scatter(self, dmu):
         """Per-cell polarization change (C/m^2) from per-molecule dipole
@@ -72,6 +75,8 @@ class CoupledOracle:
             self.f.step_e(dP)
         else:
             self.f.step_e()
+        if self.dft is not None:
+            self.dft.accumulate()
 
     def run(self, nsteps):
         for _ in range(nsteps):

@@ -85,6 +85,9 @@ def _load() -> C.CDLL:
         "ms_save": (C.c_int, [C.c_void_p, C.c_char_p]),
         "ms_check_bounded_wait": (C.c_int, [C.c_int32]),
         "ms_species_path": (C.c_int32, [C.c_void_p, C.c_int32]),
+        "ms_set_detectors": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(C.c_double), C.c_int32]),
+        "ms_read_flux": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_double)]),
+        "ms_read_dft": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P(C.c_double)]),
         "ms_load": (C.c_int, [C.c_void_p, C.c_char_p]),
         "ms_device_bytes": (C.c_size_t, [C.c_void_p]),
         "ms_timing_begin": (C.c_int, [C.c_void_p]),
@@ -105,7 +108,7 @@ LIB = _load()
 EXPORTED = ("ms_create", "ms_step", "ms_step_noalloc", "ms_step_count", "ms_read_fields", "ms_write_fields",
             "ms_read_populations", "ms_read_dissociation", "ms_read_dipoles",
             "ms_set_prescribed_field", "ms_set_replay_field", "ms_record_local_fields", "ms_save", "ms_load",
-            "ms_check_bounded_wait", "ms_species_path", "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
+            "ms_check_bounded_wait", "ms_species_path", "ms_set_detectors", "ms_read_flux", "ms_read_dft", "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
             "ms_destroy", "ms_status_string")
 
 
@@ -297,6 +300,26 @@ class Simulation:
         ln = C.c_int64()
         _check(LIB.ms_timing_end(self.h, out, C.byref(st), C.byref(ln)), "ms_timing_end")
         return list(out), st.value, ln.value
+
+    def set_detectors(self, planes, omega):
+        """Running DFTs on z-planes `planes` at angular frequencies `omega` (rad/s)."""
+        k = np.ascontiguousarray(planes, np.int32)
+        w = np.ascontiguousarray(omega, np.float64)
+        self._det = (k.size, w.size)
+        _check(LIB.ms_set_detectors(self.h, _ptr(k, C.c_int32), k.size, _ptr(w, C.c_double), w.size),
+               "ms_set_detectors")
+
+    def flux(self, plane: int) -> np.ndarray:
+        """[nsim][nfreq] Poynting flux spectrum through detector plane `plane`."""
+        out = np.empty((self.wl.nsim, self._det[1]))
+        _check(LIB.ms_read_flux(self.h, plane, _ptr(out, C.c_double)), "ms_read_flux")
+        return out
+
+    def dft(self, plane: int, sim: int, component: int, freq: int) -> np.ndarray:
+        """[ny][nx] complex accumulator (component 0 Ex, 1 Ey, 2 Hx, 3 Hy)."""
+        out = np.empty((self.wl.ny, self.wl.nx, 2))
+        _check(LIB.ms_read_dft(self.h, plane, sim, component, freq, _ptr(out, C.c_double)), "ms_read_dft")
+        return out[..., 0] + 1j * out[..., 1]
 
     def species_path(self, species: int = 0) -> int:
         """MS_MOL_FUSED or MS_MOL_STREAMING: the layout the species runs in."""

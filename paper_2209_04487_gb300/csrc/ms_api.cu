@@ -65,6 +65,7 @@ struct ms_sim {
   int64_t nmol = 0;
   int64_t steps = 0;
   int64_t nwave = 0;
+  double dx = 0.0;      // cell size (m)
   ms::Grid g{};
   ms::MolDev md{};
   ms::SpeciesDev sp[ms::kMaxSpecies]{};
@@ -429,6 +430,7 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
   const long long ncs = (long long)nx * ny * nz;
   const long long ncell = ncs * nsim;
   const double dx = G->dx_m, dt = G->dt_s;
+  s->dx = dx;
   s->drive = O ? O->drive : MS_DRIVE_FDTD;
   s->nmol = D ? D->n_molecules : 0;
   s->nspecies = D ? D->n_species : 0;
@@ -820,6 +822,10 @@ static void step_once(ms_sim* s, float2* scratch, const FieldRecorder* rec = nul
     ms::launch_yee_e(s->g, s->stream);
     ms::launch_aux_e(s->g, s->stream);
     launched += 1 + (s->g.ks >= 0);
+    if (s->g.ndet > 0) {
+      ms::launch_dft(s->g, s->stream);
+      ++launched;
+    }
   }
   ms::launch_step_counter(s->d_step, s->stream);
   ++launched;
@@ -1030,10 +1036,72 @@ ms_status ms_record_local_fields(ms_sim* s, const int64_t* mol_ids, int64_t m, f
   return st == MS_OK ? latched(s) : st;
 }
 
+// ---- spectral detection ----------------------------------------------------
+ms_status ms_set_detectors(ms_sim* s, const int32_t* planes_z, int32_t nplanes, const double* omega,
+                           int32_t nfreq) {
+  if (!s || !planes_z || !omega || s->drive != MS_DRIVE_FDTD || nplanes < 1 || nplanes > 16 || nfreq < 1 ||
+      nfreq > 512)
+    return MS_EINVAL;
+  for (int d = 0; d < nplanes; ++d)
+    if (planes_z[d] < 1 || planes_z[d] >= s->g.nz - 1) return MS_EINVAL;
+  for (int f = 0; f < nfreq; ++f)
+    if (!std::isfinite(omega[f])) return MS_EINVAL;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
+  int* dk = nullptr;
+  double* dw = nullptr;
+  double2* acc = nullptr;
+  std::vector<int> k(planes_z, planes_z + nplanes);
+  std::vector<double> w(omega, omega + nfreq);
+  MS_TRY(upload(s, &dk, k.data(), k.size()));
+  MS_TRY(upload(s, &dw, w.data(), w.size()));
+  MS_TRY(zeros(s, &acc, (size_t)s->g.nsim * nplanes * nfreq * 4 * s->g.nx * s->g.ny));
+  s->g.det_k = dk;
+  s->g.omega = dw;
+  s->g.dft = acc;
+  s->g.ndet = nplanes;
+  s->g.nfreq = nfreq;
+  return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
+}
+
+ms_status ms_read_dft(ms_sim* s, int32_t plane, int32_t sim_index, int32_t component, int32_t freq,
+                      double* dst) {
+  if (!s || !dst || plane < 0 || plane >= s->g.ndet || sim_index < 0 || sim_index >= s->g.nsim ||
+      component < 0 || component > 3 || freq < 0 || freq >= s->g.nfreq)
+    return MS_EINVAL;
+  const size_t cells = (size_t)s->g.nx * s->g.ny;
+  const double2* src =
+      s->g.dft + ((((size_t)sim_index * s->g.ndet + plane) * s->g.nfreq + freq) * 4 + component) * cells;
+  if (cudaMemcpyAsync(dst, src, cells * sizeof(double2), cudaMemcpyDeviceToHost, s->stream) != cudaSuccess)
+    return MS_ECUDA;
+  return latched(s);
+}
+
+ms_status ms_read_flux(ms_sim* s, int32_t plane, double* flux) {
+  if (!s || !flux || plane < 0 || plane >= s->g.ndet) return MS_EINVAL;
+  const size_t cells = (size_t)s->g.nx * s->g.ny, nf = (size_t)s->g.nfreq;
+  std::vector<double2> a(4 * cells);
+  const double dx2 = s->dx * s->dx;
+  for (int sim = 0; sim < s->g.nsim; ++sim)
+    for (size_t f = 0; f < nf; ++f) {
+      const double2* src = s->g.dft + ((((size_t)sim * s->g.ndet + plane) * nf + f) * 4) * cells;
+      if (cudaMemcpyAsync(a.data(), src, 4 * cells * sizeof(double2), cudaMemcpyDeviceToHost, s->stream) !=
+              cudaSuccess ||
+          cudaStreamSynchronize(s->stream) != cudaSuccess)
+        return MS_ECUDA;
+      double acc = 0.0;  // Re (Ex conj(Hy) - Ey conj(Hx))
+      for (size_t q = 0; q < cells; ++q) {
+        const double2 ex = a[q], ey = a[cells + q], hx = a[2 * cells + q], hy = a[3 * cells + q];
+        acc += (ex.x * hy.x + ex.y * hy.y) - (ey.x * hx.x + ey.y * hx.y);
+      }
+      flux[(size_t)sim * nf + f] = acc * dx2;
+    }
+  return latched(s);
+}
+
 // ---- checkpoint ------------------------------------------------------------
 namespace {
 constexpr char kCkMagic[8] = {'M', 'S', '2', '2', '0', '9', 'C', 'K'};
-constexpr uint32_t kCkVersion = 1;
+constexpr uint32_t kCkVersion = 2;
 
 struct CkHeader {
   char magic[8];
@@ -1042,6 +1110,7 @@ struct CkHeader {
   int32_t nx, ny, nz, nsim;
   int64_t nmol;
   int32_t nspecies, pml, ks, jk0, jk1, aux_len;
+  int32_t ndet, nfreq, state_rows[ms::kMaxSpecies];
   int32_t species[ms::kMaxSpecies][3];  // nr, jmax, molecules
   uint64_t nblobs;
 };
@@ -1071,6 +1140,8 @@ std::vector<Blob> state_blobs(ms_sim* s) {
       b.push_back({g.auxE, (size_t)g.nsim * (g.aux_len + 1) * sizeof(float)});
       b.push_back({g.auxH, (size_t)g.nsim * g.aux_len * sizeof(float)});
     }
+    if (g.ndet > 0)
+      b.push_back({g.dft, (size_t)g.nsim * g.ndet * g.nfreq * 4 * g.nx * g.ny * sizeof(double2)});
   }
   for (int si = 0; si < s->nspecies; ++si) {
     const ms::SpeciesDev& sp = s->sp[si];
@@ -1104,6 +1175,9 @@ CkHeader make_header(ms_sim* s, uint64_t nblobs) {
   h.jk0 = s->g.jk0;
   h.jk1 = s->g.jk1;
   h.aux_len = s->g.aux_len;
+  h.ndet = s->g.ndet;
+  h.nfreq = s->g.nfreq;
+  for (int si = 0; si < s->nspecies; ++si) h.state_rows[si] = s->sp[si].rows;
   for (int si = 0; si < s->nspecies; ++si) {
     h.species[si][0] = s->sp[si].nr;
     h.species[si][1] = s->sp[si].jmax;

@@ -72,6 +72,12 @@ struct Grid {
   const int* cell_mol;   // molecule ids sorted by cell
   const double* dmu;     // [nmol][3] lab dipole change of the last step (a.u.)
   long long* step;       // device step counter
+  // spectral detection: running DFTs on z-planes, dt sum_n F(t_n) e^{i omega t_n}
+  int ndet, nfreq;
+  const int* det_k;      // [ndet] plane indices
+  const double* omega;   // [nfreq] angular frequencies (rad/s)
+  double2* dft;          // [nsim][ndet][nfreq][4][ny][nx]: Ex, Ey on plane k at t_{n+1};
+                         // Hx, Hy averaged over z = k -+ 1/2 at t_{n+1/2}
 };
 
 // One species' device tables (all built on the host in FP64).
@@ -150,6 +156,7 @@ bool mol_mixed_supported(int nr);
 int mixed_strip_rows(int nr);
 int mixed_plane_offset(int row, int k, int nr);
 void launch_step_counter(long long* step, cudaStream_t s);
+void launch_dft(const Grid& g, cudaStream_t s);
 // E^n at the cells of the listed molecules: out[k][3] for k < m
 void launch_record_fields(const Grid& g, const int* cell, const long long* ids, int m, float* out,
                           cudaStream_t s);

@@ -215,6 +215,54 @@ void launch_record_fields(const Grid& g, const int* cell, const long long* ids, 
                           cudaStream_t s) {
   record_fields_kernel<<<(m + 127) / 128, 128, 0, s>>>(g, cell, ids, m, out);
 }
+// Spectral detection: after the E update of step n (E^{n+1}, H^{n+1/2}),
+// every cell of every detector plane adds dt F e^{i omega t} for each
+// frequency: Ex, Ey of the plane at t_{n+1}; Hx, Hy averaged over the planes
+// z = k - 1/2 and k + 1/2 (indices k - 1 and k) at t_{n+1/2}.  FP64.  A block
+// covers 256 cells of one plane and kDftF frequencies.
+constexpr int kDftF = 8;
+__global__ void dft_kernel(Grid g, int nfc) {
+  __shared__ double2 ph[2][kDftF];  // E and H phases of this block's frequencies, times dt
+  const long long n = *g.step;
+  const int d = blockIdx.y / nfc, f0 = (blockIdx.y % nfc) * kDftF, sim = blockIdx.z;
+  const int nf = min(kDftF, g.nfreq - f0);
+  if (threadIdx.x < nf) {
+    double s1, c1, s2, c2;
+    const double w = g.omega[f0 + threadIdx.x];
+    sincos(w * (double)(n + 1) * g.dt, &s1, &c1);
+    sincos(w * ((double)n + 0.5) * g.dt, &s2, &c2);
+    ph[0][threadIdx.x] = make_double2(c1 * g.dt, s1 * g.dt);
+    ph[1][threadIdx.x] = make_double2(c2 * g.dt, s2 * g.dt);
+  }
+  __syncthreads();
+  const long long plane = (long long)g.ny * g.nx;
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= plane) return;
+  const int k = g.det_k[d];
+  const long long base = sim * g.ncell_sim;
+  const long long ck = base + (long long)k * plane + q, cm = ck - plane;
+  const double v[4] = {g.E[0][ck], g.E[1][ck], 0.5 * ((double)g.H[0][cm] + (double)g.H[0][ck]),
+                       0.5 * ((double)g.H[1][cm] + (double)g.H[1][ck])};
+  double2* acc = g.dft + (((long long)sim * g.ndet + d) * g.nfreq + f0) * 4 * plane + q;
+  for (int f = 0; f < nf; ++f) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const double2 w = ph[c < 2 ? 0 : 1][f];
+      double2* a = acc + ((long long)f * 4 + c) * plane;
+      double2 x = *a;
+      x.x = fma(v[c], w.x, x.x);
+      x.y = fma(v[c], w.y, x.y);
+      *a = x;
+    }
+  }
+}
+void launch_dft(const Grid& g, cudaStream_t s) {
+  if (g.ndet <= 0) return;
+  const long long plane = (long long)g.ny * g.nx;
+  const int nfc = (g.nfreq + kDftF - 1) / kDftF;
+  const dim3 grid((unsigned)((plane + 255) / 256), (unsigned)(g.ndet * nfc), (unsigned)g.nsim);
+  dft_kernel<<<grid, 256, 0, s>>>(g, nfc);
+}
 void launch_step_counter(long long* step, cudaStream_t s) {
   step_counter_kernel<<<1, 1, 0, s>>>(step);
 }

@@ -232,6 +232,32 @@ def test_three_species_coupled_matches_oracle(B):
     assert set(np.unique(wl.species_id)) == {0, 1, 2}
 
 
+def test_flux_spectra_match_oracle(B):
+    """Running DFTs and flux spectra on two planes, one in the reflected
+    (scattered-field) region below the source and one beyond a silver slab,
+    with molecules polarising the field in between."""
+    from oracle.constants import HBAR_EVS
+    wl = W.custom("spectra", 16, 16, 64, src_k=14, pulses=[[2e10, 1.5498, 1e-15, 3e-15]],
+                  geometry=lambda nx, ny, nz: _srr_like(nx, ny, nz), layer=(22, 26), n_per_sim=40,
+                  species=[W.species_config0(jmax=1)], seed=21, nsteps=2400)
+    w0 = 1.5498 / HBAR_EVS
+    omega = w0 * np.array([0.7, 0.9, 1.0, 1.1, 1.3])
+    planes = [12, 50]
+    sim = B.Simulation(wl)
+    sim.set_detectors(planes, omega)
+    sim.step(wl.nsteps)
+    o = CoupledOracle(wl, detectors=(planes, omega)).run(wl.nsteps)
+    for d in range(2):
+        got, want = sim.flux(d)[0], o.dft.flux(d)[0]
+        assert np.max(np.abs(got - want)) < 1e-4 * np.abs(want).max(), (d, got, want)
+        for c in range(4):
+            for f in range(omega.size):
+                g = sim.dft(d, 0, c, f)
+                r = o.dft.acc[0, d, f, c]
+                assert np.linalg.norm(g - r) <= 1e-4 * max(np.linalg.norm(o.dft.acc[0, d, f]), 1e-300), (d, c, f)
+    assert o.dft.flux(1)[0].max() > 0 and o.dft.flux(0)[0].min() < 0   # transmitted +z, reflected -z
+
+
 @pytest.mark.parametrize("nr,jmax,E0", [(64, 1, 0.0), (128, 4, 0.0), (128, 4, 1e9)])
 def test_norm_drift_2000_steps(B, nr, jmax, E0):
     """Norm drift of the FP32 wavepackets over 2000 steps (target 1e-6):
