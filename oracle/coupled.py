@@ -38,10 +38,13 @@ class CoupledOracle:
             aux_len = max(4096, wl.nsteps // 2 + 64)
         self.f = YeeOracle(wl.nx, wl.ny, wl.nz, wl.nsim, wl.dx, wl.dt, wl.mat_id,
                            wl.materials, pml=wl.pml, bc_z=wl.bc_z, src_k=wl.src_k,
-                           src=wl.src, aux_len=aux_len)
+                           src=wl.src, aux_len=aux_len, src_kind=getattr(wl, "src_kind", "pulse"))
         self.nmol = wl.n_molecules if with_molecules else 0
         self.ci, self.cj, self.ck = molecule_cells(wl)
-        self.dtau = dtau_au(wl.dt)
+        # molecules advance every N-th field step by N dt (the paper's cadence:
+        # every 40th step); their polarization change enters that step's E update
+        self.N = int(getattr(wl, "mol_substeps", 1))
+        self.dtau = dtau_au(wl.dt * self.N)
         self.groups = []
         if self.nmol:
             for s, sp in enumerate(wl.species):
@@ -64,8 +67,9 @@ class CoupledOracle:
         return out
 
     def step(self):
+        molecular = self.f.n % self.N == 0
         self.f.step_h()
-        if self.nmol:
+        if self.nmol and molecular:
             E = self.f.gather(self.wl.sim_id, self.ci, self.cj, self.ck)
             mu = np.empty_like(self.mu)
             for idx, ens in self.groups:
@@ -109,7 +113,8 @@ class PrescribedOracle:
         self.sel = sel
         self.amp = np.asarray(amp, np.float64)[sel]
         self.wave = np.asarray(wave, np.float64)
-        self.dtau = dtau_au(wl.dt)
+        self.N = int(getattr(wl, "mol_substeps", 1))
+        self.dtau = dtau_au(wl.dt * self.N)
         sid = wl.species_id[sel]
         self.groups = []
         for s, sp in enumerate(wl.species):
@@ -120,9 +125,10 @@ class PrescribedOracle:
         self.mu = np.zeros((sel.size, 3))
 
     def step(self):
-        E = self.amp * self.wave[self.n]
-        for idx, ens in self.groups:
-            self.mu[idx] = ens.step(E[idx])
+        if self.n % self.N == 0:  # molecular steps only (every N-th step, by N dt)
+            E = self.amp * self.wave[self.n]
+            for idx, ens in self.groups:
+                self.mu[idx] = ens.step(E[idx])
         self.n += 1
 
     def run(self, nsteps):

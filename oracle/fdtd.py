@@ -50,6 +50,16 @@ def pulse(t, E0, carrier_ev, fwhm, t0):
     return E0 * np.exp(-4.0 * np.log(2.0) * ((t - t0) / fwhm) ** 2) * np.cos(w * (t - t0))
 
 
+def cw(t, E0, carrier_ev, t_on, t0):
+    """Continuous-wave drive switched on smoothly over t_on (Sec. 3 ramps its
+    CW runs up over the first few fs; the sin^2 envelope is our reading):
+    E0 sin^2(pi t / (2 t_on)) cos(w (t - t0)) for t < t_on, then
+    E0 cos(w (t - t0))."""
+    w = carrier_ev / HBAR_EVS
+    ramp = np.where(t < t_on, np.sin(0.5 * np.pi * np.clip(t, 0.0, None) / t_on) ** 2, 1.0)
+    return E0 * ramp * np.cos(w * (t - t0))
+
+
 def drude_coefficients(wp_ev, gamma_ev, dt):
     """alpha, beta of the central-difference discretisation of Eq. 2."""
     wp = wp_ev / HBAR_EVS
@@ -78,7 +88,7 @@ class YeeOracle:
     """FP64 field state and the two half-step updates (Eq. 1, Eq. 2)."""
 
     def __init__(self, nx, ny, nz, nsim, dx, dt, mat_id, materials, *, pml=10,
-                 bc_z="pml", src_k=-1, src=None, aux_len=None):
+                 bc_z="pml", src_k=-1, src=None, aux_len=None, src_kind="pulse"):
         self.nx, self.ny, self.nz, self.S = nx, ny, nz, nsim
         self.dx, self.dt = dx, dt
         self.bc_z = bc_z
@@ -109,6 +119,7 @@ class YeeOracle:
             self.psi_Exz, self.psi_Eyz, self.psi_Hxz, self.psi_Hyz = (np.zeros(shp) for _ in range(4))
         # TF/SF source and its 1D incident-field line
         self.src_k = src_k
+        self.src_fn = cw if src_kind == "cw" else pulse
         if src_k >= 0:
             self.src = np.asarray(src, np.float64).reshape(nsim, 4)
             L = aux_len if aux_len is not None else 4096
@@ -120,7 +131,7 @@ class YeeOracle:
     # -- helpers --------------------------------------------------------------
     def _drive(self, n):
         t = n * self.dt
-        return np.array([pulse(t, *self.src[s]) for s in range(self.S)])
+        return np.array([float(self.src_fn(t, *self.src[s])) for s in range(self.S)])
 
     def _zplus(self, F):
         """F[k+1] along z (perfect conductor beyond the top, or wrap)."""

@@ -83,6 +83,8 @@ class Workload:
     quat: np.ndarray               # float64 [n, 4], (w, x, y, z), molecule frame -> lab
     nsteps: int
     meta: Dict = field(default_factory=dict)
+    src_kind: str = "pulse"        # "pulse" (row: E0, carrier, FWHM, t0) or "cw" (E0, carrier, turn-on, t0)
+    mol_substeps: int = 1          # molecules advance every mol_substeps-th field step
 
     @property
     def n_molecules(self) -> int:
@@ -194,7 +196,7 @@ def custom(name: str, nx: int, ny: int, nz: int, *, nsim: int = 1, pml: int = 10
            species: Optional[List[Species]] = None,
            fractions: Optional[Sequence[float]] = None,
            seed: int = 0, distinct: bool = False, nsteps: int = 100,
-           dx: float = 2e-9) -> Workload:
+           dx: float = 2e-9, src_kind: str = "pulse", mol_substeps: int = 1) -> Workload:
     """General builder used by the five benchmark workloads and by tests."""
     dt = dx / (2.0 * _C0)
     if pulses is None:
@@ -236,7 +238,7 @@ def custom(name: str, nx: int, ny: int, nz: int, *, nsim: int = 1, pml: int = 10
                     bc_z=bc_z, src_k=src_k, src=src, materials=list(MATERIALS),
                     mat_id=mat, species=species, species_id=species_id, sim_id=sim_id,
                     pos=posa, quat=quata, nsteps=nsteps,
-                    meta=dict(layer=layer, seed=seed))
+                    meta=dict(layer=layer, seed=seed), src_kind=src_kind, mol_substeps=mol_substeps)
 
 
 # ----------------------------------------------------------------------------
