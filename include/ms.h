@@ -88,10 +88,18 @@ enum { MS_STATE_FULL = 0, MS_STATE_PARITY = 1 };
 /* Grid and source.  dt must satisfy dt <= dx/(sqrt(3) c) (checked).
  * src_plane_z: absolute z index of the TF/SF plane (total field for
  * k >= src_plane_z), -1 for no source; it must lie outside the z absorbers.
- * src: nsim rows of 4 doubles: peak field E0 [V/m], carrier photon energy
- * [eV], FWHM of the field envelope [s], time of the peak t0 [s]; the
- * incident plane wave is x-polarised and travels towards +z with
- * E(t) = E0 exp(-4 ln2 ((t-t0)/fwhm)^2) cos(w (t-t0)) at the plane. */
+ * The incident plane wave is x-polarised and travels towards +z; its value
+ * at the plane, with w the carrier's angular frequency, is
+ *   MS_SRC_PULSE (Sec. 3's femtosecond pulses): src rows (peak field E0
+ *     [V/m], carrier photon energy [eV], FWHM of the field envelope [s],
+ *     time of the peak t0 [s]);
+ *     E(t) = E0 exp(-4 ln2 ((t-t0)/fwhm)^2) cos(w (t-t0));
+ *   MS_SRC_CW (Sec. 3's continuous-wave drive): src rows (E0 [V/m], carrier
+ *     photon energy [eV], turn-on time t_on [s], phase reference t0 [s]);
+ *     E(t) = E0 sin^2(pi t / (2 t_on)) cos(w (t-t0)) for t < t_on, then
+ *     E0 cos(w (t-t0)).
+ * fwhm and t_on must be > 0 (MS_EINVAL otherwise). */
+enum { MS_SRC_PULSE = 0, MS_SRC_CW = 1 };
 typedef struct {
   int32_t nx, ny, nz, nsim;
   double dx_m, dt_s;
@@ -99,6 +107,7 @@ typedef struct {
   int32_t bc_z;        /* MS_BC_PML or MS_BC_PERIODIC */
   int32_t src_plane_z; /* -1 = no source */
   const double* src;   /* [nsim][4], may be NULL when src_plane_z < 0 */
+  int32_t src_kind;    /* MS_SRC_PULSE or MS_SRC_CW */
 } ms_grid_desc;
 
 /* Materials: n_materials entries of (eps_inf, plasma energy wp [eV],
@@ -148,7 +157,11 @@ typedef struct {
  * stream: cudaStream_t to run on; NULL = a stream the library creates. */
 typedef struct {
   int32_t precision;    /* MS_PREC_FP32 (MS_PREC_MIXED_BF16X3: see ms_create) */
-  int32_t mol_substeps; /* molecular step every mol_substeps field steps; 1 */
+  int32_t mol_substeps; /* N: the molecules advance on field steps n with
+                           n % N == 0, by a step of N dt, under E^n; their
+                           dipole change enters that step's E update (Sec. 2's
+                           multiscale cadence).  0 means 1; 1..65536, else
+                           MS_EINVAL. */
   int32_t drive;        /* MS_DRIVE_FDTD or MS_DRIVE_PRESCRIBED */
   void* (*alloc)(size_t bytes, void* ctx);
   void (*free)(void* ptr, void* ctx);

@@ -22,6 +22,7 @@ MS_PREC_FP32, MS_PREC_MIXED_BF16X3 = 0, 1
 MS_DRIVE_FDTD, MS_DRIVE_PRESCRIBED = 0, 1
 MS_FIELD_E, MS_FIELD_H = 0, 1
 MS_STATE_FULL, MS_STATE_PARITY = 0, 1
+MS_SRC_PULSE, MS_SRC_CW = 0, 1
 MS_MOL_AUTO, MS_MOL_FUSED, MS_MOL_STREAMING = 0, 1, 2
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -31,7 +32,8 @@ _FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
 class GridDesc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nsim", C.c_int32),
                 ("dx_m", C.c_double), ("dt_s", C.c_double), ("pml_cells", C.c_int32),
-                ("bc_z", C.c_int32), ("src_plane_z", C.c_int32), ("src", C.POINTER(C.c_double))]
+                ("bc_z", C.c_int32), ("src_plane_z", C.c_int32), ("src", C.POINTER(C.c_double)),
+                ("src_kind", C.c_int32)]
 
 
 class MaterialsDesc(C.Structure):
@@ -174,7 +176,8 @@ class Simulation:
         src = np.ascontiguousarray(wl.src, np.float64) if wl.src_k >= 0 else None
         self._keep.append(src)
         g = GridDesc(wl.nx, wl.ny, wl.nz, wl.nsim, wl.dx, wl.dt, wl.pml,
-                     MS_BC_PML if wl.bc_z == "pml" else MS_BC_PERIODIC, wl.src_k, _ptr(src, C.c_double))
+                     MS_BC_PML if wl.bc_z == "pml" else MS_BC_PERIODIC, wl.src_k, _ptr(src, C.c_double),
+                     MS_SRC_CW if wl.src_kind == "cw" else MS_SRC_PULSE)
         eps = np.array([m[0] for m in wl.materials], np.float64)
         wp = np.array([m[1] for m in wl.materials], np.float64)
         ga = np.array([m[2] for m in wl.materials], np.float64)
@@ -194,7 +197,7 @@ class Simulation:
                           _ptr(pos, C.c_double), _ptr(quat, C.c_double))
         opts = Options()
         opts.precision = precision
-        opts.mol_substeps = 1
+        opts.mol_substeps = wl.mol_substeps
         opts.drive = drive
         opts.mol_path = mol_path
         opts.state_form = state_form

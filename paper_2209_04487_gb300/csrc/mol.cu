@@ -13,8 +13,9 @@
 // phase, kinetic phase, FFT twiddle) is carried as an FP32 hi+lo pair and
 // applied with a compensated product, so the factor is exact to ~1e-15 and
 // only unbiased output rounding remains.  Every factor of the step is close
-// to the identity (|V dtau| and |k^2 dtau/2mu| are a few 1e-2), so the step
-// is computed as a correction: d2 = (T - 1) s, u = s + d2,
+// to the identity (|V dtau| and |k^2 dtau/2mu| are a few 1e-2 at one
+// molecular step per field step, O(1) under sub-stepping), so the step is
+// computed as a correction: d2 = (T - 1) s, u = s + d2,
 // d1 = (V - 1) u + V^{1/2} S with S = sum_{n>=1} (i theta sigma_x M)^n/n!
 // V^{1/2} u (Taylor series of the coupling exponential, |theta M| << 1), and
 // s' = s + (d2 + d1): the full-magnitude state is rounded once per step,
@@ -396,14 +397,6 @@ constexpr int kChunk = 32;            // widest R-space chunk (one radial point 
 //   u  = s + d2 = T s        (per radial point)
 //   s' = Mask V^{1/2} K(E') V^{1/2} u, computed as s + (d2 + d1)
 // ----------------------------------------------------------------------------
-// e^{-i V dtau/2} from v = e^{-i V dtau} - 1: sqrt(1 + v) = 1 + v/2 - v^2/8 + O(v^3).
-// It only scales the small coupling correction, where an O(|V dtau|^3)
-// relative error is far below FP32 resolution of the state.
-__device__ __forceinline__ float2 vhalf_of(float2 v) {
-  const float2 v2 = cmul(v, v);
-  return make_float2(fmaf(0.5f, v.x, fmaf(-0.125f, v2.x, 1.f)), fmaf(0.5f, v.y, -0.125f * v2.y));
-}
-
 // compensated FP32 accumulation (TwoSum): hi + lo carries ~48 bits
 __device__ __forceinline__ void acc2(float& hi, float& lo, float x) {
   const float t = hi + x;
@@ -429,9 +422,12 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
   float2* bY = st + (FUSED ? rows * NRP : 0);            // [rows][CH] Taylor terms / new state
   float2* bZ = bY + rows * CH;                           // [rows][CH] Taylor terms
   // per chunk, double buffered: old state [rows][CH], (streaming: d2
-  // [rows][CH]), e^{-iV dtau} - 1 [2(J+1)][CH] and absorber mask [CH]
+  // [rows][CH]), e^{-iV dtau} - 1 and e^{-iV dtau/2} [2(J+1)][CH] each, and
+  // absorber mask [CH].  The half-step phase is read from its exact table:
+  // with sub-stepping |V dtau| reaches O(1), where no short series of the
+  // full-step delta would keep the coupling correction unitary.
   const int nd = FUSED ? 0 : rows;
-  const int cbuf = (rows + nd + 2 * (J + 1) + 1) * CH;
+  const int cbuf = (rows + nd + 4 * (J + 1) + 1) * CH;
   float2* bC = bZ + rows * CH;
   int2* s_prog = reinterpret_cast<int2*>(bC + 2 * cbuf);  // [nrot][6] (nbr*CH, coupling) this step
   int2* s_dipp = s_prog + nrot * kMaxCoupl;              // [nrot][6] (nbr*CH, dipole coefficient)
@@ -454,20 +450,21 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
   const int m = sp.mol[lm];
   float2* gs = sp.psi + (long long)lm * rows * NR;
 
-  // chunk copy: old state, potential deltas and mask of radial points [r0, r0 + CH)
+  // chunk copy: old state, potential phases and mask of radial points [r0, r0 + CH)
   // every thread copies 16-byte pieces (cp.async); rows: old state, then
-  // the potential deltas, then the mask
+  // the potential deltas, the half-step phases, then the mask
   const float2* gd = FUSED ? nullptr : sp.d2 + (long long)lm * rows * NR;
   const int cp_per_row = CH / 2;                   // 16-byte pieces per chunk row
   const int cp_c2 = 2 * (t % cp_per_row), cp_q0 = t / cp_per_row, cp_qs = NT / cp_per_row;
   auto issue_chunk = [&](int r0, int b) {
     float2* buf = bC + b * cbuf;
-    const int nv = 2 * (J + 1), nq = rows + nd + nv + 1;
+    const int nv = 2 * (J + 1), nq = rows + nd + 2 * nv + 1;
     for (int q = cp_q0; q < nq; q += cp_qs) {
       const float2* src;
       if (q < rows) src = gs + (long long)q * NR;
       else if (q < rows + nd) src = gd + (long long)(q - rows) * NR;
       else if (q < rows + nd + nv) src = sp.vdelta + (long long)(q - rows - nd) * NR;
+      else if (q < rows + nd + 2 * nv) src = sp.vhalf + (long long)(q - rows - nd - nv) * NR;
       else src = sp.maskw;
       cp_async16(buf + q * CH + cp_c2, src + r0 + cp_c2);
     }
@@ -537,8 +534,9 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
     const int r0 = ck * CH, r = r0 + rl, b = ck & 1;
     float2* bU = bC + b * cbuf;
     const float2* bD = bU + rows * CH;              // streaming form: d2 of the chunk
-    const float2* bV = bD + nd * CH;
-    const float2* bM = bV + 2 * (J + 1) * CH;
+    const float2* bV = bD + nd * CH;                // e^{-iV dtau} - 1
+    const float2* bH = bV + 2 * (J + 1) * CH;       // e^{-iV dtau/2}
+    const float2* bM = bH + 2 * (J + 1) * CH;
     // this chunk's copies (issued one chunk earlier) are complete and
     // visible; the other buffer is free since the previous chunk's barriers
     cp_async_wait_all();
@@ -555,7 +553,7 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
         if (row < rows) {
           const int2 ri = s_rinfo[row];
           const float2 u = (FUSED ? st[row * NRP + r] : bD[row * CH + rl]) + bU[row * CH + rl];
-          bZ[row * CH + rl] = cmul(s_ph[ri.y], cmul(vhalf_of(bV[ri.x + rl]), u));
+          bZ[row * CH + rl] = cmul(s_ph[ri.y], cmul(bH[ri.x + rl], u));
         }
       }
       __syncthreads();
@@ -605,7 +603,7 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
         const float2 u = sv + d2;
         const float2 ph = s_ph[ri.y];
         const float2 vd = bV[ri.x + rl];
-        const float2 corr = cmul(vhalf_of(vd), cmul(make_float2(ph.x, -ph.y), sacc[i]));
+        const float2 corr = cmul(bH[ri.x + rl], cmul(make_float2(ph.x, -ph.y), sacc[i]));
         float2 d1 = make_float2(fmaf(u.x, vd.x, fmaf(-u.y, vd.y, corr.x)), fmaf(u.x, vd.y, fmaf(u.y, vd.x, corr.y)));
         if (mk < 1.f) {
           const float px = u.x + d1.x, py = u.y + d1.y;
@@ -1666,7 +1664,7 @@ static size_t step_smem(int nr, int nrot, int ch, bool fused) {
   const size_t nd = fused ? 0 : rows;
   return (fused ? 2 * (size_t)nr * sizeof(float2) + mol_state_smem(nr, rows) : 0) +
          2 * (size_t)rows * ch * sizeof(float2) +
-         2 * (size_t)(rows + nd + 2 * (jm + 1) + 1) * ch * sizeof(float2) +
+         2 * (size_t)(rows + nd + 4 * (jm + 1) + 1) * ch * sizeof(float2) +
          2 * (size_t)nrot * kMaxCoupl * sizeof(int2) + (size_t)rows * sizeof(int2);
 }
 

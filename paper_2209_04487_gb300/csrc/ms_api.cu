@@ -65,6 +65,8 @@ struct ms_sim {
   int64_t nmol = 0;
   int64_t steps = 0;
   int64_t nwave = 0;
+  int nsub = 1;         // molecular step every nsub field steps
+  int src_kind = 0;     // MS_SRC_PULSE or MS_SRC_CW
   double dx = 0.0;      // cell size (m)
   ms::Grid g{};
   ms::MolDev md{};
@@ -432,6 +434,8 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
   const double dx = G->dx_m, dt = G->dt_s;
   s->dx = dx;
   s->drive = O ? O->drive : MS_DRIVE_FDTD;
+  s->nsub = O && O->mol_substeps > 1 ? O->mol_substeps : 1;
+  s->src_kind = G->src_plane_z >= 0 ? G->src_kind : 0;
   s->nmol = D ? D->n_molecules : 0;
   s->nspecies = D ? D->n_species : 0;
   ms::Grid& g = s->g;
@@ -526,14 +530,11 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
         sp[q].w = G->src[4 * q + 1] / kHbarEVs;
         sp[q].fwhm = G->src[4 * q + 2];
         sp[q].t0 = G->src[4 * q + 3];
+        sp[q].kind = G->src_kind;
       }
       MS_TRY(upload(s, (ms::SrcParam**)&g.src, sp.data(), sp.size()));
       std::vector<float> aE((size_t)nsim * (kAuxLen + 1), 0.f);
-      for (int q = 0; q < nsim; ++q) {
-        const double x = (0.0 - sp[q].t0) / sp[q].fwhm;
-        aE[(size_t)q * (kAuxLen + 1)] =
-            (float)(sp[q].E0 * std::exp(-4.0 * std::log(2.0) * x * x) * std::cos(sp[q].w * (0.0 - sp[q].t0)));
-      }
+      for (int q = 0; q < nsim; ++q) aE[(size_t)q * (kAuxLen + 1)] = (float)ms::incident_field(sp[q], 0.0);
       MS_TRY(upload(s, &g.auxE, aE.data(), aE.size()));
       MS_TRY(zeros(s, &g.auxH, (size_t)nsim * kAuxLen));
     }
@@ -599,7 +600,7 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
     std::vector<int> ids;
     for (long long q = 0; q < n; ++q)
       if (D->species_id[q] == si) ids.push_back((int)q);
-    MS_TRY(build_species(s, si, D->species[si], dt, ids, O ? O->mol_path : MS_MOL_AUTO,
+    MS_TRY(build_species(s, si, D->species[si], dt * s->nsub, ids, O ? O->mol_path : MS_MOL_AUTO,
                          O && O->precision == MS_PREC_MIXED_BF16X3, O && O->state_form == MS_STATE_PARITY));
   }
   return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
@@ -617,6 +618,7 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
   if (G->bc_z == MS_BC_PML && (G->pml_cells < 0 || 2 * G->pml_cells >= G->nz)) return MS_EINVAL;
   if (G->src_plane_z >= 0) {
     if (!G->src || G->bc_z != MS_BC_PML) return MS_EINVAL;
+    if (G->src_kind != MS_SRC_PULSE && G->src_kind != MS_SRC_CW) return MS_EINVAL;
     if (G->src_plane_z < G->pml_cells + 2 || G->src_plane_z >= G->nz - G->pml_cells) return MS_EINVAL;
     for (int q = 0; q < G->nsim; ++q)
       if (!(G->src[4 * q + 2] > 0)) return MS_EINVAL;
@@ -632,7 +634,7 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
   if (drive != MS_DRIVE_FDTD && drive != MS_DRIVE_PRESCRIBED) return MS_EINVAL;
   if (O && O->precision != MS_PREC_FP32 && O->precision != MS_PREC_MIXED_BF16X3) return MS_EINVAL;
   const bool mixed = O && O->precision == MS_PREC_MIXED_BF16X3;
-  if (O && O->mol_substeps != 0 && O->mol_substeps != 1) return MS_EUNSUPPORTED;
+  if (O && (O->mol_substeps < 0 || O->mol_substeps > 65536)) return MS_EINVAL;
   if (O && ((O->alloc == nullptr) != (O->free == nullptr))) return MS_EINVAL;
   if (O && (O->mol_path < MS_MOL_AUTO || O->mol_path > MS_MOL_STREAMING)) return MS_EINVAL;
   if (O && O->state_form != MS_STATE_FULL && O->state_form != MS_STATE_PARITY) return MS_EINVAL;
@@ -795,6 +797,9 @@ struct FieldRecorder {  // ms_record_local_fields: E^n of listed molecules, one 
 
 static void step_once(ms_sim* s, float2* scratch, const FieldRecorder* rec = nullptr) {
   const bool fdtd = s->drive == MS_DRIVE_FDTD;
+  // sub-stepping: the molecules advance (by nsub dt) on every nsub-th step only,
+  // and only those steps' E updates take the molecular dipole change
+  const bool molecular = s->steps % s->nsub == 0;
   int launched = 0;
   if (s->timing) mark(s);
   if (fdtd) {
@@ -812,14 +817,18 @@ static void step_once(ms_sim* s, float2* scratch, const FieldRecorder* rec = nul
     sp[si] = s->sp[si];
     if (scratch && sp[si].path == MS_MOL_STREAMING) sp[si].d2 = scratch;  // rewritten before it is read
   }
-  for (int si = 0; si < s->nspecies; ++si)
-    launched += ms::launch_mol_stage1(sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
+  if (molecular)
+    for (int si = 0; si < s->nspecies; ++si)
+      launched += ms::launch_mol_stage1(sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
   if (s->timing) mark(s);
-  for (int si = 0; si < s->nspecies; ++si)
-    launched += ms::launch_mol_stage2(sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
+  if (molecular)
+    for (int si = 0; si < s->nspecies; ++si)
+      launched += ms::launch_mol_stage2(sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
   if (s->timing) mark(s);
   if (fdtd) {
-    ms::launch_yee_e(s->g, s->stream);
+    ms::Grid ge = s->g;
+    if (!molecular) ge.mk1 = ge.mk0;  // no molecular slab: the dipoles did not change
+    ms::launch_yee_e(ge, s->stream);
     ms::launch_aux_e(s->g, s->stream);
     launched += 1 + (s->g.ks >= 0);
     if (s->g.ndet > 0) {
@@ -829,6 +838,7 @@ static void step_once(ms_sim* s, float2* scratch, const FieldRecorder* rec = nul
   }
   ms::launch_step_counter(s->d_step, s->stream);
   ++launched;
+  ++s->steps;
   if (s->timing) {
     mark(s);
     s->timed_steps++;
@@ -840,7 +850,6 @@ ms_status ms_step(ms_sim* s, int64_t n) {
   if (!s || n < 0) return MS_EINVAL;
   if (s->drive == MS_DRIVE_PRESCRIBED && s->nmol > 0 && s->steps + n > s->nwave) return MS_EINVAL;
   for (int64_t q = 0; q < n; ++q) step_once(s, nullptr);
-  s->steps += n;
   return cudaGetLastError() == cudaSuccess ? MS_OK : MS_ECUDA;
 }
 
@@ -857,7 +866,6 @@ ms_status ms_step_noalloc(ms_sim* s, int64_t n) {
   float2* scratch = nullptr;
   MS_TRY(noalloc_scratch(&scratch));
   for (int64_t q = 0; q < n; ++q) step_once(s, scratch);
-  s->steps += n;
   return cudaGetLastError() == cudaSuccess ? MS_OK : MS_ECUDA;
 }
 
@@ -1024,7 +1032,6 @@ ms_status ms_record_local_fields(ms_sim* s, const int64_t* mol_ids, int64_t m, f
       step_once(s, nullptr, &rec);
       rec.out += (size_t)m * 3;
     }
-    s->steps += nsteps;
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemcpyAsync(dst, d_out, nout, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
         cudaStreamSynchronize(s->stream) != cudaSuccess)
@@ -1101,7 +1108,7 @@ ms_status ms_read_flux(ms_sim* s, int32_t plane, double* flux) {
 // ---- checkpoint ------------------------------------------------------------
 namespace {
 constexpr char kCkMagic[8] = {'M', 'S', '2', '2', '0', '9', 'C', 'K'};
-constexpr uint32_t kCkVersion = 2;
+constexpr uint32_t kCkVersion = 3;
 
 struct CkHeader {
   char magic[8];
@@ -1111,6 +1118,7 @@ struct CkHeader {
   int64_t nmol;
   int32_t nspecies, pml, ks, jk0, jk1, aux_len;
   int32_t ndet, nfreq, state_rows[ms::kMaxSpecies];
+  int32_t mol_substeps, src_kind;
   int32_t species[ms::kMaxSpecies][3];  // nr, jmax, molecules
   uint64_t nblobs;
 };
@@ -1178,6 +1186,8 @@ CkHeader make_header(ms_sim* s, uint64_t nblobs) {
   h.ndet = s->g.ndet;
   h.nfreq = s->g.nfreq;
   for (int si = 0; si < s->nspecies; ++si) h.state_rows[si] = s->sp[si].rows;
+  h.mol_substeps = s->nsub;
+  h.src_kind = s->src_kind;
   for (int si = 0; si < s->nspecies; ++si) {
     h.species[si][0] = s->sp[si].nr;
     h.species[si][1] = s->sp[si].jmax;

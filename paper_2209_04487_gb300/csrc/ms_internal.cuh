@@ -22,13 +22,29 @@ enum : int {
   kErrTimeout = 8,        // a bounded wait on an asynchronous copy gave up
 };
 
-// Incident pulse parameters of one sim.
+// Incident wave parameters of one sim.
 struct SrcParam {
   double E0;    // V/m
   double w;     // carrier, rad/s
-  double fwhm;  // s
+  double fwhm;  // s: pulse envelope FWHM (MS_SRC_PULSE) or CW turn-on time (MS_SRC_CW)
   double t0;    // s
+  int kind;     // MS_SRC_PULSE or MS_SRC_CW
 };
+
+// Incident field at the TF/SF plane at time t (the formulas of ms_grid_desc).
+__host__ __device__ inline double incident_field(const SrcParam& p, double t) {
+  const double u = t - p.t0;
+  if (p.kind == 1) {
+    double ramp = 1.0;
+    if (t < p.fwhm) {
+      const double r = sin(1.5707963267948966 * (t > 0.0 ? t : 0.0) / p.fwhm);
+      ramp = r * r;
+    }
+    return p.E0 * ramp * cos(p.w * u);
+  }
+  const double x = u / p.fwhm;
+  return p.E0 * exp(-2.772588722239781 * x * x) * cos(p.w * u);
+}
 
 // Per-material coefficients (constant memory).
 struct MaterialCoef {

@@ -177,10 +177,7 @@ __global__ void aux_e_kernel(Grid g) {
   const float ce = g.ce_vac;
   for (int m = 1 + threadIdx.x; m < lim; m += blockDim.x) E1[m] += ce * (0.f - (H1[m] - H1[m - 1]));
   if (threadIdx.x == 0) {
-    const SrcParam p = g.src[s];
-    const double t = (double)(n + 1) * g.dt - p.t0;
-    const double x = t / p.fwhm;
-    E1[0] = (float)(p.E0 * exp(-2.772588722239781 * x * x) * cos(p.w * t));
+    E1[0] = (float)incident_field(g.src[s], (double)(n + 1) * g.dt);
   }
 }
 

@@ -368,3 +368,110 @@ def test_independent_sims_in_one_launch(B):
     assert np.abs(P - o.populations()).max() < 1e-5
     # the two carriers give different responses
     assert np.abs(sim.fields(B.MS_FIELD_E, 0) - sim.fields(B.MS_FIELD_E, 1)).max() > 1e6
+
+
+# Multiscale cadence (Sec. 2): the molecules advance every N-th field step by
+# N dt, under that step's field, and only those steps' E updates take their
+# dipole change.  Both drives (the femtosecond pulse and the CW wave with its
+# sin^2 turn-on) against the oracle at the plain FP32 tolerances.
+@pytest.mark.parametrize("N,src_kind,path", [(4, "pulse", "fused"), (4, "pulse", "streaming"),
+                                             (8, "cw", "fused"), (40, "cw", "streaming")])
+def test_substepped_coupled_matches_oracle(B, N, src_kind, path):
+    row = [2e10, 1.5498, 2e-15, 2e-15] if src_kind == "pulse" else [1e10, 1.5498, 0.5e-15, 0.0]
+    wl = W.custom("coupled substeps", 16, 16, 48, src_k=14, pulses=[row], layer=(22, 26), n_per_sim=150,
+                  species=[W.species_config0(jmax=1)], seed=5, nsteps=480, src_kind=src_kind,
+                  mol_substeps=N)
+    sim = B.Simulation(wl, mol_path=B.MS_MOL_FUSED if path == "fused" else B.MS_MOL_STREAMING)
+    sim.step(wl.nsteps - 1)     # ends just after a molecular step when N divides nsteps
+    sim.step(1)
+    E = sim.fields(B.MS_FIELD_E)
+    P = sim.populations()
+    mu = sim.dipoles()
+    o = CoupledOracle(wl).run(wl.nsteps)
+    Eo, _ = _fields_oracle(o)
+    assert _rel(E, Eo) < 1e-4
+    assert np.abs(P - o.populations()).max() < 1e-5
+    assert np.abs(mu - o.mu).max() < 1e-3 * np.abs(o.mu).max()
+    assert o.populations()[:, 1].max() > 1e-9          # the molecules were driven
+
+
+def test_substepped_prescribed_matches_oracle(B):
+    """Every 40th step (the paper's cadence), strong resonant drive."""
+    N, nsteps = 40, 4000
+    sp = W.Species(nr=128, jmax=4, A=0.05)
+    wl = W.custom("prescribed substeps", 8, 8, 48, n_per_sim=19, species=[sp], layer=(20, 24), seed=3,
+                  nsteps=nsteps, mol_substeps=N)
+    amp, wave = W.prescribed_drive(19, nsteps, wl.dt, E0=3e10, carrier_ev=6.0, fwhm=4e-15, t0=5e-15)
+    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED)
+    sim.set_prescribed(amp, wave)
+    o = PrescribedOracle(wl, amp, wave)
+    # at the pulse peak (t = 5 fs): the dipole is large
+    sim.step(1520)
+    o.run(1520)
+    assert np.abs(sim.dipoles() - o.mu).max() < 1e-4 * np.abs(o.mu).max()
+    assert np.abs(o.mu).max() > 1e-3
+    # after the pulse: the excited wavepacket has left the Franck-Condon
+    # region, the dipole is a small residual of terms of size d sqrt(P_g P_e)
+    # ~ 0.5 a.u., and its FP32 error is bounded on that scale
+    sim.step(nsteps - 1520)
+    o.run(nsteps - 1520)
+    P = sim.populations()
+    Po = o.populations()
+    assert Po[:, 1].max() > 1e-6
+    assert np.abs(P - Po).max() < 1e-5
+    assert np.abs(sim.dipoles() - o.mu).max() < 1e-6 * sp.dipole
+
+
+def test_substepped_checkpoint_resumes_mid_cycle(B, tmp_path):
+    """A checkpoint taken between molecular steps resumes on the same cadence."""
+    wl = W.custom("substep ck", 16, 16, 48, src_k=14, pulses=[[2e10, 1.5498, 1e-15, 0.0]], layer=(22, 26),
+                  n_per_sim=60, species=[W.species_config0(jmax=1)], seed=8, nsteps=200, src_kind="cw",
+                  mol_substeps=7)
+    ref = B.Simulation(wl)
+    ref.step(200)
+    want = (ref.populations(), ref.dipoles(), ref.fields(B.MS_FIELD_E))
+    ref.close()
+    a = B.Simulation(wl)
+    a.step(103)                 # 103 = 14 * 7 + 5: between molecular steps
+    path = str(tmp_path / "mid.ck")
+    a.save(path)
+    a.close()
+    b = B.Simulation(wl)
+    b.load(path)
+    b.step(97)
+    got = (b.populations(), b.dipoles(), b.fields(B.MS_FIELD_E))
+    for x, y in zip(want, got):
+        assert np.array_equal(x, y)
+    # a handle with another cadence refuses the checkpoint
+    import dataclasses
+    c = B.Simulation(dataclasses.replace(wl, mol_substeps=5))
+    with pytest.raises(B.MSError) as e:
+        c.load(path)
+    assert e.value.code == B.MS_EINVAL
+    b.close()
+    c.close()
+
+
+def test_cw_frequency_sweep_matches_oracle(B):
+    """A carrier sweep as independent sims in one launch: CW drive, molecules
+    every 10th step, per-sim populations and excited-surface <R> (Sec. 3's
+    steady-state dissociation experiment, on a short run)."""
+    rows = [[1e10, e, 0.5e-15, 0.0] for e in (1.3, 1.55, 1.8)]
+    wl = W.custom("cw sweep", 12, 12, 48, nsim=3, src_k=14, pulses=rows, layer=(22, 26), n_per_sim=40,
+                  species=[W.species_config0(jmax=1)], seed=17, nsteps=600, src_kind="cw", mol_substeps=10)
+    sim = B.Simulation(wl)
+    sim.step(wl.nsteps)
+    P = sim.populations()
+    absb, Rr = sim.dissociation()
+    o = CoupledOracle(wl).run(wl.nsteps)
+    Po = o.populations()
+    assert np.abs(P - Po).max() < 1e-5
+    Ro = o.excited_R()
+    assert np.abs(Rr[:, 1] - Ro[:, 1]).max() < 1e-3 * Ro[:, 1].max() + 1e-12
+    for s in range(3):
+        E = sim.fields(B.MS_FIELD_E, s)
+        Eo = np.stack([o.f.Ex[s], o.f.Ey[s], o.f.Ez[s]])
+        assert _rel(E, Eo) < 1e-4, s
+    # the sims differ: each carrier drives its own molecules
+    pe = [Po[wl.sim_id == s, 1].mean() for s in range(3)]
+    assert len(set(np.round(pe, 12))) == 3

@@ -21,7 +21,7 @@ def _create(B, wl, mutate=None):
     keep = []
     src = np.ascontiguousarray(wl.src, np.float64)
     g = B.GridDesc(wl.nx, wl.ny, wl.nz, wl.nsim, wl.dx, wl.dt, wl.pml, B.MS_BC_PML, wl.src_k,
-                   src.ctypes.data_as(C.POINTER(C.c_double)))
+                   src.ctypes.data_as(C.POINTER(C.c_double)), B.MS_SRC_PULSE)
     eps = np.array([m[0] for m in wl.materials])
     wp = np.array([m[1] for m in wl.materials])
     ga = np.array([m[2] for m in wl.materials])
@@ -56,12 +56,15 @@ def _wl():
     return W.custom("v", 8, 8, 48, src_k=14, layer=(20, 24), n_per_sim=5, nsteps=10)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "mixed"])
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "cw_substeps"])
 def test_valid_descriptor_reaches_the_device_check(B, precision):
     import torch
 
     def mutate(g, m, d, o, keep):
         o.precision = B.MS_PREC_MIXED_BF16X3 if precision == "mixed" else B.MS_PREC_FP32
+        if precision == "cw_substeps":
+            g.src_kind = B.MS_SRC_CW
+            o.mol_substeps = 40
     rc = _create(B, _wl(), mutate)
     if torch.cuda.is_available():
         assert rc == B.MS_OK
@@ -71,7 +74,8 @@ def test_valid_descriptor_reaches_the_device_check(B, precision):
 
 @pytest.mark.parametrize("what", ["courant", "nx", "pml", "src_in_pml", "material_id", "species_nr",
                                   "jmax", "position", "quaternion", "precision_unknown", "mixed_fused",
-                                  "mixed_nr256", "alloc_half"])
+                                  "mixed_nr256", "alloc_half", "src_kind", "cw_turn_on", "substeps_negative",
+                                  "substeps_huge"])
 def test_invalid_descriptors_are_rejected(B, what):
     def mutate(g, m, d, o, keep):
         if what == "courant":
@@ -109,6 +113,17 @@ def test_invalid_descriptors_are_rejected(B, what):
             d.species[0].nr = 256
         elif what == "alloc_half":
             o.alloc = B._ALLOC(lambda n, c: None)
+        elif what == "src_kind":
+            g.src_kind = 2
+        elif what == "cw_turn_on":
+            g.src_kind = B.MS_SRC_CW
+            bad = np.array([1e9, 1.5, 0.0, 0.0])
+            keep.append(bad)
+            g.src = bad.ctypes.data_as(C.POINTER(C.c_double))
+        elif what == "substeps_negative":
+            o.mol_substeps = -1
+        elif what == "substeps_huge":
+            o.mol_substeps = 1 << 20
     rc = _create(B, _wl(), mutate)
     expect = {"species_nr": B.MS_EUNSUPPORTED, "jmax": B.MS_EUNSUPPORTED,
               "mixed_fused": B.MS_EUNSUPPORTED, "mixed_nr256": B.MS_EUNSUPPORTED}.get(what, B.MS_EINVAL)
