@@ -8,3 +8,4 @@ A0 = 5.29177210903e-11           # m (Bohr radius)
 T_AU = 2.4188843265857e-17       # s (atomic unit of time)
 F_AU = 5.14220674763e11          # V/m (atomic unit of field)
 EA0 = 8.4783536255e-30           # C*m (atomic unit of dipole)
+HARTREE_EV = 27.211386245988     # eV (atomic unit of energy)

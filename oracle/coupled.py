@@ -18,10 +18,19 @@ from __future__ import annotations
 
 import numpy as np
 
+from .bloch import BlochEnsemble
 from .constants import EA0
 from .fdtd import YeeOracle
 from .molecule import SpeciesEnsemble, dtau_au
 from .spectra import FluxDFT
+
+
+def ensemble(sp, quat, dtau):
+    """The molecular model of a species: ro-vibrational wavepackets, or frozen
+    two-level emitters (Bloch equations)."""
+    if getattr(sp, "model", "wavepacket") == "bloch":
+        return BlochEnsemble(sp, quat, dtau)
+    return SpeciesEnsemble(sp, quat, dtau)
 
 
 def molecule_cells(wl):
@@ -50,7 +59,7 @@ class CoupledOracle:
             for s, sp in enumerate(wl.species):
                 idx = np.nonzero(wl.species_id == s)[0]
                 if idx.size:
-                    self.groups.append((idx, SpeciesEnsemble(sp, wl.quat[idx], self.dtau)))
+                    self.groups.append((idx, ensemble(sp, wl.quat[idx], self.dtau)))
         self.mu = np.zeros((self.nmol, 3))
         # detectors = (planes_z, omega): running DFTs after every E half step
         self.dft = FluxDFT(self.f, *detectors) if detectors is not None else None
@@ -120,7 +129,7 @@ class PrescribedOracle:
         for s, sp in enumerate(wl.species):
             idx = np.nonzero(sid == s)[0]
             if idx.size:
-                self.groups.append((idx, SpeciesEnsemble(sp, wl.quat[sel][idx], self.dtau)))
+                self.groups.append((idx, ensemble(sp, wl.quat[sel][idx], self.dtau)))
         self.n = 0
         self.mu = np.zeros((sel.size, 3))
 

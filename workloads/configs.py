@@ -55,6 +55,13 @@ class Species:
     dipole: float = 1.0
     absorber_r: float = 8.5
     absorber_power: float = 0.125
+    # "wavepacket" (the two-surface ro-vibrational model) or "bloch" (frozen
+    # two-level emitter: transition energy w0_ev, dipole along the molecular
+    # axis, optional relaxation times T1, T2 in s, 0 = none)
+    model: str = "wavepacket"
+    w0_ev: float = 0.0
+    T1: float = 0.0
+    T2: float = 0.0
 
     @property
     def nrot(self) -> int:
