@@ -316,6 +316,18 @@ def main():
             "ms_per_step": f["ms"] / a.steps, "molecular_steps_timed": nmolsteps,
             "layout": "fused" if f["path"] == B.MS_MOL_FUSED else "streaming",
             "note": f"CW drive (5 fs sin^2 turn-on), molecules every {nsub}th field step by {nsub} dt"}
+        # the frozen molecules of Fig. 5d: the same ensemble as two-level emitters
+        # (Bloch equations, RK4), transition at the carrier
+        import workloads as W
+        wbl = dataclasses.replace(wl, species=[W.Species(model="bloch", w0_ev=float(wl.src[0][1]),
+                                                         dipole=wl.species[0].dipole)])
+        fb = time_form(path, B.MS_PREC_FP32, w=wbl)
+        bl = form_entry(fb)
+        bl.pop("populations_max_abs_diff_vs_default")
+        bl["cell_updates_per_s"] = job_rate(wl.cells * a.steps, world, fb["ms"] / 1e3)
+        bl["note"] = ("frozen two-level molecules (Bloch equations, one RK4 step per field step, FP64 state); "
+                      "the step is field-bound")
+        other["bloch_frozen"] = bl
         if B.mixed_supported(wl):
             mixed = form_entry(time_form(B.MS_MOL_STREAMING, B.MS_PREC_MIXED_BF16X3))
             mixed["stated_error_vs_fp64"] = ("populations 6e-6 abs, dipoles 6e-6 rel after 300 strongly driven "

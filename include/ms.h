@@ -121,13 +121,29 @@ typedef struct {
   const uint8_t* material_id;
 } ms_materials_desc;
 
-/* One molecular species (atomic units).  Radial grid r_i = rmin + i dR,
+/* One molecular species (atomic units).
+ *
+ * MS_MODEL_WAVEPACKET (Eqs. 3-7): radial grid r_i = rmin + i dR,
  * dR = (rmax - rmin)/(nr - 1), nr in {64, 128, 256}; rotational channels
  * j <= jmax, |m| <= j ((jmax+1)^2 per surface), jmax <= 16.
  * Ground surface De (1 - exp(-a (r - re)))^2 - De (Eq. 6); excited surface
  * A + B exp(-beta (r - rc)) (Eq. 7 is A = 0, B = 2 D_e); constant
  * transition dipole d [e a0]; absorbing mask cos(pi/2 (r-ra)/(rmax-ra))^p
- * for r > ra (ra >= rmax disables it). */
+ * for r > ra (ra >= rmax disables it).
+ *
+ * MS_MODEL_BLOCH (the frozen molecules of the scaling-experiments section,
+ * Fig. 5d): a two-level emitter with its ro-vibrational degrees of freedom
+ * frozen, H = w0 |e><e| - d (n . E)(|g><e| + |e><g|), transition energy
+ * bloch_w0_eV >= 0, transition dipole dipole_ea0 along the molecule frame's
+ * z axis n, optional population relaxation and dephasing times bloch_T1_s,
+ * bloch_T2_s >= 0 (0 = none).  The Bloch vector (u, v, w) = (2 Re rho_eg,
+ * 2 Im rho_eg, rho_ee - rho_gg) starts at (0, 0, -1) and takes one RK4 step
+ * per molecular step with the field held at E^n; the dipole is d u along n.
+ * morse_re is the frozen bond length (Eq. 8 readout: numerator re P_e,
+ * denominator P_e); the other fields are ignored, and the mol_path,
+ * precision and state_form options do not apply to it (its state is three
+ * FP64 numbers per molecule). */
+enum { MS_MODEL_WAVEPACKET = 0, MS_MODEL_BLOCH = 1 };
 typedef struct {
   int32_t nr, jmax;
   double rmin, rmax, mass_me;
@@ -135,6 +151,9 @@ typedef struct {
   double exc_A, exc_B, exc_beta, exc_rc;
   double dipole_ea0;
   double absorber_r, absorber_power;
+  int32_t model;              /* MS_MODEL_WAVEPACKET or MS_MODEL_BLOCH */
+  double bloch_w0_eV;         /* MS_MODEL_BLOCH: transition energy */
+  double bloch_T1_s, bloch_T2_s;  /* MS_MODEL_BLOCH: relaxation times, 0 = none */
 } ms_species;
 
 /* Molecules: species_id, sim_id [n]; pos_m [n][3] absolute position in the
@@ -338,8 +357,9 @@ ms_status ms_timing_end(ms_sim* sim, double out[6], int64_t* steps, int64_t* lau
 ms_status ms_check_bounded_wait(int32_t tries);
 
 /* The molecular kernel layout a species runs in (MS_MOL_FUSED or
- * MS_MOL_STREAMING, after MS_MOL_AUTO resolved it); MS_EINVAL for a NULL
- * handle or a species index out of range. */
+ * MS_MOL_STREAMING, after MS_MOL_AUTO resolved it; a MS_MODEL_BLOCH species
+ * reports MS_MOL_FUSED: one kernel reads and writes its state once per step);
+ * MS_EINVAL for a NULL handle or a species index out of range. */
 int32_t ms_species_path(const ms_sim* sim, int32_t species);
 
 /* Device memory held by the simulation, in bytes. */

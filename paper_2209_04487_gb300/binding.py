@@ -23,6 +23,7 @@ MS_DRIVE_FDTD, MS_DRIVE_PRESCRIBED = 0, 1
 MS_FIELD_E, MS_FIELD_H = 0, 1
 MS_STATE_FULL, MS_STATE_PARITY = 0, 1
 MS_SRC_PULSE, MS_SRC_CW = 0, 1
+MS_MODEL_WAVEPACKET, MS_MODEL_BLOCH = 0, 1
 MS_MOL_AUTO, MS_MOL_FUSED, MS_MOL_STREAMING = 0, 1, 2
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -47,7 +48,8 @@ class SpeciesDesc(C.Structure):
                 ("mass_me", C.c_double), ("morse_De", C.c_double), ("morse_a", C.c_double),
                 ("morse_re", C.c_double), ("exc_A", C.c_double), ("exc_B", C.c_double),
                 ("exc_beta", C.c_double), ("exc_rc", C.c_double), ("dipole_ea0", C.c_double),
-                ("absorber_r", C.c_double), ("absorber_power", C.c_double)]
+                ("absorber_r", C.c_double), ("absorber_power", C.c_double), ("model", C.c_int32),
+                ("bloch_w0_eV", C.c_double), ("bloch_T1_s", C.c_double), ("bloch_T2_s", C.c_double)]
 
 
 class MoleculesDesc(C.Structure):
@@ -155,13 +157,15 @@ class _TorchAllocator:
 
 
 def species_desc(sp) -> SpeciesDesc:
+    bloch = getattr(sp, "model", "wavepacket") == "bloch"
     return SpeciesDesc(sp.nr, sp.jmax, sp.rmin, sp.rmax, sp.mass, sp.De, sp.a, sp.re, sp.A, sp.B,
-                       sp.beta, sp.rc, sp.dipole, sp.absorber_r, sp.absorber_power)
+                       sp.beta, sp.rc, sp.dipole, sp.absorber_r, sp.absorber_power,
+                       MS_MODEL_BLOCH if bloch else MS_MODEL_WAVEPACKET, sp.w0_ev, sp.T1, sp.T2)
 
 
 def mixed_supported(wl) -> bool:
-    """Whether every species of the workload can take the mixed kinetic pass."""
-    return all(sp.nr in (64, 128) for sp in wl.species)
+    """Whether every wavepacket species of the workload can take the mixed kinetic pass."""
+    return all(sp.nr in (64, 128) for sp in wl.species if getattr(sp, "model", "wavepacket") != "bloch")
 
 
 class Simulation:

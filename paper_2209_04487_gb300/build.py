@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libms.so")
-SOURCES = ["ms_api.cu", "yee.cu", "mol.cu"]
+SOURCES = ["ms_api.cu", "yee.cu", "mol.cu", "bloch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcudafe", "--diag_suppress=177"]

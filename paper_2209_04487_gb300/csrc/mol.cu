@@ -319,34 +319,6 @@ cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip)
   return cudaMemcpyToSymbol(c_dip, dip, sizeof(CouplEntry) * kMaxRot * kMaxCoupl);
 }
 
-// Lab-frame field (V/m) driving molecule m during the current step: the
-// replay samples, the prescribed amp x wave, or the components its cell owns
-// on the grid (E^n, before this step's E update).
-__device__ __forceinline__ void lab_field(const MolDev& md, const Grid& g, int prescribed, int m, float E[3],
-                                          int* err) {
-  const long long n = *g.step;
-  if (prescribed) {
-    const long long nn = n < md.nwave ? n : md.nwave - 1;
-    if (n >= md.nwave) atomicOr(err, kErrPrescribedRange);
-    if (md.replay) {
-      const float* e = md.replay + (nn * md.n + m) * 3;
-      E[0] = e[0];
-      E[1] = e[1];
-      E[2] = e[2];
-    } else {
-      const float wv = md.wave[nn];
-      E[0] = md.amp[3 * (long long)m] * wv;
-      E[1] = md.amp[3 * (long long)m + 1] * wv;
-      E[2] = md.amp[3 * (long long)m + 2] * wv;
-    }
-  } else {
-    const long long c = md.cell[m];
-    E[0] = g.E[0][c];
-    E[1] = g.E[1][c];
-    E[2] = g.E[2][c];
-  }
-}
-
 // Local field at molecule m in its own frame (a.u.): fld = (E_perp, E'_z), the
 // phases e^{i m' phi_E} (ph[m' + J], m' = -J..J) of the frame turned about z
 // so that E'_y = 0, and the number of coupling-series terms, until
@@ -2099,7 +2071,7 @@ static int launch_stage2_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
 
 int launch_mol_stage1(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
                       cudaStream_t s) {
-  if (sp.nmol == 0) return 0;
+  if (sp.nmol == 0 || sp.bloch) return 0;
   switch (sp.nr) {
     case 64: return launch_stage1_t<64>(sp, md, g, prescribed, err, s);
     case 128: return launch_stage1_t<128>(sp, md, g, prescribed, err, s);
@@ -2111,6 +2083,7 @@ int launch_mol_stage1(const SpeciesDev& sp, const MolDev& md, const Grid& g, int
 int launch_mol_stage2(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
                       cudaStream_t s) {
   if (sp.nmol == 0) return 0;
+  if (sp.bloch) return launch_bloch_step(sp, md, g, prescribed, err, s);
   switch (sp.nr) {
     case 64: return launch_stage2_t<64>(sp, md, g, prescribed, err, s);
     case 128: return launch_stage2_t<128>(sp, md, g, prescribed, err, s);
@@ -2129,6 +2102,10 @@ static void launch_observe_t(const SpeciesDev& sp, const MolDev& md, cudaStream_
 
 void launch_mol_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s) {
   if (sp.nmol == 0) return;
+  if (sp.bloch) {
+    launch_bloch_observe(sp, md, s);
+    return;
+  }
   switch (sp.nr) {
     case 64: launch_observe_t<64>(sp, md, s); break;
     case 128: launch_observe_t<128>(sp, md, s); break;

@@ -24,6 +24,7 @@ constexpr double kMu0 = 1.25663706212e-6;
 constexpr double kEps0 = 8.8541878128e-12;
 constexpr double kHbarEVs = 6.582119569e-16;
 constexpr double kTau = 2.4188843265857e-17;  // atomic unit of time, s
+constexpr double kHartreeEV = 27.211386245988;  // atomic unit of energy, eV
 constexpr double kEA0 = 8.4783536255e-30;     // atomic unit of dipole, C m
 constexpr double kPi = 3.14159265358979323846;
 
@@ -294,8 +295,41 @@ std::vector<uint16_t> mixed_kinetic_planes(int nr, double dR, double dtau, doubl
   return out;
 }
 
+// P_g, P_e of one species' molecules at t = 0 into the shared population array
+ms_status initial_populations(ms_sim* s, const std::vector<int>& ids, double pg) {
+  const double p[2] = {pg, 0.0};
+  for (size_t q = 0; q < ids.size(); ++q)
+    if (cudaMemcpyAsync(s->md.pop + 2 * (size_t)ids[q], p, 2 * sizeof(double), cudaMemcpyHostToDevice,
+                        s->stream) != cudaSuccess)
+      return MS_ECUDA;
+  return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
+}
+
+// Frozen two-level species (MS_MODEL_BLOCH): rates in atomic units, Bloch
+// vectors at the ground state (0, 0, -1)
+ms_status build_bloch_species(ms_sim* s, int si, const ms_species& d, double dt, const std::vector<int>& ids) {
+  ms::SpeciesDev& sp = s->sp[si];
+  sp.bloch = 1;
+  sp.path = MS_MOL_FUSED;
+  sp.nr = sp.jmax = sp.nrot = sp.rows = sp.rows_g = 0;
+  sp.nmol = (int)ids.size();
+  sp.dtau = dt / kTau;
+  sp.dipole = d.dipole_ea0;
+  sp.theta = d.dipole_ea0 * sp.dtau;
+  sp.bloch_w0 = (float)(d.bloch_w0_eV / kHartreeEV);
+  sp.bloch_g1 = d.bloch_T1_s > 0 ? (float)(kTau / d.bloch_T1_s) : 0.f;
+  sp.bloch_g2 = d.bloch_T2_s > 0 ? (float)(kTau / d.bloch_T2_s) : 0.f;
+  sp.bloch_re = d.morse_re;
+  std::vector<double> y(3 * ids.size(), 0.0);
+  for (size_t q = 0; q < ids.size(); ++q) y[3 * q + 2] = -1.0;
+  MS_TRY(upload(s, &sp.bloch_y, y.data(), y.size()));
+  MS_TRY(upload(s, (int**)&sp.mol, ids.data(), ids.size()));
+  return initial_populations(s, ids, 1.0);
+}
+
 ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const std::vector<int>& ids,
                         int path, bool mixed, bool par) {
+  if (d.model == MS_MODEL_BLOCH) return build_bloch_species(s, si, d, dt, ids);
   ms::SpeciesDev& sp = s->sp[si];
   const int nr = d.nr, J = d.jmax, nrot = (J + 1) * (J + 1);
   // layout: the streaming form unless the caller asks for the fused one
@@ -414,16 +448,7 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   // populations at t = 0
   double n0 = 0.0;
   for (double v : psi0) n0 += v * v * dR;
-  std::vector<double> pop(2 * ids.size());
-  for (size_t q = 0; q < ids.size(); ++q) {
-    pop[2 * q] = n0;
-    pop[2 * q + 1] = 0.0;
-  }
-  for (size_t q = 0; q < ids.size(); ++q)
-    if (cudaMemcpyAsync(s->md.pop + 2 * (size_t)ids[q], &pop[2 * q], 2 * sizeof(double),
-                        cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
-      return MS_ECUDA;
-  return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
+  return initial_populations(s, ids, n0);
 }
 
 ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const ms_molecules_desc* D,
@@ -646,6 +671,14 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
     if (D->n_molecules >= (1LL << 31)) return MS_EUNSUPPORTED;
     for (int si = 0; si < D->n_species; ++si) {
       const ms_species& sp = D->species[si];
+      if (sp.model == MS_MODEL_BLOCH) {  // frozen two-level emitter: its own parameters only
+        if (!(sp.bloch_w0_eV >= 0) || !(sp.bloch_T1_s >= 0) || !(sp.bloch_T2_s >= 0) ||
+            !std::isfinite(sp.bloch_w0_eV) || !std::isfinite(sp.bloch_T1_s) || !std::isfinite(sp.bloch_T2_s) ||
+            !std::isfinite(sp.dipole_ea0) || !std::isfinite(sp.morse_re))
+          return MS_EINVAL;
+        continue;
+      }
+      if (sp.model != MS_MODEL_WAVEPACKET) return MS_EINVAL;
       if (sp.nr != 64 && sp.nr != 128 && sp.nr != 256) return MS_EUNSUPPORTED;
       if (sp.jmax < 0 || sp.jmax > ms::kMaxJ) return MS_EUNSUPPORTED;
       if (!(sp.rmax > sp.rmin) || !(sp.rmin > 0) || !(sp.mass_me > 0) || sp.absorber_power < 0)
@@ -1153,7 +1186,8 @@ std::vector<Blob> state_blobs(ms_sim* s) {
   }
   for (int si = 0; si < s->nspecies; ++si) {
     const ms::SpeciesDev& sp = s->sp[si];
-    b.push_back({sp.psi, (size_t)sp.nmol * sp.rows * sp.nr * sizeof(float2)});
+    if (sp.bloch) b.push_back({sp.bloch_y, (size_t)sp.nmol * 3 * sizeof(double)});
+    else b.push_back({sp.psi, (size_t)sp.nmol * sp.rows * sp.nr * sizeof(float2)});
   }
   if (s->nmol > 0) {
     const size_t n = (size_t)s->nmol;

@@ -120,6 +120,13 @@ struct SpeciesDev {
   double theta;             // d * dtau
   double dipole;            // d (e a0)
   float dR;
+  // frozen two-level molecules (MS_MODEL_BLOCH): Bloch vector per molecule
+  int bloch;
+  double* bloch_y;          // [nmol][3] (u, v, w), FP64
+  double dtau;              // molecular step (a.u.)
+  float bloch_w0;           // transition energy (a.u.)
+  float bloch_g1, bloch_g2; // 1/T1, 1/T2 (a.u.), 0 = none
+  double bloch_re;          // frozen bond length (a0), for the Eq. 8 readout
 };
 
 // One nonzero of an angular coupling row.
@@ -148,6 +155,34 @@ struct MolDev {
   const float* replay;      // replay drive [nwave][n][3] (lab V/m), else null
 };
 
+// Lab-frame field (V/m) driving molecule m during the current step: the
+// replay samples, the prescribed amp x wave, or the components its cell owns
+// on the grid (E^n, before this step's E update).
+__device__ __forceinline__ void lab_field(const MolDev& md, const Grid& g, int prescribed, int m, float E[3],
+                                          int* err) {
+  const long long n = *g.step;
+  if (prescribed) {
+    const long long nn = n < md.nwave ? n : md.nwave - 1;
+    if (n >= md.nwave) atomicOr(err, kErrPrescribedRange);
+    if (md.replay) {
+      const float* e = md.replay + (nn * md.n + m) * 3;
+      E[0] = e[0];
+      E[1] = e[1];
+      E[2] = e[2];
+    } else {
+      const float wv = md.wave[nn];
+      E[0] = md.amp[3 * (long long)m] * wv;
+      E[1] = md.amp[3 * (long long)m + 1] * wv;
+      E[2] = md.amp[3 * (long long)m + 2] * wv;
+    }
+  } else {
+    const long long c = md.cell[m];
+    E[0] = g.E[0][c];
+    E[1] = g.E[1][c];
+    E[2] = g.E[2][c];
+  }
+}
+
 // launchers (yee.cu)
 void launch_yee_h(const Grid& g, cudaStream_t s);
 void launch_yee_e(const Grid& g, cudaStream_t s);
@@ -161,6 +196,10 @@ int launch_mol_stage1(const SpeciesDev& sp, const MolDev& md, const Grid& g, int
 int launch_mol_stage2(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
                       cudaStream_t s);
 void launch_mol_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s);
+// launchers (bloch.cu): the frozen two-level step and its Eq. 8 readout
+int launch_bloch_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
+                      cudaStream_t s);
+void launch_bloch_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s);
 bool mol_step_supported(int nr, int nrot, int path);
 cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip);
 cudaError_t upload_triplet_tables(const CouplEntry* dip);

@@ -56,7 +56,7 @@ def _wl():
     return W.custom("v", 8, 8, 48, src_k=14, layer=(20, 24), n_per_sim=5, nsteps=10)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "mixed", "cw_substeps"])
+@pytest.mark.parametrize("precision", ["fp32", "mixed", "cw_substeps", "bloch"])
 def test_valid_descriptor_reaches_the_device_check(B, precision):
     import torch
 
@@ -65,6 +65,11 @@ def test_valid_descriptor_reaches_the_device_check(B, precision):
         if precision == "cw_substeps":
             g.src_kind = B.MS_SRC_CW
             o.mol_substeps = 40
+        if precision == "bloch":       # the wavepacket fields are ignored, even invalid ones
+            d.species[0].model = B.MS_MODEL_BLOCH
+            d.species[0].bloch_w0_eV = 1.5
+            d.species[0].bloch_T2_s = 1e-14
+            d.species[0].nr = 100
     rc = _create(B, _wl(), mutate)
     if torch.cuda.is_available():
         assert rc == B.MS_OK
@@ -75,7 +80,7 @@ def test_valid_descriptor_reaches_the_device_check(B, precision):
 @pytest.mark.parametrize("what", ["courant", "nx", "pml", "src_in_pml", "material_id", "species_nr",
                                   "jmax", "position", "quaternion", "precision_unknown", "mixed_fused",
                                   "mixed_nr256", "alloc_half", "src_kind", "cw_turn_on", "substeps_negative",
-                                  "substeps_huge"])
+                                  "substeps_huge", "model_unknown", "bloch_w0", "bloch_T1"])
 def test_invalid_descriptors_are_rejected(B, what):
     def mutate(g, m, d, o, keep):
         if what == "courant":
@@ -124,6 +129,15 @@ def test_invalid_descriptors_are_rejected(B, what):
             o.mol_substeps = -1
         elif what == "substeps_huge":
             o.mol_substeps = 1 << 20
+        elif what == "model_unknown":
+            d.species[0].model = 5
+        elif what == "bloch_w0":
+            d.species[0].model = B.MS_MODEL_BLOCH
+            d.species[0].bloch_w0_eV = -1.0
+        elif what == "bloch_T1":
+            d.species[0].model = B.MS_MODEL_BLOCH
+            d.species[0].bloch_w0_eV = 1.0
+            d.species[0].bloch_T1_s = float("nan")
     rc = _create(B, _wl(), mutate)
     expect = {"species_nr": B.MS_EUNSUPPORTED, "jmax": B.MS_EUNSUPPORTED,
               "mixed_fused": B.MS_EUNSUPPORTED, "mixed_nr256": B.MS_EUNSUPPORTED}.get(what, B.MS_EINVAL)
