@@ -38,8 +38,9 @@ def _args():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--molecules", type=int, default=50000)
-    p.add_argument("--preroll", type=int, default=60,
-                   help="untimed steps that bring the pulse to the molecular layer")
+    p.add_argument("--preroll", type=int, default=None,
+                   help="untimed steps before warm-up; default: the timed steps are centred on the "
+                        "pulse peak at the molecular layer")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--mol-path", default="auto", choices=["auto", "fused", "streaming"])
@@ -182,7 +183,7 @@ def run_reference(a):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * sum(tsteps) / len(tsteps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": _config(wl),
+            "data": "synthetic", "config": _config(wl, peak_preroll(wl, a.warmup, a.steps)),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cpu_desc(), "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -190,13 +191,49 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
-def _config(wl):
+def peak_preroll(wl, warmup: int, steps: int) -> int:
+    """Untimed steps that centre the timed window on the pulse peak at the
+    molecular layer: the peak leaves the TF/SF plane at t0 and crosses one
+    cell per two steps (Courant number 1/2)."""
+    k0, k1 = wl.meta["layer"]
+    n_peak = int(round(float(wl.src[0][3]) / wl.dt)) + 2 * ((k0 + k1) // 2 - wl.src_k)
+    return max(0, n_peak - warmup - steps // 2)
+
+
+def fdtd_bytes(wl):
+    """Algorithmic bytes of the two half steps per step: H reads E and reads
+    and writes H (36 B per cell), E reads H, the material id and reads and
+    writes E (37 B); the CPML cells add two psi values read and written
+    (16 B) to each, and the Drude cells of the metal slab the current
+    (24 B) to the E step."""
+    import numpy as np
+    cells = wl.cells * wl.nsim
+    pml_cells = 2 * wl.pml * wl.nx * wl.ny * wl.nsim if wl.bc_z == "pml" else 0
+    metal = {i for i, m in enumerate(wl.materials) if m[1] > 0}
+    drude = int(np.isin(np.asarray(wl.mat_id), list(metal)).sum()) if metal else 0
+    return 36 * cells + 16 * pml_cells, 37 * cells + 16 * pml_cells + 24 * drude
+
+
+def fdtd_roofline(wl, h_ms, e_ms, peak):
+    hb, eb = fdtd_bytes(wl)
+    out = {"bound": "hbm", "peak": peak, "unit": "GB/s"}
+    for name, b, ms in (("yee_h_kernel", hb, h_ms), ("yee_e_kernel", eb, e_ms)):
+        ach = b / (ms / 1e3) / 1e9
+        out[name] = {"achieved": ach, "frac": ach / peak, "bytes_per_launch": b, "ms_per_launch": ms,
+                     "traffic": _kernel_traffic(name)}
+    out["note"] = ("per half step, CUDA events around each phase (the E phase also holds the one-thread "
+                   "step-counter kernel); the fields are evicted from L2 by the molecular state every step")
+    return out
+
+
+def _config(wl, preroll):
     sp = wl.species[0]
     return {"workload": "split-ring array 128x128x192 (2 nm, Ag Drude rings on glass, CPML z, TF/SF "
                         f"pulse) + {wl.n_molecules} molecules (Nr {sp.nr}, J<={sp.jmax}, 2 surfaces)",
             "cells": wl.cells, "molecules": wl.n_molecules, "nr": sp.nr, "jmax": sp.jmax,
             "form": "plain FP32 (FP64 accumulators)",
-            "preroll": "pulse advanced 60 untimed steps so every molecule sees a non-zero field",
+            "preroll": f"{preroll} untimed steps: the timed steps are centred on the pulse peak at the "
+                       "molecular layer, where the local fields, and the coupling series' term count, are largest",
             "l2": "inputs larger than L2 "
             f"(wavepacket state {2 * sp.nrot * sp.nr * 8 * wl.n_molecules / 1e9:.2f} GB per step)",
             "parallelism": "replicas"}
@@ -232,19 +269,23 @@ def main():
 
     wl = _workload(a.molecules)
     path = {"auto": B.MS_MOL_AUTO, "fused": B.MS_MOL_FUSED, "streaming": B.MS_MOL_STREAMING}[a.mol_path]
+    preroll = peak_preroll(wl, a.warmup, a.steps) if a.preroll is None else a.preroll
+    ck_path = None   # the main form's state at the start of its timed window (for e2e)
 
-    def time_form(mol_path, precision, clocks=False, state_form=0, detectors=None, w=None):
+    def time_form(mol_path, precision, clocks=False, state_form=0, detectors=None, w=None, save_to=None):
         """Preroll, warm-up, then a.steps timed steps of one form (CUDA events on
         the library's stream, max over ranks) and its phase timings."""
         sim = B.Simulation(w or wl, mol_path=mol_path, precision=precision, state_form=state_form)
         if detectors is not None:
             sim.set_detectors(*detectors)
         form_path = sim.species_path(0)
-        # the TF/SF wave needs ~40 steps to reach the molecular layer: before that
-        # the molecules see E' = 0 and skip the coupling work, which is not the
-        # regime the step is measured in
-        sim.step(a.preroll)
+        # the molecules' work depends on the local field (the coupling series
+        # runs until its terms fall below 1e-10): the timed steps sit at the
+        # pulse peak, not in the near-zero field before the pulse arrives
+        sim.step(preroll)
         sim.step(a.warmup)
+        if save_to is not None:
+            sim.save(save_to)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -270,7 +311,28 @@ def main():
         return {"ms": ms_, "phases": ph, "nsteps": nst, "launches": nlaunch, "clocks": cl, "P": Pf,
                 "norm_err": nerr, "path": form_path}
 
-    main_form = time_form(path, B.MS_PREC_FP32, clocks=True)
+    # the e2e leg resumes from this state: in memory-backed storage when it fits
+    import shutil
+    import tempfile
+    sp0 = wl.species[0]
+    ck_bytes = 16 * sp0.nr * sp0.nrot * wl.n_molecules + 60 * wl.cells * wl.nsim
+    ck_dir = None
+    if not a.no_e2e:
+        for d in ("/dev/shm", None):
+            try:
+                if d is not None and (not os.path.isdir(d) or shutil.disk_usage(d).free < 2 * ck_bytes):
+                    continue
+                ck_dir = tempfile.mkdtemp(prefix="ms_bench_", dir=d)
+                if shutil.disk_usage(ck_dir).free < 2 * ck_bytes:
+                    shutil.rmtree(ck_dir)
+                    ck_dir = None
+                    continue
+                break
+            except OSError:
+                ck_dir = None
+        if ck_dir is not None:
+            ck_path = os.path.join(ck_dir, f"rank{rank}.ck")
+    main_form = time_form(path, B.MS_PREC_FP32, clocks=True, save_to=ck_path)
     ms, phases, nsteps, launches = main_form["ms"], main_form["phases"], main_form["nsteps"], main_form["launches"]
     cl, P, norm_err = main_form["clocks"], main_form["P"], main_form["norm_err"]
     fused = main_form["path"] == B.MS_MOL_FUSED
@@ -307,7 +369,7 @@ def main():
         wcw = dataclasses.replace(wl, src_kind="cw", mol_substeps=nsub,
                                   src=np.array([[r[0], r[1], 5e-15, 0.0] for r in wl.src]))
         f = time_form(path, B.MS_PREC_FP32, w=wcw)
-        t0 = a.preroll + a.warmup
+        t0 = preroll + a.warmup
         nmolsteps = sum(1 for n in range(t0, t0 + a.steps) if n % nsub == 0)
         other["cw_substeps40"] = {
             "value": job_rate(wl.n_molecules * nmolsteps, world, f["ms"] / 1e3), "unit": UNIT,
@@ -375,24 +437,35 @@ def main():
                  "unit": "GB/s", "frac": step_bytes / (per_step(1) / 1e3) / 1e9 / peak,
                  "bytes_per_step": step_bytes, "ms_per_step": per_step(1),
                  "note": "molecular step (all its kernels) vs one read and one write of the FP32 state"}
+    roof_fdtd = fdtd_roofline(wl, per_step(0), per_step(2), peak)
 
     e2e = None
     if not a.no_e2e:
+        # through the public API: a handle created from the host inputs resumes the
+        # run from the checkpoint of the main form's timed window (file -> host ->
+        # device), then steps once at a time, reading every population back
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = B.Simulation(wl, mol_path=path)
         host_in = (wl.mat_id.nbytes + wl.pos.nbytes + wl.quat.nbytes + wl.species_id.nbytes
                    + wl.sim_id.nbytes)
+        if ck_path is not None:
+            s2.load(ck_path)
+            host_in += os.path.getsize(ck_path)
         for _ in range(a.steps):
             s2.step(1)
             s2.populations()
         t1 = time.perf_counter()
         s2.close()
+        if ck_dir is not None:
+            shutil.rmtree(ck_dir, ignore_errors=True)
         e2e_s = max_over_ranks(t1 - t0, dist, "cuda")
+        start = ("the checkpoint of the timed window (ms_load)" if ck_path is not None
+                 else "t = 0 (no room for the checkpoint: early-time steps)")
         e2e = {"value": job_rate(wl.n_molecules * a.steps, world, e2e_s), "unit": UNIT,
                "h2d_bytes_per_step": host_in / a.steps, "d2h_bytes_per_step": 16 * wl.n_molecules,
-               "note": "ms_create from host inputs + per step ms_step(1) and a D2H read of all "
-                       "populations, host wall clock"}
+               "note": f"ms_create from host inputs, resume from {start}, then per step ms_step(1) and a "
+                       "D2H read of all populations; host wall clock"}
 
     cpu = None
     if rank == 0 and not a.no_cpu_baseline:
@@ -405,11 +478,12 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": _config(wl), "cell_updates_per_s": cells_rate,
+                "config": _config(wl, preroll), "cell_updates_per_s": cells_rate,
                 "phases_ms_per_step": {"h": phases[0] / nsteps, "molecules": phases[1] / nsteps,
                                        "e": phases[2] / nsteps, "molecules_stage1": phases[4] / nsteps,
                                        "molecules_stage2": phases[5] / nsteps},
                 "roofline": roof, "roofline_kinetic": roof_kin, "roofline_molecular_step": roof_step,
+                "roofline_fdtd": roof_fdtd,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
                 "clocks": cl, "norm_bookkeeping_max_err": norm_err,
                 "forms": {"plain_fp32": {"value": value, "unit": UNIT, "ms_per_step": ms / a.steps,

@@ -836,9 +836,8 @@ static void step_once(ms_sim* s, float2* scratch, const FieldRecorder* rec = nul
   int launched = 0;
   if (s->timing) mark(s);
   if (fdtd) {
-    ms::launch_yee_h(s->g, s->stream);
-    ms::launch_aux_h(s->g, s->stream);
-    launched += 1 + (s->g.ks >= 0);
+    ms::launch_yee_h(s->g, s->stream);  // with the incident lines' H half step
+    ++launched;
   }
   if (rec) {
     ms::launch_record_fields(s->g, s->md.cell, rec->ids, rec->m, rec->out, s->stream);
@@ -861,19 +860,18 @@ static void step_once(ms_sim* s, float2* scratch, const FieldRecorder* rec = nul
   if (fdtd) {
     ms::Grid ge = s->g;
     if (!molecular) ge.mk1 = ge.mk0;  // no molecular slab: the dipoles did not change
-    ms::launch_yee_e(ge, s->stream);
-    ms::launch_aux_e(s->g, s->stream);
-    launched += 1 + (s->g.ks >= 0);
+    ms::launch_yee_e(ge, s->stream);  // with the incident lines' E half step
+    ++launched;
     if (s->g.ndet > 0) {
       ms::launch_dft(s->g, s->stream);
       ++launched;
     }
   }
+  if (s->timing) mark(s);  // the phases end here; the counter runs between steps
   ms::launch_step_counter(s->d_step, s->stream);
   ++launched;
   ++s->steps;
   if (s->timing) {
-    mark(s);
     s->timed_steps++;
     s->launches += launched;
   }

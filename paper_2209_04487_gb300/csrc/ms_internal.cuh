@@ -186,8 +186,6 @@ __device__ __forceinline__ void lab_field(const MolDev& md, const Grid& g, int p
 // launchers (yee.cu)
 void launch_yee_h(const Grid& g, cudaStream_t s);
 void launch_yee_e(const Grid& g, cudaStream_t s);
-void launch_aux_h(const Grid& g, cudaStream_t s);
-void launch_aux_e(const Grid& g, cudaStream_t s);
 
 // launchers (mol.cu)
 // one species' molecular step in two stages (see mol.cu); each returns the kernels it launched

@@ -57,6 +57,38 @@ def test_fields_match_oracle(B, geo, nx, ny, nz, steps):
     assert np.abs(Eo).max() > 1e8
 
 
+@pytest.mark.parametrize("nx,ny,nz,nsim", [(13, 7, 33, 2), (40, 9, 20, 1)])
+def test_periodic_z_ragged_tiles_match_oracle(B, nx, ny, nz, nsim):
+    """Periodic z (no absorber, no source), grid sizes that leave ragged
+    32 x 8 x 8 tiles in every direction, a Drude block and random seeded
+    initial fields: the marching kernels' wraps and tile edges."""
+    def geo(nx_, ny_, nz_):
+        m = np.zeros((nz_, ny_, nx_), np.uint8)
+        m[nz_ // 3: nz_ // 2, 1: ny_ - 1, 2: nx_ - 3] = W.configs.MAT_SILVER
+        m[2 * nz_ // 3:] = W.configs.MAT_GLASS
+        return m
+    wl = W.custom("periodic", nx, ny, nz, nsim=nsim, pml=0, bc_z="periodic", src_k=-1, geometry=geo,
+                  n_per_sim=0, nsteps=150)
+    rng = np.random.default_rng(nx * ny + nz)
+    E0 = rng.standard_normal((nsim, 3, nz, ny, nx)) * 1e8
+    H0 = rng.standard_normal((nsim, 3, nz, ny, nx)) * 1e5
+    sim = B.Simulation(wl)
+    o = CoupledOracle(wl)
+    for s_ in range(nsim):
+        sim.write_fields(B.MS_FIELD_E, s_, E0[s_])
+        sim.write_fields(B.MS_FIELD_H, s_, H0[s_])
+    E0f, H0f = E0.astype(np.float32).astype(np.float64), H0.astype(np.float32).astype(np.float64)
+    o.f.Ex[:], o.f.Ey[:], o.f.Ez[:] = E0f[:, 0], E0f[:, 1], E0f[:, 2]
+    o.f.Hx[:], o.f.Hy[:], o.f.Hz[:] = H0f[:, 0], H0f[:, 1], H0f[:, 2]
+    sim.step(wl.nsteps)
+    o.run(wl.nsteps)
+    for s_ in range(nsim):
+        E, H = sim.fields(B.MS_FIELD_E, s_), sim.fields(B.MS_FIELD_H, s_)
+        Eo, Ho = _fields_oracle(o, s_)
+        assert _rel(E, Eo) < 1e-4, s_
+        assert _rel(H, Ho) < 1e-4, s_
+
+
 @pytest.mark.parametrize("nr,jmax,nmol,path", [
     (64, 1, 37, "fused"), (64, 1, 37, "streaming"), (128, 4, 19, "fused"), (128, 4, 19, "streaming"),
     (64, 8, 9, "fused"), (64, 8, 9, "streaming"), (256, 2, 5, "streaming"), (128, 8, 4, "streaming"),
