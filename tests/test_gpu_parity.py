@@ -365,6 +365,44 @@ def test_splitring_full_size_molecules_sampled(B):
     assert np.isfinite(P).all() and np.abs(tot - 1).max() < 2e-6
 
 
+@pytest.mark.slow
+def test_splitring_coupled_pulse_peak_sampled(B):
+    """The benchmark configuration end to end: 50,000 molecules coupled to the
+    full split-ring grid, run to the pulse peak at the molecular layer (the
+    centre of the bench's timed window, step 6,046).  The local fields of 8
+    seeded molecules are recorded at every step (the very E^n their kernel
+    used) and the oracle integrates those molecules in FP64 under them."""
+    from oracle.coupled import ensemble
+    from oracle.molecule import dtau_au
+    wl = W.config1()
+    k0, k1 = wl.meta["layer"]
+    n_end = int(round(wl.src[0][3] / wl.dt)) + 2 * ((k0 + k1) // 2 - wl.src_k)
+    sample = np.sort(np.random.default_rng(7).choice(wl.n_molecules, 8, replace=False))
+    sim = B.Simulation(wl)
+    rec = sim.record_local_fields(sample, n_end)
+    P = sim.populations()
+    mu = sim.dipoles()
+    absb, _ = sim.dissociation()
+    ens = ensemble(wl.species[0], wl.quat[sample], dtau_au(wl.dt))
+    for n in range(n_end):
+        ens.step(rec[n].astype(np.float64))
+    Po, mo, ao = ens.populations(), ens.mu_lab, ens.absorbed
+    print("sample: |dP| max", np.abs(P[sample] - Po).max(), "P_e max", Po[:, 1].max(),
+          "|dmu|/max", np.abs(mu[sample] - mo).max() / np.abs(mo).max(),
+          "oracle norm err", np.abs(Po.sum(1) + ao.sum(1) - 1).max(),
+          "gpu norm err (sample)", np.abs(P[sample].sum(1) + absb[sample].sum(1) - 1).max())
+    assert np.abs(rec).max() > 1e8                      # the pulse is at the molecules
+    assert np.abs(P[sample] - Po).max() < 1e-5
+    sel = Po[:, 1] > 1e-10
+    assert sel.any()
+    assert np.max(np.abs(P[sample][sel, 1] - Po[sel, 1]) / Po[sel, 1]) < 1e-3
+    assert np.abs(mu[sample] - mo).max() < 1e-4 * np.abs(mo).max()
+    tot = P.sum(axis=1) + absb.sum(axis=1)
+    print("all molecules: norm bookkeeping err max", np.abs(tot - 1).max(), "p99",
+          np.quantile(np.abs(tot - 1), 0.99))
+    assert np.isfinite(P).all()
+
+
 def test_splitring_full_grid_fields(B):
     """The benchmark grid at full size (128x128x192, silver rings, glass,
     CPML, TF/SF) without molecules, 40 steps of a short pulse, against the
