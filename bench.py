@@ -390,6 +390,31 @@ def main():
         bl["note"] = ("frozen two-level molecules (Bloch equations, one RK4 step per field step, FP64 state); "
                       "the step is field-bound")
         other["bloch_frozen"] = bl
+        # the small workload (32x32x64, 1,000 molecules): launch-bound, so the
+        # captured-graph replay of ms_step matters; timed with host wall clock
+        # around ms_step(a.steps) and a synchronize, graphs on and off
+        import workloads as W
+        w0 = W.config0()
+        small = {}
+        for name, gflag in (("graphs", B.MS_GRAPHS_AUTO), ("eager", B.MS_GRAPHS_OFF)):
+            sm = B.Simulation(w0, step_graphs=gflag)
+            sm.step(1000 - a.warmup - 8)        # the pulse peak of this workload is at step 1000
+            sm.step(a.warmup + 8)
+            torch.cuda.synchronize()
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(sm.stream)
+            sm.step(a.steps)
+            ev1.record(sm.stream)
+            torch.cuda.synchronize()
+            ms_ = max_over_ranks(ev0.elapsed_time(ev1), dist, "cuda")
+            small[name] = {"value": job_rate(w0.n_molecules * a.steps, world, ms_ / 1e3), "unit": UNIT,
+                           "ms_per_step": ms_ / a.steps}
+            sm.close()
+        small["note"] = ("config0 vacuum 32x32x64 with 1,000 molecules (Nr 64, J <= 1) at its pulse peak; "
+                         "ms_step replays whole cycles from a captured CUDA graph (graphs) or launches "
+                         "every kernel (eager)")
+        other["small_workload"] = small
         if B.mixed_supported(wl):
             mixed = form_entry(time_form(B.MS_MOL_STREAMING, B.MS_PREC_MIXED_BF16X3))
             mixed["stated_error_vs_fp64"] = ("populations 6e-6 abs, dipoles 6e-6 rel after 300 strongly driven "

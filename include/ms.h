@@ -84,6 +84,13 @@ enum { MS_MOL_AUTO = 0, MS_MOL_FUSED = 1, MS_MOL_STREAMING = 2 };
  * full state.  Parity-reduced species need J <= 4, and the fused layout
  * only at N_r = 128 (MS_EUNSUPPORTED otherwise). */
 enum { MS_STATE_FULL = 0, MS_STATE_PARITY = 1 };
+/* Step replay.  MS_GRAPHS_AUTO: ms_step captures the launches of whole
+ * molecular cycles (at least 8 field steps, a multiple of mol_substeps) once
+ * into a CUDA graph and replays it, and runs leftover steps eagerly; it runs
+ * every step eagerly while phase timing is on or when the stream is already
+ * being captured by the caller.  MS_GRAPHS_OFF: always eager.  Both give the
+ * same results bit for bit. */
+enum { MS_GRAPHS_AUTO = 0, MS_GRAPHS_OFF = 1 };
 
 /* Grid and source.  dt must satisfy dt <= dx/(sqrt(3) c) (checked).
  * src_plane_z: absolute z index of the TF/SF plane (total field for
@@ -188,6 +195,7 @@ typedef struct {
   void* stream;
   int32_t mol_path;     /* MS_MOL_AUTO, MS_MOL_FUSED or MS_MOL_STREAMING */
   int32_t state_form;   /* MS_STATE_FULL or MS_STATE_PARITY */
+  int32_t step_graphs;  /* MS_GRAPHS_AUTO or MS_GRAPHS_OFF (see ms_step) */
 } ms_options;
 
 /* Create a simulation: validates the descriptors, builds the species
@@ -200,7 +208,10 @@ ms_status ms_create(const ms_grid_desc* grid, const ms_materials_desc* materials
 
 /* Advance n coupled steps (n >= 0) on the handle's stream, asynchronously.
  * Step order: H update, molecular step under E^n, polarization change,
- * E update (the paper's leap-frog with the molecular current). */
+ * E update (the paper's leap-frog with the molecular current).  With
+ * MS_GRAPHS_AUTO the launches of whole cycles replay from a CUDA graph
+ * captured on first use (and again after ms_set_prescribed_field,
+ * ms_set_replay_field or ms_set_detectors change what the kernels read). */
 ms_status ms_step(ms_sim* sim, int64_t n);
 
 /* Allocation-free stepping.  The paper has no counterpart: this is a library

@@ -24,6 +24,7 @@ MS_FIELD_E, MS_FIELD_H = 0, 1
 MS_STATE_FULL, MS_STATE_PARITY = 0, 1
 MS_SRC_PULSE, MS_SRC_CW = 0, 1
 MS_MODEL_WAVEPACKET, MS_MODEL_BLOCH = 0, 1
+MS_GRAPHS_AUTO, MS_GRAPHS_OFF = 0, 1
 MS_MOL_AUTO, MS_MOL_FUSED, MS_MOL_STREAMING = 0, 1, 2
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -62,7 +63,7 @@ class MoleculesDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mol_substeps", C.c_int32), ("drive", C.c_int32),
                 ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p),
-                ("mol_path", C.c_int32), ("state_form", C.c_int32)]
+                ("mol_path", C.c_int32), ("state_form", C.c_int32), ("step_graphs", C.c_int32)]
 
 
 def _load() -> C.CDLL:
@@ -174,7 +175,8 @@ class Simulation:
 
     def __init__(self, wl, *, drive: int = MS_DRIVE_FDTD, precision: int = MS_PREC_FP32,
                  with_molecules: bool = True, use_torch: bool = True, stream=None,
-                 mol_path: int = MS_MOL_AUTO, allocator=None, state_form: int = 0):
+                 mol_path: int = MS_MOL_AUTO, allocator=None, state_form: int = 0,
+                 step_graphs: int = 0):
         self.wl = wl
         self._keep = []
         src = np.ascontiguousarray(wl.src, np.float64) if wl.src_k >= 0 else None
@@ -205,6 +207,7 @@ class Simulation:
         opts.drive = drive
         opts.mol_path = mol_path
         opts.state_form = state_form
+        opts.step_graphs = step_graphs
         self.stream = None
         if use_torch:
             import torch

@@ -67,6 +67,11 @@ struct ms_sim {
   int64_t steps = 0;
   int64_t nwave = 0;
   int nsub = 1;         // molecular step every nsub field steps
+  // step replay from a CUDA graph of gsteps steps starting at phase 0
+  bool graphs = true;
+  cudaGraphExec_t gexec = nullptr;
+  int gsteps = 0;
+  bool gdirty = true;   // kernel arguments changed since the capture
   int src_kind = 0;     // MS_SRC_PULSE or MS_SRC_CW
   double dx = 0.0;      // cell size (m)
   ms::Grid g{};
@@ -96,6 +101,8 @@ struct ms_sim {
   }
   void release() {
     if (stream) cudaStreamSynchronize(stream);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
     for (cudaEvent_t e : events) cudaEventDestroy(e);
     events.clear();
     for (void* p : blocks) {
@@ -460,6 +467,7 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
   s->dx = dx;
   s->drive = O ? O->drive : MS_DRIVE_FDTD;
   s->nsub = O && O->mol_substeps > 1 ? O->mol_substeps : 1;
+  s->graphs = !(O && O->step_graphs == MS_GRAPHS_OFF);
   s->src_kind = G->src_plane_z >= 0 ? G->src_kind : 0;
   s->nmol = D ? D->n_molecules : 0;
   s->nspecies = D ? D->n_species : 0;
@@ -663,6 +671,7 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
   if (O && ((O->alloc == nullptr) != (O->free == nullptr))) return MS_EINVAL;
   if (O && (O->mol_path < MS_MOL_AUTO || O->mol_path > MS_MOL_STREAMING)) return MS_EINVAL;
   if (O && O->state_form != MS_STATE_FULL && O->state_form != MS_STATE_PARITY) return MS_EINVAL;
+  if (O && O->step_graphs != MS_GRAPHS_AUTO && O->step_graphs != MS_GRAPHS_OFF) return MS_EINVAL;
   const bool par = O && O->state_form == MS_STATE_PARITY;
   if (D && D->n_molecules > 0) {
     if (D->n_species <= 0 || D->n_species > ms::kMaxSpecies || !D->species || !D->species_id ||
@@ -877,9 +886,52 @@ static void step_once(ms_sim* s, float2* scratch, const FieldRecorder* rec = nul
   }
 }
 
+// Capture the launches of s->gsteps steps from phase 0 into a graph.  The
+// host step count is restored: capturing runs nothing.
+static ms_status capture_cycle(ms_sim* s) {
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = nullptr;
+  s->gsteps = s->nsub * std::max(1, (8 + s->nsub - 1) / s->nsub);
+  const int64_t saved = s->steps;
+  if (cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return MS_ECUDA;
+  for (int q = 0; q < s->gsteps; ++q) step_once(s, nullptr);
+  s->steps = saved;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s->stream, &g);
+  if (e != cudaSuccess || !g) {
+    cudaGetLastError();
+    return MS_ECUDA;
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&s->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    s->gexec = nullptr;
+    return MS_ECUDA;
+  }
+  s->gdirty = false;
+  return MS_OK;
+}
+
 ms_status ms_step(ms_sim* s, int64_t n) {
   if (!s || n < 0) return MS_EINVAL;
   if (s->drive == MS_DRIVE_PRESCRIBED && s->nmol > 0 && s->steps + n > s->nwave) return MS_EINVAL;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s->stream, &cs) != cudaSuccess) return MS_ECUDA;
+  if (s->graphs && !s->timing && cs == cudaStreamCaptureStatusNone) {
+    while (n > 0 && s->steps % s->nsub != 0) {  // to the start of a molecular cycle
+      step_once(s, nullptr);
+      --n;
+    }
+    const int L = s->nsub * std::max(1, (8 + s->nsub - 1) / s->nsub);
+    if (n >= L) {
+      if (!s->gexec || s->gdirty || s->gsteps != L) MS_TRY(capture_cycle(s));
+      for (; n >= L; n -= L) {
+        if (cudaGraphLaunch(s->gexec, s->stream) != cudaSuccess) return MS_ECUDA;
+        s->steps += L;
+      }
+    }
+  }
   for (int64_t q = 0; q < n; ++q) step_once(s, nullptr);
   return cudaGetLastError() == cudaSuccess ? MS_OK : MS_ECUDA;
 }
@@ -1007,6 +1059,7 @@ ms_status ms_read_dipoles(ms_sim* s, int64_t first, int64_t count, double* mu) {
 
 ms_status ms_set_prescribed_field(ms_sim* s, const float* amp, const float* wave, int64_t nsteps) {
   if (!s || !amp || !wave || nsteps <= 0 || s->drive != MS_DRIVE_PRESCRIBED) return MS_EINVAL;
+  s->gdirty = true;
   if (s->md.amp == nullptr) MS_TRY(upload(s, (float**)&s->md.amp, amp, 3 * (size_t)(s->nmol > 0 ? s->nmol : 1)));
   else if (cudaMemcpyAsync((void*)s->md.amp, amp, 3 * sizeof(float) * s->nmol, cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
     return MS_ECUDA;
@@ -1020,6 +1073,7 @@ ms_status ms_set_prescribed_field(ms_sim* s, const float* amp, const float* wave
 
 ms_status ms_set_replay_field(ms_sim* s, const float* E, int64_t nsteps) {
   if (!s || !E || nsteps <= 0 || s->drive != MS_DRIVE_PRESCRIBED) return MS_EINVAL;
+  s->gdirty = true;
   float* d = nullptr;
   MS_TRY(upload(s, &d, E, (size_t)nsteps * 3 * (size_t)(s->nmol > 0 ? s->nmol : 1)));
   s->md.replay = d;
@@ -1080,6 +1134,7 @@ ms_status ms_set_detectors(ms_sim* s, const int32_t* planes_z, int32_t nplanes, 
   if (!s || !planes_z || !omega || s->drive != MS_DRIVE_FDTD || nplanes < 1 || nplanes > 16 || nfreq < 1 ||
       nfreq > 512)
     return MS_EINVAL;
+  s->gdirty = true;
   for (int d = 0; d < nplanes; ++d)
     if (planes_z[d] < 1 || planes_z[d] >= s->g.nz - 1) return MS_EINVAL;
   for (int f = 0; f < nfreq; ++f)
