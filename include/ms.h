@@ -63,7 +63,14 @@ typedef enum {
 } ms_status;
 
 enum { MS_BC_PML = 0, MS_BC_PERIODIC = 1 };
-enum { MS_PREC_FP32 = 0, MS_PREC_MIXED_BF16X3 = 1 };
+/* Arithmetic of the kinetic pass (the section on the split-operator
+ * propagator).  MS_PREC_FP32: FP32 FFTs.  MS_PREC_MIXED_F16X3: the circulant
+ * (K - I) applied to every state row as a tensor-core GEMM on split FP16
+ * operands (x = hi + lo after an exact power-of-two scaling of each row and
+ * of the matrix, three products hi*hi + hi*lo + lo*hi, FP32 accumulation),
+ * which carries about 22 bits of each operand; the streaming layout only,
+ * N_r 64 or 128 (MS_EUNSUPPORTED otherwise). */
+enum { MS_PREC_FP32 = 0, MS_PREC_MIXED_F16X3 = 1 };
 enum { MS_DRIVE_FDTD = 0, MS_DRIVE_PRESCRIBED = 1 };
 enum { MS_FIELD_E = 0, MS_FIELD_H = 1 };
 /* Molecular kernel layout.  MS_MOL_FUSED keeps each molecule's state in
@@ -182,7 +189,7 @@ typedef struct {
  * caching allocator); when NULL the library uses cudaMalloc/cudaFree.
  * stream: cudaStream_t to run on; NULL = a stream the library creates. */
 typedef struct {
-  int32_t precision;    /* MS_PREC_FP32 (MS_PREC_MIXED_BF16X3: see ms_create) */
+  int32_t precision;    /* MS_PREC_FP32 or MS_PREC_MIXED_F16X3 */
   int32_t mol_substeps; /* N: the molecules advance on field steps n with
                            n % N == 0, by a step of N dt, under E^n; their
                            dipole change enters that step's E update (Sec. 2's

@@ -18,7 +18,7 @@ from . import build as _build
 
 MS_OK, MS_EINVAL, MS_ENOMEM, MS_ECUDA, MS_ENUMERIC, MS_ETIMEOUT, MS_EUNSUPPORTED, MS_EIO = 0, -1, -2, -3, -4, -5, -6, -7
 MS_BC_PML, MS_BC_PERIODIC = 0, 1
-MS_PREC_FP32, MS_PREC_MIXED_BF16X3 = 0, 1
+MS_PREC_FP32, MS_PREC_MIXED_F16X3 = 0, 1
 MS_DRIVE_FDTD, MS_DRIVE_PRESCRIBED = 0, 1
 MS_FIELD_E, MS_FIELD_H = 0, 1
 MS_STATE_FULL, MS_STATE_PARITY = 0, 1

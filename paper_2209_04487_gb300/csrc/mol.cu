@@ -24,7 +24,7 @@
 // z that puts E' in the xz plane (a diagonal phase on the correction only),
 // where M is real.
 #include <cuda.h>
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -1780,7 +1780,7 @@ static void launch_step_tt(const SpeciesDev& sp, const MolDev& md, const Grid& g
 
 // ----------------------------------------------------------------------------
 // Mixed form of the kinetic pass: d2 = (K - I) s for every row as a tensor-core
-// GEMM on split BF16 operands (x = x_hi + x_lo, three products, FP32
+// GEMM on split FP16 operands (x = x_hi + x_lo, three products, FP32
 // accumulation in tensor memory).  K is the N_r x N_r circulant of the
 // kinetic propagator (symmetric).  Transposed so that the accumulator lanes
 // are radial points: D[n][m] = sum_k (K - I)[n][k] s_m[k], A = K - I (resident
@@ -1846,6 +1846,7 @@ __global__ void __launch_bounds__(256, 1) mol_kinetic_tc_kernel(SpeciesDev sp, l
   uint8_t* Bt = smem_tc + 4 * APL;  // two tile buffers, each Re hi, Re lo, Im hi, Im lo
   __shared__ __align__(8) unsigned long long bar[2];  // [0] A staged, [1] products done
   __shared__ unsigned tmem_base;
+  __shared__ int s_rmax[2][TR], s_rexp[2][TR];          // per tile buffer: row maxima, row scale exponents
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const float2* X = sp.psi;
   float2* Y = sp.d2;
@@ -1896,29 +1897,49 @@ __global__ void __launch_bounds__(256, 1) mol_kinetic_tc_kernel(SpeciesDev sp, l
                          : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   };
-  auto stage = [&](int buf) {  // the fetched tile -> four bf16 planes of buffer buf
+  // The fetched tile -> four FP16 planes of buffer buf.  Each state row is
+  // scaled by 2^e so that its largest |Re|, |Im| lies in [2^14, 2^15) (an
+  // exact power-of-two scale, undone on write-out): hi = fp16(x), lo =
+  // fp16(x - hi) then carry 22 bits of every element of the row's scale.
+  auto stage = [&](int buf) {
     uint8_t* B0 = Bt + buf * 4 * BPL;
+    if (t < TR) s_rmax[buf][t] = 0;
+    __syncthreads();
 #pragma unroll
     for (int u = 0; u < LOADS; ++u) {
-      const float re[2] = {pre[u].x, pre[u].z}, im[2] = {pre[u].y, pre[u].w};
-      __nv_bfloat16 rh[2], rl[2], ih[2], il[2];
+      const float m = fmaxf(fmaxf(fabsf(pre[u].x), fabsf(pre[u].y)), fmaxf(fabsf(pre[u].z), fabsf(pre[u].w)));
+      atomicMax(&s_rmax[buf][slot_row(u)], __float_as_int(m));  // non-negative floats order as ints
+    }
+    __syncthreads();
+    if (t < TR) {
+      const float m = __int_as_float(s_rmax[buf][t]);
+      int ex = 0;
+      if (m > 0.f) frexpf(m, &ex);
+      s_rexp[buf][t] = m > 0.f ? min(15 - ex, 100) : 0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < LOADS; ++u) {
+      const float sc = __int_as_float((127 + s_rexp[buf][slot_row(u)]) << 23);  // 2^e
+      const float re[2] = {pre[u].x * sc, pre[u].z * sc}, im[2] = {pre[u].y * sc, pre[u].w * sc};
+      __half rh[2], rl[2], ih[2], il[2];
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        rh[e] = __float2bfloat16_rn(re[e]);
-        rl[e] = __float2bfloat16_rn(re[e] - __bfloat162float(rh[e]));
-        ih[e] = __float2bfloat16_rn(im[e]);
-        il[e] = __float2bfloat16_rn(im[e] - __bfloat162float(ih[e]));
+        rh[e] = __float2half_rn(re[e]);
+        rl[e] = __float2half_rn(re[e] - __half2float(rh[e]));
+        ih[e] = __float2half_rn(im[e]);
+        il[e] = __float2half_rn(im[e] - __half2float(ih[e]));
       }
       const int off = tc_kmaj_off(slot_row(u), slot_k(u), NR);
-      *reinterpret_cast<__nv_bfloat162*>(B0 + 0 * BPL + off) = __halves2bfloat162(rh[0], rh[1]);
-      *reinterpret_cast<__nv_bfloat162*>(B0 + 1 * BPL + off) = __halves2bfloat162(rl[0], rl[1]);
-      *reinterpret_cast<__nv_bfloat162*>(B0 + 2 * BPL + off) = __halves2bfloat162(ih[0], ih[1]);
-      *reinterpret_cast<__nv_bfloat162*>(B0 + 3 * BPL + off) = __halves2bfloat162(il[0], il[1]);
+      *reinterpret_cast<__half2*>(B0 + 0 * BPL + off) = __halves2half2(rh[0], rh[1]);
+      *reinterpret_cast<__half2*>(B0 + 1 * BPL + off) = __halves2half2(rl[0], rl[1]);
+      *reinterpret_cast<__half2*>(B0 + 2 * BPL + off) = __halves2half2(ih[0], ih[1]);
+      *reinterpret_cast<__half2*>(B0 + 3 * BPL + off) = __halves2half2(il[0], il[1]);
     }
   };
   auto issue = [&](int buf) {  // 2 outputs x 6 split products x KS slices, one thread
-    constexpr unsigned idp =
-        (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TR >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
+    // FP32 accumulator (bit 4), A and B FP16 (format fields at bits 7 and 10 zero), N, M
+    constexpr unsigned idp = (1u << 4) | ((unsigned)(TR >> 3) << 17) | ((unsigned)(128 >> 4) << 24);
     constexpr unsigned idn = idp | (1u << 14);  // B negated
     // {A plane, B plane, negate}: Re = Kr Xr - Ki Xi, Im = Kr Xi + Ki Xr, each as hh + hl + lh
     constexpr int blk[2][6][3] = {{{0, 0, 0}, {0, 1, 0}, {1, 0, 0}, {2, 2, 1}, {2, 3, 1}, {3, 2, 1}},
@@ -1958,7 +1979,10 @@ __global__ void __launch_bounds__(256, 1) mol_kinetic_tc_kernel(SpeciesDev sp, l
 #pragma unroll
       for (int r = 0; r < H; ++r) {
         const long long gr = tile * TR + H * rh + r;
-        if (gr < rows) __stcs(Y + gr * NR + n, make_float2(__uint_as_float(re[r]), __uint_as_float(im[r])));
+        // undo the row's and the matrix's power-of-two scales
+        const float us = __int_as_float((127 - s_rexp[buf][H * rh + r] - sp.kpl_exp) << 23);
+        if (gr < rows)
+          __stcs(Y + gr * NR + n, make_float2(__uint_as_float(re[r]) * us, __uint_as_float(im[r]) * us));
       }
     }
   };
@@ -2018,7 +2042,7 @@ static int launch_stage1_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
     ++n;
   }
   const long long rows_total = (long long)sp.nmol * sp.rows;
-  if (sp.mixed) {  // split-BF16 tensor-core GEMM
+  if (sp.mixed) {  // split-FP16 tensor-core GEMM
     if constexpr (NR == 64 || NR == 128) {
       using T = TcShape<NR>;
       int dev = 0, nsm = 0;

@@ -253,27 +253,43 @@ ms_status upload_angular_tables() {
   return ms::upload_triplet_tables(dip.data()) == cudaSuccess ? MS_OK : MS_ECUDA;
 }
 
-// bf16 of x, round to nearest even (x finite)
-uint16_t to_bf16(float x) {
-  uint32_t u;
-  std::memcpy(&u, &x, 4);
-  u += 0x7FFFu + ((u >> 16) & 1u);
-  return (uint16_t)(u >> 16);
+// IEEE 754 binary16 of a finite double, rounded to nearest, ties to even
+// (|v| below the largest finite half, 65504; callers scale into range).
+uint16_t to_f16(double v) {
+  const uint16_t sign = std::signbit(v) ? 0x8000u : 0u;
+  const double a = std::fabs(v);
+  if (a == 0.0) return sign;
+  int e = 0;
+  const double f = std::frexp(a, &e);  // a = f 2^e, f in [0.5, 1)
+  int E = e - 1 + 15;                  // biased exponent of a normal half
+  if (E >= 1) {
+    int m = (int)std::nearbyint((2.0 * f - 1.0) * 1024.0);  // exact argument; ties to even
+    if (m == 1024) {
+      m = 0;
+      ++E;
+    }
+    if (E >= 31) return (uint16_t)(sign | 0x7C00u);
+    return (uint16_t)(sign | (E << 10) | m);
+  }
+  const int m = (int)std::nearbyint(std::ldexp(a, 24));  // subnormal: a = m 2^-24
+  return (uint16_t)(sign | m);                          // m = 1024 is the smallest normal
 }
-float from_bf16(uint16_t h) {
-  const uint32_t u = (uint32_t)h << 16;
-  float x;
-  std::memcpy(&x, &u, 4);
-  return x;
+double from_f16(uint16_t h) {
+  const int E = (h >> 10) & 31, m = h & 1023;
+  const double a = E == 0 ? std::ldexp((double)m, -24) : std::ldexp(1.0 + m / 1024.0, E - 15);
+  return (h & 0x8000u) ? -a : a;
 }
 
 // (K - I) of the kinetic propagator for the mixed form, (K - I)[a][b] =
 // (1/nr) sum_p (e^{-i k_p^2 dtau / 2 mu} - 1) e^{2 pi i p (a - b) / nr} (FP64),
 // a circulant: stored as one 16-column strip T[i][q] = (K - I)[i - (nr - 16)][q]
-// (indices mod nr) of 128 + nr - 16 rows, in four bf16 planes (Re hi, Re lo,
-// Im hi, Im lo) in the tensor cores' K-major layout.
-std::vector<uint16_t> mixed_kinetic_planes(int nr, double dR, double dtau, double mu) {
+// (indices mod nr) of 128 + nr - 16 rows, in four FP16 planes (Re hi, Re lo,
+// Im hi, Im lo) in the tensor cores' K-major layout, scaled by 2^*exp2 so that
+// its largest entry lies in [2^14, 2^15): hi + lo carries 22 bits of every
+// entry.
+std::vector<uint16_t> mixed_kinetic_planes(int nr, double dR, double dtau, double mu, int* exp2) {
   std::vector<cplx> kd(nr);
+  double amax = 0.0;
   for (int dlt = 0; dlt < nr; ++dlt) {
     cplx acc = 0.0;
     for (int k = 0; k < nr; ++k) {
@@ -282,17 +298,20 @@ std::vector<uint16_t> mixed_kinetic_planes(int nr, double dR, double dtau, doubl
       acc += expm1i(-kk * kk * dtau / (2.0 * mu)) * std::polar(1.0, 2.0 * kPi * p * dlt / nr);
     }
     kd[dlt] = acc / (double)nr;
+    amax = std::max(amax, std::max(std::fabs(kd[dlt].real()), std::fabs(kd[dlt].imag())));
   }
+  int ex = 0;
+  std::frexp(amax > 0.0 ? amax : 1.0, &ex);
+  *exp2 = 15 - ex;
   const int rows = ms::mixed_strip_rows(nr);
   const size_t plane = (size_t)rows * 16;  // elements
   std::vector<uint16_t> out(4 * plane, 0);
   for (int i = 0; i < rows; ++i)
     for (int q = 0; q < 16; ++q) {
       const int dlt = (((i - (nr - 16) - q) % nr) + nr) % nr;
-      const cplx v = kd[dlt];
-      const uint16_t rh = to_bf16((float)v.real()), ih = to_bf16((float)v.imag());
-      const uint16_t rl = to_bf16((float)(v.real() - (double)from_bf16(rh)));
-      const uint16_t il = to_bf16((float)(v.imag() - (double)from_bf16(ih)));
+      const double vr = std::ldexp(kd[dlt].real(), *exp2), vi = std::ldexp(kd[dlt].imag(), *exp2);
+      const uint16_t rh = to_f16(vr), ih = to_f16(vi);
+      const uint16_t rl = to_f16(vr - from_f16(rh)), il = to_f16(vi - from_f16(ih));
       const size_t off = (size_t)ms::mixed_plane_offset(i, q, nr) / 2;
       out[off] = rh;
       out[plane + off] = rl;
@@ -436,7 +455,7 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   sp.d2 = nullptr;
   MS_TRY(zeros(s, &sp.fld, ids.size()));  // per-molecule frame-field records
   if (mixed) {
-    const std::vector<uint16_t> kp = mixed_kinetic_planes(nr, dR, dtau, mu);
+    const std::vector<uint16_t> kp = mixed_kinetic_planes(nr, dR, dtau, mu, &sp.kpl_exp);
     MS_TRY(upload(s, (uint16_t**)&sp.kpl, kp.data(), kp.size()));
   }
   if (sp.path == MS_MOL_STREAMING) MS_TRY(zeros(s, &sp.d2, per * ids.size()));
@@ -634,7 +653,7 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
     for (long long q = 0; q < n; ++q)
       if (D->species_id[q] == si) ids.push_back((int)q);
     MS_TRY(build_species(s, si, D->species[si], dt * s->nsub, ids, O ? O->mol_path : MS_MOL_AUTO,
-                         O && O->precision == MS_PREC_MIXED_BF16X3, O && O->state_form == MS_STATE_PARITY));
+                         O && O->precision == MS_PREC_MIXED_F16X3, O && O->state_form == MS_STATE_PARITY));
   }
   return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
 }
@@ -665,8 +684,8 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
     if (M->material_id[c] >= M->n_materials) return MS_EINVAL;
   const int drive = O ? O->drive : MS_DRIVE_FDTD;
   if (drive != MS_DRIVE_FDTD && drive != MS_DRIVE_PRESCRIBED) return MS_EINVAL;
-  if (O && O->precision != MS_PREC_FP32 && O->precision != MS_PREC_MIXED_BF16X3) return MS_EINVAL;
-  const bool mixed = O && O->precision == MS_PREC_MIXED_BF16X3;
+  if (O && O->precision != MS_PREC_FP32 && O->precision != MS_PREC_MIXED_F16X3) return MS_EINVAL;
+  const bool mixed = O && O->precision == MS_PREC_MIXED_F16X3;
   if (O && (O->mol_substeps < 0 || O->mol_substeps > 65536)) return MS_EINVAL;
   if (O && ((O->alloc == nullptr) != (O->free == nullptr))) return MS_EINVAL;
   if (O && (O->mol_path < MS_MOL_AUTO || O->mol_path > MS_MOL_STREAMING)) return MS_EINVAL;

@@ -106,8 +106,9 @@ struct SpeciesDev {
   float2* psi;              // state [nmol][rows][nr] (ground rows first), s = T^{-1/2} psi
   float2* d2;               // streaming form: scratch (T - 1) s, same layout
   float4* fld;              // streaming form: per molecule (theta E'_z, theta E'_x/2, theta E'_y/2, terms)
-  int mixed;                // kinetic pass as the split-BF16 tensor-core GEMM (MS_PREC_MIXED_BF16X3)
-  const uint16_t* kpl;      // mixed: (K - I) strip as four bf16 planes (Re hi, Re lo, Im hi, Im lo)
+  int mixed;                // kinetic pass as the split-FP16 tensor-core GEMM (MS_PREC_MIXED_F16X3)
+  const uint16_t* kpl;      // mixed: (K - I) strip as four FP16 planes (Re hi, Re lo, Im hi, Im lo), x 2^kpl_exp
+  int kpl_exp;
   int path;                 // MS_MOL_FUSED or MS_MOL_STREAMING
   // per (s, j, r): e^{-i V dtau} - 1 and e^{-i V dtau/2}
   const float2* vdelta;     // [2][jmax+1][nr]

@@ -176,12 +176,14 @@ def test_parity_reduced_coupled_matches_oracle(B):
     assert np.abs(mu - o.mu).max() < 1e-3 * np.abs(o.mu).max()
 
 
-# Mixed form (kinetic pass as a split-BF16 tensor-core GEMM): its stated
-# error.  bf16 hi + lo keeps ~17 bits of each operand, so the kinetic
-# correction carries a ~5e-6 relative error per step.  Over 300 steps of the
-# strong resonant drive, measured on GB300: populations 6e-6 absolute, P_e
-# and dipoles 6e-6 relative, norm bookkeeping 6e-6 (plain FP32: ~1e-7).  The
-# rounding is deterministic, so the bounds sit at 5x the measured errors.
+# Mixed form (kinetic pass as a split-FP16 tensor-core GEMM): its stated
+# error.  Each state row and the matrix are scaled by powers of two into
+# FP16's range and split as hi + lo, which keeps ~22 bits of each operand.
+# Over 300 steps of the strong resonant drive, measured on GB300:
+# populations 3.7e-7 to 6.1e-7 absolute, P_e 4.3e-7 to 6.6e-7 and dipoles
+# 4.0e-7 to 5.2e-7 relative, norm bookkeeping 3.9e-7 to 6.5e-7 (a split of
+# BF16 halves, ~16 bits, gave 6e-6).  The rounding is deterministic, so the
+# bounds sit at 5x the measured errors.
 @pytest.mark.parametrize("nr,jmax,nmol", [(128, 4, 19), (64, 1, 37), (128, 2, 7)])
 def test_mixed_kinetic_matches_oracle_at_stated_error(B, nr, jmax, nmol):
     sp = W.Species(nr=nr, jmax=jmax, A=0.05)
@@ -189,7 +191,7 @@ def test_mixed_kinetic_matches_oracle_at_stated_error(B, nr, jmax, nmol):
                   seed=nr + jmax, nsteps=300)
     amp, wave = W.prescribed_drive(nmol, 300, wl.dt, E0=3e10, carrier_ev=6.0, fwhm=0.5e-15,
                                    t0=0.5e-15)
-    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, precision=B.MS_PREC_MIXED_BF16X3,
+    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, precision=B.MS_PREC_MIXED_F16X3,
                        mol_path=B.MS_MOL_STREAMING)
     sim.set_prescribed(amp, wave)
     sim.step(300)
@@ -204,27 +206,29 @@ def test_mixed_kinetic_matches_oracle_at_stated_error(B, nr, jmax, nmol):
             "mu_rel": np.abs(mu - o.mu).max() / np.abs(o.mu).max(),
             "norm": np.abs(P.sum(axis=1) + absb.sum(axis=1) - 1).max()}
     print(f"mixed nr={nr} J={jmax}: " + ", ".join(f"{k} {v:.2e}" for k, v in errs.items()))
-    assert errs["P"] < 3e-5
-    assert errs["Pe_rel"] < 3e-5
-    assert errs["mu_rel"] < 3e-5
-    assert errs["norm"] < 3e-5
+    assert errs["P"] < 3e-6
+    assert errs["Pe_rel"] < 3.5e-6
+    assert errs["mu_rel"] < 3e-6
+    assert errs["norm"] < 3.5e-6
 
 
 def test_mixed_norm_drift_2000_steps(B):
-    """Norm drift of the mixed form under the benchmark's 1e9 V/m pulse,
-    beside the plain form's 1e-6 target (reported; bounded at 5x the measured)."""
+    """Norm drift of the mixed form under the benchmark's 1e9 V/m pulse, held
+    to the plain form's bounds (the 1e-6 target on the ensemble rms): measured
+    rms 7.5e-7, max 1.87e-6 over 64 molecules (plain FP32: 5.9e-7, 1.88e-6)."""
     sp = W.Species(nr=128, jmax=4)
     n = 64
     wl = W.custom("norm mixed", 8, 8, 48, n_per_sim=n, species=[sp], layer=(20, 24), seed=3, nsteps=2000)
     amp, wave = W.prescribed_drive(n, 2000, wl.dt, E0=1e9, t0=3e-15)
-    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, precision=B.MS_PREC_MIXED_BF16X3)
+    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, precision=B.MS_PREC_MIXED_F16X3)
     sim.set_prescribed(amp, wave)
     sim.step(2000)
     P = sim.populations()
     absb, _ = sim.dissociation()
     drift = np.abs(P.sum(axis=1) + absb.sum(axis=1) - 1.0)
     print(f"mixed norm drift: max {drift.max():.3e} rms {np.sqrt((drift ** 2).mean()):.3e}")
-    assert drift.max() < 1.5e-4   # measured 2.8e-5 (plain FP32: 1.9e-6)
+    assert np.sqrt((drift ** 2).mean()) < 1e-6
+    assert drift.max() < 2e-6
 
 
 @pytest.mark.parametrize("path", ["fused", "streaming"])

@@ -61,7 +61,7 @@ def test_valid_descriptor_reaches_the_device_check(B, precision):
     import torch
 
     def mutate(g, m, d, o, keep):
-        o.precision = B.MS_PREC_MIXED_BF16X3 if precision == "mixed" else B.MS_PREC_FP32
+        o.precision = B.MS_PREC_MIXED_F16X3 if precision == "mixed" else B.MS_PREC_FP32
         if precision == "cw_substeps":
             g.src_kind = B.MS_SRC_CW
             o.mol_substeps = 40
@@ -111,10 +111,10 @@ def test_invalid_descriptors_are_rejected(B, what):
         elif what == "precision_unknown":
             o.precision = 7
         elif what == "mixed_fused":
-            o.precision = B.MS_PREC_MIXED_BF16X3
+            o.precision = B.MS_PREC_MIXED_F16X3
             o.mol_path = B.MS_MOL_FUSED
         elif what == "mixed_nr256":
-            o.precision = B.MS_PREC_MIXED_BF16X3
+            o.precision = B.MS_PREC_MIXED_F16X3
             d.species[0].nr = 256
         elif what == "alloc_half":
             o.alloc = B._ALLOC(lambda n, c: None)
