@@ -190,6 +190,11 @@ class SpeciesEnsemble:
         self.Thalf = kinetic_propagator(sp, 0.5 * dtau)
         self.mask = mask(sp)
         self.taylor_tol = taylor_tol
+        # transition dipole at each radial point (e a0): the constant d, or an
+        # R-dependent d(R) given at the grid points
+        dR_tab = getattr(sp, "dipole_R", None)
+        self.d_r = (np.full(sp.nr, float(sp.dipole)) if dR_tab is None
+                    else np.asarray(dR_tab, np.float64).reshape(sp.nr))
         self.psi = np.zeros((self.n, 2, self.nrot, sp.nr), np.complex128)
         self.psi[:, 0, 0, :] = ground_state(sp)[None, :]
         self.absorbed = np.zeros((self.n, 2))
@@ -201,29 +206,31 @@ class SpeciesEnsemble:
         return psi @ Kp.T
 
     def coupling(self, psi, E_mol_au):
-        """exp(+i d dtau sigma_x (x) M) psi by its Taylor series, with
-        M = E'_x X + E'_y Y + E'_z Z per molecule (Eq. 4 coupling terms)."""
-        theta = self.sp.dipole * self.dtau
+        """exp(+i dtau d(R) sigma_x (x) M) psi by its Taylor series, with
+        M = E'_x X + E'_y Y + E'_z Z per molecule (Eq. 4 coupling terms) and
+        the transition dipole d(R) acting point-wise along R (constant d:
+        the paper's case)."""
         M = (E_mol_au[:, 0, None, None] * self.X + E_mol_au[:, 1, None, None] * self.Y
              + E_mol_au[:, 2, None, None] * self.Z)
         out = psi.copy()
         term = psi.copy()
         for n in range(1, 200):
-            # sigma_x (x) M: swap the surfaces, apply M along the channel index
-            sw = term[:, ::-1]
-            term = (1j * theta / n) * (M[:, None] @ sw)
+            # sigma_x (x) M (x) d(R): swap the surfaces, apply M along the
+            # channel index and d(R) along R
+            sw = term[:, ::-1] * self.d_r
+            term = (1j * self.dtau / n) * (M[:, None] @ sw)
             out += term
             if np.sqrt((np.abs(term) ** 2).sum()) < self.taylor_tol:
                 break
         return out
 
     def dipole_mol(self, psi):
-        """mu' = 2 d Re sum_R xi_g^dagger A xi_e dR for A = X, Y, Z (a.u.)."""
+        """mu' = 2 Re sum_R d(R) xi_g^dagger A xi_e dR for A = X, Y, Z (a.u.)."""
         g, e = psi[:, 0], psi[:, 1]
         out = np.empty((psi.shape[0], 3))
         for c, A in enumerate((self.X, self.Y, self.Z)):
             Ae = A @ e                                           # [k, a, r]
-            out[:, c] = 2.0 * self.sp.dipole * self.dR * (g.conj() * Ae).sum(axis=(1, 2)).real
+            out[:, c] = 2.0 * self.dR * (g.conj() * Ae * self.d_r).sum(axis=(1, 2)).real
         return out
 
     # -- one split-operator step ------------------------------------------------

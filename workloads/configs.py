@@ -37,7 +37,8 @@ class Species:
 
     Ground surface: Morse, De*(1-exp(-a(r-re)))^2 - De (Eq. 6 form).
     Excited surface: A + B*exp(-beta*(r-rc)) (Eq. 7 is A=0, B=2De_e).
-    The transition dipole is constant in R (the paper's choice).
+    The transition dipole is constant in R (the paper's choice) unless a
+    table d(R) at the grid points is given.
     The absorber is cos(pi/2*(r-ra)/(rmax-ra))**power for r > ra.
     """
     nr: int = 64
@@ -55,6 +56,9 @@ class Species:
     dipole: float = 1.0
     absorber_r: float = 8.5
     absorber_power: float = 0.125
+    # R-dependent transition dipole d(R) at the radial grid points (e a0), a
+    # tuple of nr values; None = the constant `dipole` (the paper's choice)
+    dipole_R: Optional[tuple] = None
     # "wavepacket" (the two-surface ro-vibrational model) or "bloch" (frozen
     # two-level emitter: transition energy w0_ev, dipole along the molecular
     # axis, optional relaxation times T1, T2 in s, 0 = none)
