@@ -145,6 +145,14 @@ typedef struct {
  * transition dipole d [e a0]; absorbing mask cos(pi/2 (r-ra)/(rmax-ra))^p
  * for r > ra (ra >= rmax disables it).
  *
+ * An R-dependent transition dipole (dipole_R) acts point-wise along R in the
+ * coupling, exp(i dtau d(R) sigma_x (x) E'.R^), and in the dipole,
+ * 2 Re sum_R d(R) chi_g^dagger R^ chi_e dR; the dipole is then read from
+ * psi = T^{1/2} s by one more kernel per molecular step.  It needs jmax <= 4,
+ * nr 64 or 128 and the full state (the point-resident kernels; the fused
+ * layout at nr 128 only), else MS_EUNSUPPORTED; non-finite values give
+ * MS_EINVAL.
+ *
  * MS_MODEL_BLOCH (the frozen molecules of the scaling-experiments section,
  * Fig. 5d): a two-level emitter with its ro-vibrational degrees of freedom
  * frozen, H = w0 |e><e| - d (n . E)(|g><e| + |e><g|), transition energy
@@ -168,6 +176,9 @@ typedef struct {
   int32_t model;              /* MS_MODEL_WAVEPACKET or MS_MODEL_BLOCH */
   double bloch_w0_eV;         /* MS_MODEL_BLOCH: transition energy */
   double bloch_T1_s, bloch_T2_s;  /* MS_MODEL_BLOCH: relaxation times, 0 = none */
+  const double* dipole_R;     /* MS_MODEL_WAVEPACKET: NULL for the constant dipole_ea0, or an
+                                 R-dependent transition dipole d(R) at the nr grid points
+                                 (e a0), copied; see below */
 } ms_species;
 
 /* Molecules: species_id, sim_id [n]; pos_m [n][3] absolute position in the

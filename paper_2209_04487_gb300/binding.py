@@ -50,7 +50,8 @@ class SpeciesDesc(C.Structure):
                 ("morse_re", C.c_double), ("exc_A", C.c_double), ("exc_B", C.c_double),
                 ("exc_beta", C.c_double), ("exc_rc", C.c_double), ("dipole_ea0", C.c_double),
                 ("absorber_r", C.c_double), ("absorber_power", C.c_double), ("model", C.c_int32),
-                ("bloch_w0_eV", C.c_double), ("bloch_T1_s", C.c_double), ("bloch_T2_s", C.c_double)]
+                ("bloch_w0_eV", C.c_double), ("bloch_T1_s", C.c_double), ("bloch_T2_s", C.c_double),
+                ("dipole_R", C.POINTER(C.c_double))]
 
 
 class MoleculesDesc(C.Structure):
@@ -159,9 +160,14 @@ class _TorchAllocator:
 
 def species_desc(sp) -> SpeciesDesc:
     bloch = getattr(sp, "model", "wavepacket") == "bloch"
-    return SpeciesDesc(sp.nr, sp.jmax, sp.rmin, sp.rmax, sp.mass, sp.De, sp.a, sp.re, sp.A, sp.B,
-                       sp.beta, sp.rc, sp.dipole, sp.absorber_r, sp.absorber_power,
-                       MS_MODEL_BLOCH if bloch else MS_MODEL_WAVEPACKET, sp.w0_ev, sp.T1, sp.T2)
+    d = SpeciesDesc(sp.nr, sp.jmax, sp.rmin, sp.rmax, sp.mass, sp.De, sp.a, sp.re, sp.A, sp.B,
+                    sp.beta, sp.rc, sp.dipole, sp.absorber_r, sp.absorber_power,
+                    MS_MODEL_BLOCH if bloch else MS_MODEL_WAVEPACKET, sp.w0_ev, sp.T1, sp.T2)
+    if getattr(sp, "dipole_R", None) is not None:
+        tab = np.ascontiguousarray(sp.dipole_R, np.float64)
+        d.dipole_R = tab.ctypes.data_as(C.POINTER(C.c_double))
+        d._keep_dipole_R = tab      # alive as long as the descriptor
+    return d
 
 
 def mixed_supported(wl) -> bool:
@@ -193,7 +199,9 @@ class Simulation:
                           _ptr(ga, C.c_double), _ptr(mid, C.c_uint8))
         nmol = wl.n_molecules if with_molecules else 0
         self.nmol = nmol
-        sp_arr = (SpeciesDesc * max(1, len(wl.species)))(*[species_desc(s) for s in wl.species])
+        descs = [species_desc(s) for s in wl.species]       # they keep any d(R) tables alive
+        self._keep += descs
+        sp_arr = (SpeciesDesc * max(1, len(wl.species)))(*descs)
         sid = np.ascontiguousarray(wl.species_id[:nmol], np.int32)
         simid = np.ascontiguousarray(wl.sim_id[:nmol], np.int32)
         pos = np.ascontiguousarray(wl.pos[:nmol], np.float64)

@@ -1254,7 +1254,7 @@ __device__ __forceinline__ void dipole_rows(const V& gv, const W& ev, float2& ac
 // scratch.  Every CTA barrier sits in code all threads run; the per-surface
 // work between them is compiled once per surface (row counts differ when
 // PAR).
-template <int J, int NR, bool FUSED, bool PAR>
+template <int J, int NR, bool FUSED, bool PAR, bool DIPR = false>
 __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 : 2) : 1))
     mol_rpoint_kernel(SpeciesDev sp, MolDev md, int* err) {
   using L = Rows<J, PAR>;
@@ -1309,7 +1309,15 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
   if (t >= 32 && t < 41) s_rot[t - 32] = md.rot[9 * (long long)m + (t - 32)];
   else if (t >= 64 && t < 67) s_mu[t - 64] = md.mu[3 * (long long)m + (t - 64)];
   else if (t >= 67 && t < 69) s_abs[t - 67] = md.absorbed[2 * (long long)m + (t - 67)];
-  const float4 f = __ldg(&sp.fld[lm]);
+  // theta E' of the molecule, times d(R) / max|d| at this thread's point
+  // (1 for a constant dipole)
+  float4 f = __ldg(&sp.fld[lm]);
+  if constexpr (DIPR) {
+    const float dw = __ldg(&sp.dipw[p]);
+    f.x *= dw;
+    f.y *= dw;
+    f.z *= dw;
+  }
   const int nterms = __float_as_int(f.w);
   const float mk = sp.maskw[p].x;
   float2 vh[J + 1], vd[J + 1];
@@ -1464,11 +1472,13 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
     }
     __syncthreads();
     if (t < 3) {  // lab dipole: mu = O mu', mu' = d dR (Re(S+ + S-), Im(S+ - S-), 2 Re Z)
-      const float sc = (float)sp.dipole * sp.dR;
-      const float lab = sc * (s_rot[3 * t] * s_fin[4] + s_rot[3 * t + 1] * s_fin[5] + s_rot[3 * t + 2] * s_fin[6]);
-      const double nl = (double)lab;
-      md.dmu[3 * (long long)m + t] = nl - s_mu[t];
-      md.mu[3 * (long long)m + t] = nl;
+      if constexpr (!DIPR) {  // with d(R) the dipole is read from T^{1/2} s' by mol_dipole_r_kernel
+        const float sc = (float)sp.dipole * sp.dR;
+        const float lab = sc * (s_rot[3 * t] * s_fin[4] + s_rot[3 * t + 1] * s_fin[5] + s_rot[3 * t + 2] * s_fin[6]);
+        const double nl = (double)lab;
+        md.dmu[3 * (long long)m + t] = nl - s_mu[t];
+        md.mu[3 * (long long)m + t] = nl;
+      }
     } else if (t < 5) {
       const double P = ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
       md.pop[2 * (long long)m + (t - 3)] = P;
@@ -1479,17 +1489,23 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
   }
 }
 
-template <int J, int NR, bool FUSED, bool PAR>
+template <int J, int NR, bool FUSED, bool PAR, bool DIPR = false>
 static void launch_rpoint_jnp(const SpeciesDev& sp, const MolDev& md, int* err, cudaStream_t s) {
   constexpr int ROWS = Rows<J, PAR>::ROWS;
   const size_t smem = (size_t)2 * ROWS * NR * sizeof(float2) + (FUSED ? 2 * NR * sizeof(float2) : 0);
-  auto k = mol_rpoint_kernel<J, NR, FUSED, PAR>;
+  auto k = mol_rpoint_kernel<J, NR, FUSED, PAR, DIPR>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   k<<<sp.nmol, 2 * NR, smem, s>>>(sp, md, err);
 }
 template <int J, int NR, bool FUSED>
 static void launch_rpoint_jn(const SpeciesDev& sp, const MolDev& md, int* err, cudaStream_t s) {
+  if constexpr (NR <= 128) {  // R-dependent dipole: full state, N_r 64 or 128
+    if (sp.dipw) {
+      launch_rpoint_jnp<J, NR, FUSED, false, true>(sp, md, err, s);
+      return;
+    }
+  }
   if (sp.par) launch_rpoint_jnp<J, NR, FUSED, true>(sp, md, err, s);
   else launch_rpoint_jnp<J, NR, FUSED, false>(sp, md, err, s);
 }
@@ -1502,6 +1518,104 @@ static void launch_rpoint_n(const SpeciesDev& sp, const MolDev& md, int* err, cu
     case 2: launch_rpoint_jn<2, NR, FUSED>(sp, md, err, s); break;
     case 3: launch_rpoint_jn<3, NR, FUSED>(sp, md, err, s); break;
     case 4: launch_rpoint_jn<4, NR, FUSED>(sp, md, err, s); break;
+  }
+}
+
+// Dipole of a species with an R-dependent transition dipole d(R).  The
+// stored state is s = T^{-1/2} psi; the populations are the same from s and
+// psi (T^{1/2} is unitary per channel), and so is the dipole while d is
+// constant (T commutes with d sigma_x (x) R^).  With d(R) it does not, so the
+// dipole is taken from psi' = T^{1/2} s' after the step: one CTA per
+// molecule stages s', turns it into psi' with the shared-memory FFT and sums
+// 2 Re sum_R d(R) g^dagger A e dR for A = S+, S-, Z (threads t < N_r: one
+// radial point each), then writes mu and the change over the step.
+template <int J, int NR, bool PAR>
+__global__ void __launch_bounds__(FFTShape<NR>::THREADS) mol_dipole_r_kernel(SpeciesDev sp, MolDev md, int* err) {
+  using L = Rows<J, PAR>;
+  constexpr int ROWS = L::ROWS, NG = L::NG, NE = L::NE, NT = FFTShape<NR>::THREADS, NW = NT / 32;
+  constexpr unsigned kStateBytes = (unsigned)ROWS * NR * sizeof(float2);
+  extern __shared__ __align__(16) float4 smem4[];
+  float2* X = reinterpret_cast<float2*>(smem4);  // [ROWS][NR]: s', then psi'
+  float2* s_tw = X + ROWS * NR;
+  float2* s_kh = s_tw + NR;
+  __shared__ __align__(8) unsigned long long s_bar[1];
+  __shared__ float s_red[NW][3];
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int lm = blockIdx.x;
+  const int m = sp.mol[lm];
+  if (t == 0) {
+    mbar_init(&s_bar[0], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&s_bar[0], kStateBytes);
+    bulk_g2s(X, sp.psi + (long long)lm * ROWS * NR, kStateBytes, &s_bar[0]);
+  }
+  for (int q = t; q < NR; q += NT) {
+    s_tw[q] = __ldg(&sp.twiddle[q]);
+    s_kh[q] = __ldg(&sp.khalf[q]);
+  }
+  __syncthreads();
+  const bool ok = mbar_wait_sleep(&s_bar[0], 0);
+  if (!__syncthreads_and(ok)) {
+    if (t == 0) atomicOr(err, kErrTimeout);
+    if (!ok) mbar_wait_sleep(&s_bar[0], 0);
+    return;
+  }
+  kinetic_pass<NR>(X, ROWS, s_kh, s_tw);  // psi' = T^{1/2} s'
+  float dP = 0.f, dQ = 0.f, dZ = 0.f;
+  if (t < NR) {
+    float2 gv[NG], ev[NE > 0 ? NE : 1];  // J = 0, parity-reduced: no excited row
+#pragma unroll
+    for (int r = 0; r < NG; ++r) gv[r] = X[r * NR + t];
+#pragma unroll
+    for (int r = 0; r < NE; ++r) ev[r] = X[(NG + r) * NR + t];
+    float2 accP = make_float2(0.f, 0.f), accM = accP, accZ = accP;
+    dipole_rows<J, PAR, 0, NG>(gv, ev, accP, accM, accZ);
+    const float d = (float)sp.dipole * __ldg(&sp.dipw[t]);
+    dP = d * (accP.x + accM.x);
+    dQ = d * (accP.y - accM.y);
+    dZ = d * 2.f * accZ.x;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dP += __shfl_xor_sync(0xffffffffu, dP, o);
+    dQ += __shfl_xor_sync(0xffffffffu, dQ, o);
+    dZ += __shfl_xor_sync(0xffffffffu, dZ, o);
+  }
+  if (lane == 0) {
+    s_red[w][0] = dP;
+    s_red[w][1] = dQ;
+    s_red[w][2] = dZ;
+  }
+  __syncthreads();
+  if (t < 3) {
+    float v[3] = {0.f, 0.f, 0.f};
+    for (int ww = 0; ww < NW; ++ww)
+      for (int k = 0; k < 3; ++k) v[k] += s_red[ww][k];
+    const float* O = md.rot + 9 * (long long)m;  // molecule -> lab, row-major
+    const double lab = (double)(sp.dR * (O[3 * t] * v[0] + O[3 * t + 1] * v[1] + O[3 * t + 2] * v[2]));
+    md.dmu[3 * (long long)m + t] = lab - md.mu[3 * (long long)m + t];
+    md.mu[3 * (long long)m + t] = lab;
+  }
+}
+
+template <int J, int NR>
+static void launch_dipole_r_jn(const SpeciesDev& sp, const MolDev& md, int* err, cudaStream_t s) {
+  auto run = [&](auto k, int rows) {
+    const size_t smem = ((size_t)rows * NR + 2 * NR) * sizeof(float2);
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k<<<sp.nmol, FFTShape<NR>::THREADS, smem, s>>>(sp, md, err);
+  };
+  run(mol_dipole_r_kernel<J, NR, false>, Rows<J, false>::ROWS);  // d(R): full state only
+}
+
+template <int NR>
+static void launch_dipole_r(const SpeciesDev& sp, const MolDev& md, int* err, cudaStream_t s) {
+  switch (sp.jmax) {
+    case 0: launch_dipole_r_jn<0, NR>(sp, md, err, s); break;
+    case 1: launch_dipole_r_jn<1, NR>(sp, md, err, s); break;
+    case 2: launch_dipole_r_jn<2, NR>(sp, md, err, s); break;
+    case 3: launch_dipole_r_jn<3, NR>(sp, md, err, s); break;
+    case 4: launch_dipole_r_jn<4, NR>(sp, md, err, s); break;
   }
 }
 
@@ -2072,7 +2186,8 @@ static int launch_stage2_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
     if constexpr (NR == 128) {
       if (fused_point(sp)) {
         launch_rpoint_n<NR, true>(sp, md, err, s);
-        return 1;
+        if (sp.dipw) launch_dipole_r<NR>(sp, md, err, s);
+        return sp.dipw ? 2 : 1;
       }
     }
     launch_step_tt<NR, true, 12>(sp, md, g, prescribed, err, sh, s);
@@ -2080,6 +2195,12 @@ static int launch_stage2_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
   }
   if (sp.jmax <= 4) {  // point-resident R-space pass
     launch_rpoint_n<NR>(sp, md, err, s);
+    if constexpr (NR <= 128) {
+      if (sp.dipw) {
+        launch_dipole_r<NR>(sp, md, err, s);
+        return 2;
+      }
+    }
     return 1;
   }
   RspaceMaps maps;

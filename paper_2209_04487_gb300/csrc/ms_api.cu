@@ -388,6 +388,16 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   sp.dR = (float)dR;
   sp.theta = d.dipole_ea0 * dtau;
   sp.dipole = d.dipole_ea0;
+  sp.dipw = nullptr;
+  if (d.dipole_R) {  // d(R) = dipole * dipw[i]: the coupling's term count follows max |d|
+    double dmax = 0.0;
+    for (int i = 0; i < nr; ++i) dmax = std::max(dmax, std::fabs(d.dipole_R[i]));
+    std::vector<float> w(nr);
+    for (int i = 0; i < nr; ++i) w[i] = dmax > 0.0 ? (float)(d.dipole_R[i] / dmax) : 0.f;
+    sp.dipole = dmax;
+    sp.theta = dmax * dtau;
+    MS_TRY(upload(s, (float**)&sp.dipw, w.data(), w.size()));
+  }
   std::vector<double> r(nr), Ug(nr), Ue(nr);
   for (int i = 0; i < nr; ++i) {
     r[i] = d.rmin + i * dR;
@@ -708,6 +718,12 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
       }
       if (sp.model != MS_MODEL_WAVEPACKET) return MS_EINVAL;
       if (sp.nr != 64 && sp.nr != 128 && sp.nr != 256) return MS_EUNSUPPORTED;
+      if (sp.dipole_R) {  // R-dependent dipole: the point-resident kernels only
+        for (int i = 0; i < sp.nr; ++i)
+          if (!std::isfinite(sp.dipole_R[i])) return MS_EINVAL;
+        const int path = O ? O->mol_path : MS_MOL_AUTO;
+        if (sp.jmax > 4 || sp.nr == 256 || par || (path == MS_MOL_FUSED && sp.nr != 128)) return MS_EUNSUPPORTED;
+      }
       if (sp.jmax < 0 || sp.jmax > ms::kMaxJ) return MS_EUNSUPPORTED;
       if (!(sp.rmax > sp.rmin) || !(sp.rmin > 0) || !(sp.mass_me > 0) || sp.absorber_power < 0)
         return MS_EINVAL;

@@ -118,8 +118,9 @@ struct SpeciesDev {
   const float2* twiddle;    // [n2][n1]: exp(-2 pi i n1 k2 / nr)
   const float2* maskw;      // [nr]: (m, 1 - m^2)
   const float* r;           // [nr]
-  double theta;             // d * dtau
-  double dipole;            // d (e a0)
+  double theta;             // d * dtau (d(R): its largest |d| times dtau)
+  double dipole;            // d (e a0) (d(R): its largest |d|)
+  const float* dipw;        // d(R) / max|d| at the grid points [nr], null for a constant dipole
   float dR;
   // frozen two-level molecules (MS_MODEL_BLOCH): Bloch vector per molecule
   int bloch;

@@ -549,3 +549,58 @@ def test_cw_frequency_sweep_matches_oracle(B):
     # the sims differ: each carrier drives its own molecules
     pe = [Po[wl.sim_id == s, 1].mean() for s in range(3)]
     assert len(set(np.round(pe, 12))) == 3
+
+
+# R-dependent transition dipole d(R) (the parity-reduced state's NEXT-row
+# companion): the coupling takes d(R) point by point and the dipole is read
+# from psi = T^{1/2} s by its own kernel.  Against the oracle at the plain
+# tolerances, both layouts, and the mixed kinetic pass.
+def _dR_species(nr, jmax):
+    from oracle.molecule import radial_grid
+    sp = W.Species(nr=nr, jmax=jmax, A=0.05)
+    r, _ = radial_grid(sp)
+    tab = 0.6 + 0.5 * np.tanh(r - 3.0) + 0.4 * np.exp(-(r - 2.2) ** 2)
+    import dataclasses
+    return dataclasses.replace(sp, dipole_R=tuple(tab))
+
+
+@pytest.mark.parametrize("nr,jmax,nmol,path,precision", [
+    (128, 4, 19, "fused", "fp32"), (128, 4, 19, "streaming", "fp32"), (64, 1, 37, "streaming", "fp32"),
+    (128, 2, 7, "streaming", "mixed"),
+])
+def test_dipole_R_prescribed_matches_oracle(B, nr, jmax, nmol, path, precision):
+    sp = _dR_species(nr, jmax)
+    wl = W.custom("dipole R", 8, 8, 48, n_per_sim=nmol, species=[sp], layer=(20, 24), seed=nr + 3 * jmax,
+                  nsteps=300)
+    amp, wave = W.prescribed_drive(nmol, 300, wl.dt, E0=3e10, carrier_ev=6.0, fwhm=0.5e-15, t0=0.5e-15)
+    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED,
+                       mol_path=B.MS_MOL_FUSED if path == "fused" else B.MS_MOL_STREAMING,
+                       precision=B.MS_PREC_MIXED_F16X3 if precision == "mixed" else B.MS_PREC_FP32)
+    sim.set_prescribed(amp, wave)
+    sim.step(300)
+    P, mu = sim.populations(), sim.dipoles()
+    o = PrescribedOracle(wl, amp, wave).run(300)
+    Po = o.populations()
+    assert Po[:, 1].max() > 1e-6
+    assert np.abs(P - Po).max() < 1e-5
+    sel = Po[:, 1] > 1e-10
+    assert np.max(np.abs(P[sel, 1] - Po[sel, 1]) / Po[sel, 1]) < 1e-3
+    assert np.abs(mu - o.mu).max() < 1e-4 * np.abs(o.mu).max()
+    # d(R) matters: the constant-dipole oracle differs
+    import dataclasses
+    wl0 = dataclasses.replace(wl, species=[dataclasses.replace(sp, dipole_R=None)])
+    o0 = PrescribedOracle(wl0, amp, wave).run(300)
+    assert np.abs(o0.mu - o.mu).max() > 1e-2 * np.abs(o.mu).max()
+
+
+def test_dipole_R_coupled_matches_oracle(B):
+    sp = _dR_species(128, 1)
+    wl = W.custom("coupled dipole R", 16, 16, 48, src_k=14, pulses=[[2e10, 1.5498, 2e-15, 2e-15]],
+                  layer=(22, 26), n_per_sim=150, species=[sp], seed=5, nsteps=400)
+    sim = B.Simulation(wl)
+    sim.step(wl.nsteps)
+    o = CoupledOracle(wl).run(wl.nsteps)
+    Eo, _ = _fields_oracle(o)
+    assert _rel(sim.fields(B.MS_FIELD_E), Eo) < 1e-4
+    assert np.abs(sim.populations() - o.populations()).max() < 1e-5
+    assert np.abs(sim.dipoles() - o.mu).max() < 1e-3 * np.abs(o.mu).max()

@@ -80,7 +80,8 @@ def test_valid_descriptor_reaches_the_device_check(B, precision):
 @pytest.mark.parametrize("what", ["courant", "nx", "pml", "src_in_pml", "material_id", "species_nr",
                                   "jmax", "position", "quaternion", "precision_unknown", "mixed_fused",
                                   "mixed_nr256", "alloc_half", "src_kind", "cw_turn_on", "substeps_negative",
-                                  "substeps_huge", "model_unknown", "bloch_w0", "bloch_T1"])
+                                  "substeps_huge", "model_unknown", "bloch_w0", "bloch_T1", "dipole_R_nan",
+                                  "dipole_R_jmax", "dipole_R_parity"])
 def test_invalid_descriptors_are_rejected(B, what):
     def mutate(g, m, d, o, keep):
         if what == "courant":
@@ -129,6 +130,16 @@ def test_invalid_descriptors_are_rejected(B, what):
             o.mol_substeps = -1
         elif what == "substeps_huge":
             o.mol_substeps = 1 << 20
+        elif what in ("dipole_R_nan", "dipole_R_jmax", "dipole_R_parity"):
+            tab = np.full(d.species[0].nr, 1.0)
+            if what == "dipole_R_nan":
+                tab[3] = np.nan
+            elif what == "dipole_R_jmax":
+                d.species[0].jmax = 5
+            else:
+                o.state_form = B.MS_STATE_PARITY
+            keep.append(tab)
+            d.species[0].dipole_R = tab.ctypes.data_as(C.POINTER(C.c_double))
         elif what == "model_unknown":
             d.species[0].model = 5
         elif what == "bloch_w0":
@@ -140,7 +151,8 @@ def test_invalid_descriptors_are_rejected(B, what):
             d.species[0].bloch_T1_s = float("nan")
     rc = _create(B, _wl(), mutate)
     expect = {"species_nr": B.MS_EUNSUPPORTED, "jmax": B.MS_EUNSUPPORTED,
-              "mixed_fused": B.MS_EUNSUPPORTED, "mixed_nr256": B.MS_EUNSUPPORTED}.get(what, B.MS_EINVAL)
+              "mixed_fused": B.MS_EUNSUPPORTED, "mixed_nr256": B.MS_EUNSUPPORTED,
+              "dipole_R_jmax": B.MS_EUNSUPPORTED, "dipole_R_parity": B.MS_EUNSUPPORTED}.get(what, B.MS_EINVAL)
     assert rc == expect, (what, rc)
 
 
