@@ -272,10 +272,13 @@ def main():
     preroll = peak_preroll(wl, a.warmup, a.steps) if a.preroll is None else a.preroll
     ck_path = None   # the main form's state at the start of its timed window (for e2e)
 
-    def time_form(mol_path, precision, clocks=False, state_form=0, detectors=None, w=None, save_to=None):
+    def time_form(mol_path, precision, clocks=False, state_form=0, detectors=None, w=None, save_to=None,
+                  tune=False):
         """Preroll, warm-up, then a.steps timed steps of one form (CUDA events on
         the library's stream, max over ranks) and its phase timings."""
-        sim = B.Simulation(w or wl, mol_path=mol_path, precision=precision, state_form=state_form)
+        sim = B.Simulation(w or wl, mol_path=mol_path, precision=precision, state_form=state_form,
+                           autotune=B.MS_TUNE_MEASURE if tune else B.MS_TUNE_OFF)
+        plan = sim.plan(0)
         if detectors is not None:
             sim.set_detectors(*detectors)
         form_path = sim.species_path(0)
@@ -309,7 +312,7 @@ def main():
         del sim
         torch.cuda.empty_cache()
         return {"ms": ms_, "phases": ph, "nsteps": nst, "launches": nlaunch, "clocks": cl, "P": Pf,
-                "norm_err": nerr, "path": form_path}
+                "norm_err": nerr, "path": form_path, "plan": plan}
 
     # the e2e leg resumes from this state: in memory-backed storage when it fits
     import shutil
@@ -390,6 +393,13 @@ def main():
         bl["note"] = ("frozen two-level molecules (Bloch equations, one RK4 step per field step, FP64 state); "
                       "the step is field-bound")
         other["bloch_frozen"] = bl
+        # the same workload with the species' plan picked by the create-time autotuner
+        ft = time_form(B.MS_MOL_AUTO, B.MS_PREC_FP32, tune=True)
+        tuned = form_entry(ft)
+        tuned["plan"] = {"layout": ft["plan"][0], "kernel": ft["plan"][1], "chunk": ft["plan"][2]}
+        tuned["note"] = ("ms_options.autotune: every plan the species can run timed on a sandbox of 2,048 "
+                         "molecules at create (kernel 1 point-resident, 2 tiled, 3 chunked)")
+        other["plain_fp32_autotuned"] = tuned
         # the small workload (32x32x64, 1,000 molecules): launch-bound, so the
         # captured-graph replay of ms_step matters; timed with host wall clock
         # around ms_step(a.steps) and a synchronize, graphs on and off

@@ -98,6 +98,23 @@ enum { MS_STATE_FULL = 0, MS_STATE_PARITY = 1 };
  * being captured by the caller.  MS_GRAPHS_OFF: always eager.  Both give the
  * same results bit for bit. */
 enum { MS_GRAPHS_AUTO = 0, MS_GRAPHS_OFF = 1 };
+/* A species' plan: its layout (MS_MOL_FUSED or MS_MOL_STREAMING) and the
+ * kernel of its R-space pass.  MS_KERN_POINT: one CTA of 2 N_r threads per
+ * molecule, thread = (radial point, surface) (J <= 4; fused at N_r 128).
+ * MS_KERN_TILE: one CTA per molecule over 32-point tiles of all rows, staged
+ * by tensor copies (J <= 7, streaming).  MS_KERN_CHUNK: one CTA per molecule
+ * over chunks of `chunk` radial points (4, 8, 16 or 32) of all rows (any J).
+ * MS_KERN_DEFAULT: the static rule (the first that applies of point, tile,
+ * chunk at the widest fitting chunk).  Parity-reduced and d(R) species run
+ * the point-resident kernel only.  Every plan computes the same step; their
+ * results differ by FP32 rounding.
+ * Autotuning (ms_options.autotune = MS_TUNE_MEASURE): ms_create times every
+ * plan a species can run on a sandbox copy of up to 2,048 of its molecules
+ * under a strong prescribed field (three coupling-series terms, as at a
+ * pulse peak) and keeps the fastest; ms_species_plan reports the choice and
+ * ms_set_species_plan pins one, so a tuned choice can be replayed. */
+enum { MS_KERN_DEFAULT = 0, MS_KERN_POINT = 1, MS_KERN_TILE = 2, MS_KERN_CHUNK = 3 };
+enum { MS_TUNE_OFF = 0, MS_TUNE_MEASURE = 1 };
 
 /* Grid and source.  dt must satisfy dt <= dx/(sqrt(3) c) (checked).
  * src_plane_z: absolute z index of the TF/SF plane (total field for
@@ -214,6 +231,7 @@ typedef struct {
   int32_t mol_path;     /* MS_MOL_AUTO, MS_MOL_FUSED or MS_MOL_STREAMING */
   int32_t state_form;   /* MS_STATE_FULL or MS_STATE_PARITY */
   int32_t step_graphs;  /* MS_GRAPHS_AUTO or MS_GRAPHS_OFF (see ms_step) */
+  int32_t autotune;     /* MS_TUNE_OFF or MS_TUNE_MEASURE (see MS_KERN_*) */
 } ms_options;
 
 /* Create a simulation: validates the descriptors, builds the species
@@ -390,6 +408,17 @@ ms_status ms_check_bounded_wait(int32_t tries);
  * reports MS_MOL_FUSED: one kernel reads and writes its state once per step);
  * MS_EINVAL for a NULL handle or a species index out of range. */
 int32_t ms_species_path(const ms_sim* sim, int32_t species);
+
+/* The plan of a species (see MS_KERN_*): layout, kernel and chunk width (0
+ * where the kernel has none or follows its rule).  MS_EINVAL for a NULL
+ * handle or pointer or a species index out of range. */
+ms_status ms_species_plan(const ms_sim* sim, int32_t species, int32_t* path, int32_t* kernel, int32_t* chunk);
+
+/* Pin a species' plan: one of the plans it can run (MS_EINVAL otherwise,
+ * nothing changed); kernel MS_KERN_DEFAULT restores the static rule for the
+ * given layout.  A switch to the streaming layout allocates its (T - 1)s
+ * scratch (MS_ENOMEM if that fails).  Takes effect from the next step. */
+ms_status ms_set_species_plan(ms_sim* sim, int32_t species, int32_t path, int32_t kernel, int32_t chunk);
 
 /* Device memory held by the simulation, in bytes. */
 size_t ms_device_bytes(const ms_sim* sim);

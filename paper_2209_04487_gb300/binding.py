@@ -25,6 +25,8 @@ MS_STATE_FULL, MS_STATE_PARITY = 0, 1
 MS_SRC_PULSE, MS_SRC_CW = 0, 1
 MS_MODEL_WAVEPACKET, MS_MODEL_BLOCH = 0, 1
 MS_GRAPHS_AUTO, MS_GRAPHS_OFF = 0, 1
+MS_KERN_DEFAULT, MS_KERN_POINT, MS_KERN_TILE, MS_KERN_CHUNK = 0, 1, 2, 3
+MS_TUNE_OFF, MS_TUNE_MEASURE = 0, 1
 MS_MOL_AUTO, MS_MOL_FUSED, MS_MOL_STREAMING = 0, 1, 2
 
 _ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
@@ -64,7 +66,8 @@ class MoleculesDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("mol_substeps", C.c_int32), ("drive", C.c_int32),
                 ("alloc", _ALLOC), ("free", _FREE), ("alloc_ctx", C.c_void_p), ("stream", C.c_void_p),
-                ("mol_path", C.c_int32), ("state_form", C.c_int32), ("step_graphs", C.c_int32)]
+                ("mol_path", C.c_int32), ("state_form", C.c_int32), ("step_graphs", C.c_int32),
+                ("autotune", C.c_int32)]
 
 
 def _load() -> C.CDLL:
@@ -91,6 +94,8 @@ def _load() -> C.CDLL:
         "ms_save": (C.c_int, [C.c_void_p, C.c_char_p]),
         "ms_check_bounded_wait": (C.c_int, [C.c_int32]),
         "ms_species_path": (C.c_int32, [C.c_void_p, C.c_int32]),
+        "ms_species_plan": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_int32), P(C.c_int32), P(C.c_int32)]),
+        "ms_set_species_plan": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
         "ms_set_detectors": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(C.c_double), C.c_int32]),
         "ms_read_flux": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_double)]),
         "ms_read_dft": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P(C.c_double)]),
@@ -114,7 +119,7 @@ LIB = _load()
 EXPORTED = ("ms_create", "ms_step", "ms_step_noalloc", "ms_step_count", "ms_read_fields", "ms_write_fields",
             "ms_read_populations", "ms_read_dissociation", "ms_read_dipoles",
             "ms_set_prescribed_field", "ms_set_replay_field", "ms_record_local_fields", "ms_save", "ms_load",
-            "ms_check_bounded_wait", "ms_species_path", "ms_set_detectors", "ms_read_flux", "ms_read_dft", "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
+            "ms_check_bounded_wait", "ms_species_path", "ms_species_plan", "ms_set_species_plan", "ms_set_detectors", "ms_read_flux", "ms_read_dft", "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
             "ms_destroy", "ms_status_string")
 
 
@@ -182,7 +187,7 @@ class Simulation:
     def __init__(self, wl, *, drive: int = MS_DRIVE_FDTD, precision: int = MS_PREC_FP32,
                  with_molecules: bool = True, use_torch: bool = True, stream=None,
                  mol_path: int = MS_MOL_AUTO, allocator=None, state_form: int = 0,
-                 step_graphs: int = 0):
+                 step_graphs: int = 0, autotune: int = 0):
         self.wl = wl
         self._keep = []
         src = np.ascontiguousarray(wl.src, np.float64) if wl.src_k >= 0 else None
@@ -216,6 +221,7 @@ class Simulation:
         opts.mol_path = mol_path
         opts.state_form = state_form
         opts.step_graphs = step_graphs
+        opts.autotune = autotune
         self.stream = None
         if use_torch:
             import torch
@@ -342,6 +348,15 @@ class Simulation:
     def species_path(self, species: int = 0) -> int:
         """MS_MOL_FUSED or MS_MOL_STREAMING: the layout the species runs in."""
         return int(LIB.ms_species_path(self.h, species))
+
+    def plan(self, species: int = 0):
+        """(layout, MS_KERN_* kernel, chunk width) of a species' molecular step."""
+        p, k, c = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(LIB.ms_species_plan(self.h, species, C.byref(p), C.byref(k), C.byref(c)), "ms_species_plan")
+        return p.value, k.value, c.value
+
+    def set_plan(self, species: int, path: int, kernel: int, chunk: int = 0):
+        _check(LIB.ms_set_species_plan(self.h, species, path, kernel, chunk), "ms_set_species_plan")
 
     @property
     def device_bytes(self) -> int:

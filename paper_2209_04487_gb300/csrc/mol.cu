@@ -1619,8 +1619,13 @@ static void launch_dipole_r(const SpeciesDev& sp, const MolDev& md, int* err, cu
   }
 }
 
-// The fused form of a species runs the point-resident kernel when it applies
-static bool fused_point(const SpeciesDev& sp) { return sp.path == MS_MOL_FUSED && sp.jmax <= 4 && sp.nr == 128; }
+// The point-resident kernel runs a species' R-space pass (and, fused, its
+// kinetic pass) where it applies (J <= 4; fused only at N_r = 128) unless the
+// species' plan names another kernel.
+static bool use_point(const SpeciesDev& sp) {
+  if (sp.jmax > 4 || (sp.path == MS_MOL_FUSED && sp.nr != 128)) return false;
+  return sp.kern == MS_KERN_DEFAULT || sp.kern == MS_KERN_POINT;
+}
 }  // namespace ms
 
 // ----------------------------------------------------------------------------
@@ -1791,9 +1796,50 @@ bool mol_step_supported(int nr, int nrot, int path) {
   return step_shape(nr, nrot, path == MS_MOL_FUSED).ok;
 }
 
+// The chunked kernel's launch shape at a given chunk width (the plan a tuner
+// picked), or ok = false where that width does not fit.
+static StepShape step_shape_ch(int nr, int nrot, bool fused, int ch) {
+  auto cap = [](int k) { return (size_t)(228 * 1024 / k - 1024 - 800); };
+  if (ch != 4 && ch != 8 && ch != 16 && ch != 32) return {ch, 12, 0, false};
+  if (fused) {
+    const size_t sm = step_smem(nr, nrot, ch, true);
+    return {ch, 12, sm, ch >= 8 && rows_per_thread(nrot, ch) <= 12 && sm <= cap(1)};
+  }
+  for (int maxr : {4, 12, 24})
+    if (rows_per_thread(nrot, ch) <= maxr && step_smem(nr, nrot, ch, false) <= cap(maxr == 4 ? 4 : (maxr == 12 ? 2 : 1)))
+      return {ch, maxr, step_smem(nr, nrot, ch, false), true};
+  return {ch, 24, 0, false};
+}
+
 // The streaming R-space kernel covers J <= 7 (rows <= 128) on radial grids of
 // whole 32-point chunks.
 static bool rspace_ok(int nr, int jmax) { return nr % kTile == 0 && (nr / kTile) % 2 == 0 && jmax <= 7; }
+
+// The plans a species can run: (layout, kernel, chunk width).  Parity-reduced
+// and d(R) species have one (the point-resident kernel); the mixed kinetic
+// pass needs the streaming layout.
+int mol_plan_candidates(const SpeciesDev& sp, int (*out)[3], int max) {
+  int n = 0;
+  auto add = [&](int path, int kern, int ch) {
+    if (n < max) {
+      out[n][0] = path;
+      out[n][1] = kern;
+      out[n][2] = ch;
+    }
+    ++n;
+  };
+  if (sp.bloch || sp.par || sp.dipw) return 0;
+  if (!sp.mixed) {
+    if (sp.nr == 128 && sp.jmax <= 4) add(MS_MOL_FUSED, MS_KERN_POINT, 0);
+    for (int ch : {32, 16, 8})
+      if (step_shape_ch(sp.nr, sp.nrot, true, ch).ok) add(MS_MOL_FUSED, MS_KERN_CHUNK, ch);
+  }
+  if (sp.jmax <= 4) add(MS_MOL_STREAMING, MS_KERN_POINT, 0);
+  if (rspace_ok(sp.nr, sp.jmax)) add(MS_MOL_STREAMING, MS_KERN_TILE, 0);
+  for (int ch : {32, 16, 8, 4})
+    if (step_shape_ch(sp.nr, sp.nrot, false, ch).ok) add(MS_MOL_STREAMING, MS_KERN_CHUNK, ch);
+  return n < max ? n : max;
+}
 
 template <int J>
 static void launch_rspace_j(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
@@ -2146,12 +2192,12 @@ template <int NR>
 static int launch_stage1_t(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
                            cudaStream_t s) {
   if (sp.path == MS_MOL_FUSED) {
-    if (!fused_point(sp)) return 0;
+    if (!use_point(sp)) return 0;
     mol_field_kernel<<<(sp.nmol + 127) / 128, 128, 0, s>>>(sp, md, g, prescribed, err);
     return 1;
   }
   int n = 0;
-  if (sp.jmax <= 4) {
+  if (use_point(sp)) {
     mol_field_kernel<<<(sp.nmol + 127) / 128, 128, 0, s>>>(sp, md, g, prescribed, err);
     ++n;
   }
@@ -2181,10 +2227,11 @@ template <int NR>
 static int launch_stage2_t(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
                            cudaStream_t s) {
   const bool fused = sp.path == MS_MOL_FUSED;
-  const StepShape sh = step_shape(NR, sp.nrot, fused);
+  const StepShape sh = sp.kern == MS_KERN_CHUNK && sp.ch > 0 ? step_shape_ch(NR, sp.nrot, fused, sp.ch)
+                                                             : step_shape(NR, sp.nrot, fused);
   if (fused) {
     if constexpr (NR == 128) {
-      if (fused_point(sp)) {
+      if (use_point(sp)) {
         launch_rpoint_n<NR, true>(sp, md, err, s);
         if (sp.dipw) launch_dipole_r<NR>(sp, md, err, s);
         return sp.dipw ? 2 : 1;
@@ -2193,7 +2240,7 @@ static int launch_stage2_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
     launch_step_tt<NR, true, 12>(sp, md, g, prescribed, err, sh, s);
     return 1;
   }
-  if (sp.jmax <= 4) {  // point-resident R-space pass
+  if (use_point(sp)) {  // point-resident R-space pass
     launch_rpoint_n<NR>(sp, md, err, s);
     if constexpr (NR <= 128) {
       if (sp.dipw) {
@@ -2204,7 +2251,7 @@ static int launch_stage2_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
     return 1;
   }
   RspaceMaps maps;
-  if (rspace_ok(NR, sp.jmax) && rspace_maps(sp, &maps)) {
+  if ((sp.kern == MS_KERN_DEFAULT || sp.kern == MS_KERN_TILE) && rspace_ok(NR, sp.jmax) && rspace_maps(sp, &maps)) {
     launch_rspace(sp, md, g, prescribed, err, maps, s);
     return 1;
   }

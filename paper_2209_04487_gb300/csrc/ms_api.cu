@@ -487,6 +487,156 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   return initial_populations(s, ids, n0);
 }
 
+// A plan switch to the streaming layout needs the (T - 1)s scratch.
+ms_status ensure_scratch(ms_sim* s, ms::SpeciesDev& sp) {
+  if (sp.d2 || sp.nmol == 0) return MS_OK;
+  return zeros(s, &sp.d2, (size_t)sp.nmol * sp.rows * sp.nr);
+}
+
+// Device memory released before returning (the tuner's sandbox).
+struct Scratch {
+  ms_sim* s;
+  std::vector<void*> p;
+  void* get(size_t n) {
+    void* q = nullptr;
+    if (s->al.fn) q = s->al.fn(n ? n : 16, s->al.ctx);
+    else if (cudaMalloc(&q, n ? n : 16) != cudaSuccess) {
+      cudaGetLastError();
+      q = nullptr;
+    }
+    if (q) p.push_back(q);
+    return q;
+  }
+  ~Scratch() {
+    cudaStreamSynchronize(s->stream);
+    for (void* q : p) {
+      if (s->al.fr) s->al.fr(q, s->al.ctx);
+      else cudaFree(q);
+    }
+  }
+};
+
+// Measure every plan of species si on a sandbox copy of up to 2,048 of its
+// molecules (own state, scratch, records and per-molecule arrays; the
+// species' read-only tables are shared) under a prescribed field of 5e9 V/m
+// along a seeded direction per molecule, and keep the fastest plan.
+ms_status tune_species(ms_sim* s, int si) {
+  ms::SpeciesDev& sp = s->sp[si];
+  int cand[16][3];
+  const int nc = ms::mol_plan_candidates(sp, cand, 16);
+  if (nc < 2 || sp.nmol == 0) return MS_OK;
+  const int nt = std::min(sp.nmol, 2048);
+  const size_t per = (size_t)sp.rows * sp.nr;
+  Scratch sc{s, {}};
+  ms::SpeciesDev t = sp;
+  ms::MolDev m = s->md;
+  t.nmol = nt;
+  t.psi = (float2*)sc.get(per * nt * sizeof(float2));
+  t.d2 = (float2*)sc.get(per * nt * sizeof(float2));
+  t.fld = (float4*)sc.get((size_t)nt * sizeof(float4));
+  int* mol = (int*)sc.get((size_t)nt * sizeof(int));
+  float* rot = (float*)sc.get((size_t)nt * 9 * sizeof(float));
+  double* dbl = (double*)sc.get((size_t)nt * 14 * sizeof(double));  // mu, dmu, pop, absorbed, Rnum, Rden
+  float* amp = (float*)sc.get((size_t)nt * 3 * sizeof(float));
+  float* wave = (float*)sc.get(sizeof(float));
+  long long* step = (long long*)sc.get(sizeof(long long));
+  int* err = (int*)sc.get(sizeof(int));
+  if (!t.psi || !t.d2 || !t.fld || !mol || !rot || !dbl || !amp || !wave || !step || !err) return MS_ENOMEM;
+  // the first nt molecules of the species: state and rotations
+  std::vector<int> ids(nt);
+  if (cudaMemcpy(ids.data(), sp.mol, nt * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MS_ECUDA;
+  std::vector<float> rh(9 * (size_t)nt);
+  for (int k = 0; k < nt; ++k)
+    if (cudaMemcpy(&rh[9 * (size_t)k], s->md.rot + 9 * (size_t)ids[k], 9 * sizeof(float),
+                   cudaMemcpyDeviceToHost) != cudaSuccess)
+      return MS_ECUDA;
+  std::vector<int> iota(nt);
+  std::vector<float> ah(3 * (size_t)nt);
+  uint64_t x = 0x9E3779B97F4A7C15ull;  // splitmix64: a seeded direction per molecule
+  for (int k = 0; k < nt; ++k) {
+    iota[k] = k;
+    double v[3], nn = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      x += 0x9E3779B97F4A7C15ull;
+      uint64_t z = x;
+      z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+      z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+      z ^= z >> 31;
+      v[c] = (double)(z >> 11) / 9007199254740992.0 - 0.5;
+      nn += v[c] * v[c];
+    }
+    nn = std::sqrt(nn > 0 ? nn : 1.0);
+    for (int c = 0; c < 3; ++c) ah[3 * (size_t)k + c] = (float)(5e9 * v[c] / nn);
+  }
+  const float one = 1.f;
+  const long long zero = 0;
+  if (cudaMemcpyAsync(t.psi, sp.psi, per * nt * sizeof(float2), cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess ||
+      cudaMemcpyAsync(mol, iota.data(), nt * sizeof(int), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      cudaMemcpyAsync(rot, rh.data(), rh.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      cudaMemcpyAsync(amp, ah.data(), ah.size() * sizeof(float), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      cudaMemcpyAsync(wave, &one, sizeof(float), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      cudaMemcpyAsync(step, &zero, sizeof(long long), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+      cudaMemsetAsync(dbl, 0, (size_t)nt * 14 * sizeof(double), s->stream) != cudaSuccess ||
+      cudaMemsetAsync(err, 0, sizeof(int), s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return MS_ECUDA;
+  t.mol = mol;
+  m.n = nt;
+  m.cell = nullptr;
+  m.rot = rot;
+  m.mu = dbl;
+  m.dmu = dbl + 3 * (size_t)nt;
+  m.pop = dbl + 6 * (size_t)nt;
+  m.absorbed = dbl + 8 * (size_t)nt;
+  m.Rnum = dbl + 10 * (size_t)nt;
+  m.Rden = dbl + 11 * (size_t)nt;
+  m.amp = amp;
+  m.wave = wave;
+  m.nwave = 1;
+  m.replay = nullptr;
+  ms::Grid g = s->g;
+  g.step = step;  // stays 0: the prescribed sample 0 every step
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MS_ECUDA;
+  float best = 0.f;
+  int pick = -1;
+  for (int c = 0; c < nc; ++c) {
+    t.path = cand[c][0];
+    t.kern = cand[c][1];
+    t.ch = cand[c][2];
+    auto run = [&]() {
+      ms::launch_mol_stage1(t, m, g, 1, err, s->stream);
+      ms::launch_mol_stage2(t, m, g, 1, err, s->stream);
+    };
+    for (int w = 0; w < 2; ++w) run();
+    cudaEventRecord(e0, s->stream);
+    for (int r = 0; r < 5; ++r) run();
+    cudaEventRecord(e1, s->stream);
+    float ms_ = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms_, e0, e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      return MS_ECUDA;
+    }
+    if (pick < 0 || ms_ < best) {
+      best = ms_;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int e = 0;
+  if (cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MS_ECUDA;
+  if (e != 0 || pick < 0) return MS_OK;  // a plan misbehaved in the sandbox: keep the static rule
+  ms::SpeciesDev trial = sp;
+  trial.path = cand[pick][0];
+  if (trial.path == MS_MOL_STREAMING) MS_TRY(ensure_scratch(s, trial));
+  sp = trial;
+  sp.kern = cand[pick][1];
+  sp.ch = cand[pick][2];
+  return MS_OK;
+}
+
 ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const ms_molecules_desc* D,
                       const ms_options* O, ms_sim* s) {
   const int nx = G->nx, ny = G->ny, nz = G->nz, nsim = G->nsim;
@@ -665,7 +815,10 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
     MS_TRY(build_species(s, si, D->species[si], dt * s->nsub, ids, O ? O->mol_path : MS_MOL_AUTO,
                          O && O->precision == MS_PREC_MIXED_F16X3, O && O->state_form == MS_STATE_PARITY));
   }
-  return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
+  if (O && O->autotune == MS_TUNE_MEASURE)
+    for (int si = 0; si < s->nspecies; ++si) MS_TRY(tune_species(s, si));
+  return MS_OK;
 }
 
 ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_molecules_desc* D,
@@ -701,6 +854,7 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
   if (O && (O->mol_path < MS_MOL_AUTO || O->mol_path > MS_MOL_STREAMING)) return MS_EINVAL;
   if (O && O->state_form != MS_STATE_FULL && O->state_form != MS_STATE_PARITY) return MS_EINVAL;
   if (O && O->step_graphs != MS_GRAPHS_AUTO && O->step_graphs != MS_GRAPHS_OFF) return MS_EINVAL;
+  if (O && O->autotune != MS_TUNE_OFF && O->autotune != MS_TUNE_MEASURE) return MS_EINVAL;
   const bool par = O && O->state_form == MS_STATE_PARITY;
   if (D && D->n_molecules > 0) {
     if (D->n_species <= 0 || D->n_species > ms::kMaxSpecies || !D->species || !D->species_id ||
@@ -1425,6 +1579,40 @@ ms_status ms_check_bounded_wait(int32_t tries) {
 int32_t ms_species_path(const ms_sim* s, int32_t species) {
   if (!s || species < 0 || species >= s->nspecies) return MS_EINVAL;
   return s->sp[species].path;
+}
+
+ms_status ms_species_plan(const ms_sim* s, int32_t species, int32_t* path, int32_t* kernel, int32_t* chunk) {
+  if (!s || !path || !kernel || !chunk || species < 0 || species >= s->nspecies) return MS_EINVAL;
+  const ms::SpeciesDev& sp = s->sp[species];
+  *path = sp.path;
+  *kernel = sp.kern;
+  *chunk = sp.ch;
+  return MS_OK;
+}
+
+ms_status ms_set_species_plan(ms_sim* s, int32_t species, int32_t path, int32_t kernel, int32_t chunk) {
+  if (!s || species < 0 || species >= s->nspecies) return MS_EINVAL;
+  ms::SpeciesDev& sp = s->sp[species];
+  if (sp.bloch) return MS_EINVAL;
+  int cand[16][3];
+  const int nc = ms::mol_plan_candidates(sp, cand, 16);
+  bool ok = false;
+  if (kernel == MS_KERN_DEFAULT && chunk == 0) {
+    for (int c = 0; c < nc; ++c) ok = ok || cand[c][0] == path;
+    ok = ok || path == sp.path;  // the layout it already runs
+  } else {
+    for (int c = 0; c < nc; ++c) ok = ok || (cand[c][0] == path && cand[c][1] == kernel && cand[c][2] == chunk);
+  }
+  if (!ok) return MS_EINVAL;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
+  ms::SpeciesDev trial = sp;
+  trial.path = path;
+  if (path == MS_MOL_STREAMING) MS_TRY(ensure_scratch(s, trial));
+  sp = trial;
+  sp.kern = kernel;
+  sp.ch = chunk;
+  s->gdirty = true;
+  return MS_OK;
 }
 
 size_t ms_device_bytes(const ms_sim* s) { return s ? s->bytes : 0; }

@@ -110,6 +110,7 @@ struct SpeciesDev {
   const uint16_t* kpl;      // mixed: (K - I) strip as four FP16 planes (Re hi, Re lo, Im hi, Im lo), x 2^kpl_exp
   int kpl_exp;
   int path;                 // MS_MOL_FUSED or MS_MOL_STREAMING
+  int kern, ch;             // plan: MS_KERN_* of the R-space pass, chunk width of the chunked kernel (0: its rule)
   // per (s, j, r): e^{-i V dtau} - 1 and e^{-i V dtau/2}
   const float2* vdelta;     // [2][jmax+1][nr]
   const float2* vhalf;      // [2][jmax+1][nr]
@@ -201,6 +202,8 @@ int launch_bloch_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int
                       cudaStream_t s);
 void launch_bloch_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s);
 bool mol_step_supported(int nr, int nrot, int path);
+// the (layout, kernel, chunk width) plans a species can run; returns how many
+int mol_plan_candidates(const SpeciesDev& sp, int (*out)[3], int max);
 cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip);
 cudaError_t upload_triplet_tables(const CouplEntry* dip);
 cudaError_t launch_wait_timeout_probe(int tries, int* flag, cudaStream_t s);

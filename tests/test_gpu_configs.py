@@ -5,7 +5,7 @@ sampled outputs the oracle computes one by one:
     state), mixed kinetic pass;
   * the 192^3 split-ring grid with 400,000 molecules of three species
     (N_r 64/128/256, J 4/8/16; 120 GB of state), plain FP32 (the mixed pass
-    has no N_r = 256 form);
+    has no N_r = 256 form), each species' plan picked by the autotuner;
   * 16 independent 64x64x128 nanohole cells with 20,000 molecules each at
     J <= 8, stepped in one launch per kernel.
 
@@ -108,9 +108,12 @@ def test_nanohole_700k_molecules_mixed(B):
 
 
 def test_splitring_three_species_400k(B):
+    """Plans picked by the create-time autotuner (the configuration's
+    scheduling), one per species."""
     wl = W.config3()
-    _need(2 * _state_bytes(wl) + 8e9)
-    sim = B.Simulation(wl)
+    _need(2 * _state_bytes(wl) + 12e9)
+    sim = B.Simulation(wl, autotune=B.MS_TUNE_MEASURE)
+    print("tuned plans", [sim.plan(s) for s in range(3)])
     _inject(B, sim, wl)
     rng = np.random.default_rng(22)
     sample = np.sort(np.concatenate([rng.choice(np.nonzero(wl.species_id == s)[0], 3, replace=False)

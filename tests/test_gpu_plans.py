@@ -1,0 +1,106 @@
+"""Every (layout, kernel, chunk width) plan a species can run computes the
+same step: each is pinned in turn through ms_set_species_plan and compared
+with the FP64 oracle at the plain tolerances.  The create-time autotuner
+picks one of them, and pinning its pick reproduces the tuned run bit for bit.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.coupled import CoupledOracle, PrescribedOracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2209_04487_gb300 import build
+    build.build()
+    from paper_2209_04487_gb300 import binding
+    return binding
+
+
+def _plans(B):
+    kc = [(B.MS_KERN_POINT, 0), (B.MS_KERN_TILE, 0)] + [(B.MS_KERN_CHUNK, c) for c in (32, 16, 8, 4)]
+    return [(p, k, c) for p in (B.MS_MOL_FUSED, B.MS_MOL_STREAMING) for k, c in kc]
+
+
+@pytest.mark.parametrize("nr,jmax,nmol", [(64, 1, 23), (128, 4, 9), (128, 6, 5), (64, 8, 4)])
+def test_every_plan_matches_oracle(B, nr, jmax, nmol):
+    sp = W.Species(nr=nr, jmax=jmax, A=0.05)
+    nsteps = 200
+    wl = W.custom("plans", 8, 8, 48, n_per_sim=nmol, species=[sp], layer=(20, 24), seed=nr + jmax, nsteps=nsteps)
+    amp, wave = W.prescribed_drive(nmol, nsteps, wl.dt, E0=3e10, carrier_ev=6.0, fwhm=0.5e-15, t0=0.4e-15)
+    o = PrescribedOracle(wl, amp, wave).run(nsteps)
+    Po = o.populations()
+    assert Po[:, 1].max() > 1e-6
+    ran = []
+    for plan in _plans(B):
+        sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, mol_path=B.MS_MOL_STREAMING)
+        try:
+            sim.set_plan(0, *plan)
+        except B.MSError as e:
+            assert e.code == B.MS_EINVAL
+            sim.close()
+            continue
+        assert sim.plan(0) == plan
+        sim.set_prescribed(amp, wave)
+        sim.step(nsteps)
+        P, mu = sim.populations(), sim.dipoles()
+        sim.close()
+        assert np.abs(P - Po).max() < 1e-5, plan
+        sel = Po[:, 1] > 1e-10
+        assert np.max(np.abs(P[sel, 1] - Po[sel, 1]) / Po[sel, 1]) < 1e-3, plan
+        assert np.abs(mu - o.mu).max() < 1e-4 * np.abs(o.mu).max(), plan
+        ran.append(plan)
+    kinds = {k for _, k, _ in ran}
+    assert B.MS_KERN_CHUNK in kinds and len(ran) >= 3, ran
+    if jmax <= 4:
+        assert B.MS_KERN_POINT in kinds
+    if jmax <= 7:
+        assert B.MS_KERN_TILE in kinds
+
+
+def test_autotuned_three_species_coupled(B):
+    """Three species tuned at create time, coupled run against the oracle;
+    pinning the tuned plans reproduces the run bit for bit."""
+    species = [W.species_config0(jmax=1), W.Species(nr=128, jmax=4, A=0.05), W.Species(nr=64, jmax=6)]
+    wl = W.custom("tuned", 16, 16, 48, src_k=14, pulses=[[2e10, 1.5498, 2e-15, 2e-15]], layer=(22, 26),
+                  n_per_sim=120, species=species, fractions=[0.4, 0.3, 0.3], seed=31, nsteps=300)
+    a = B.Simulation(wl, autotune=B.MS_TUNE_MEASURE)
+    plans = [a.plan(s) for s in range(3)]
+    print("tuned plans", plans)
+    a.step(wl.nsteps)
+    got = (a.populations(), a.dipoles(), a.fields(B.MS_FIELD_E))
+    a.close()
+    o = CoupledOracle(wl).run(wl.nsteps)
+    Eo = np.stack([o.f.Ex[0], o.f.Ey[0], o.f.Ez[0]])
+    assert np.linalg.norm(got[2] - Eo) / np.linalg.norm(Eo) < 1e-4
+    assert np.abs(got[0] - o.populations()).max() < 1e-5
+    assert np.abs(got[1] - o.mu).max() < 1e-3 * np.abs(o.mu).max()
+    b = B.Simulation(wl)
+    for s, p in enumerate(plans):
+        b.set_plan(s, *p)
+    b.step(wl.nsteps)
+    for x, y in zip(got, (b.populations(), b.dipoles(), b.fields(B.MS_FIELD_E))):
+        assert np.array_equal(x, y)
+    b.close()
+
+
+def test_plan_validation(B):
+    wl = W.custom("plan checks", 8, 8, 48, n_per_sim=5, species=[W.Species(nr=64, jmax=8)], layer=(20, 24),
+                  nsteps=10)
+    sim = B.Simulation(wl)
+    for bad in ((B.MS_MOL_STREAMING, B.MS_KERN_POINT, 0),    # J = 8: no point-resident kernel
+                (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 0),     # J = 8: no tile kernel
+                (B.MS_MOL_STREAMING, B.MS_KERN_CHUNK, 12),   # not a chunk width
+                (7, B.MS_KERN_CHUNK, 8)):
+        with pytest.raises(B.MSError) as e:
+            sim.set_plan(0, *bad)
+        assert e.value.code == B.MS_EINVAL
+    sim.set_plan(0, B.MS_MOL_STREAMING, B.MS_KERN_DEFAULT, 0)
+    sim.step(2)
+    sim.close()
