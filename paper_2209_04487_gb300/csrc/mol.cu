@@ -2006,7 +2006,8 @@ __global__ void __launch_bounds__(256, 1) mol_kinetic_tc_kernel(SpeciesDev sp, l
   uint8_t* Bt = smem_tc + 4 * APL;  // two tile buffers, each Re hi, Re lo, Im hi, Im lo
   __shared__ __align__(8) unsigned long long bar[2];  // [0] A staged, [1] products done
   __shared__ unsigned tmem_base;
-  __shared__ int s_rmax[2][TR], s_rexp[2][TR];          // per tile buffer: row maxima, row scale exponents
+  __shared__ float s_wmax[8][TR];                       // per warp: row maxima of the tile being staged
+  __shared__ int s_rexp[2][TR];                         // per tile buffer: row scale exponents
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   const float2* X = sp.psi;
   float2* Y = sp.d2;
@@ -2061,18 +2062,35 @@ __global__ void __launch_bounds__(256, 1) mol_kinetic_tc_kernel(SpeciesDev sp, l
   // scaled by 2^e so that its largest |Re|, |Im| lies in [2^14, 2^15) (an
   // exact power-of-two scale, undone on write-out): hi = fp16(x), lo =
   // fp16(x - hi) then carry 22 bits of every element of the row's scale.
+  // Row maxima: slot u of every thread lies in row group u / UPQ (rows 8 q +
+  // (lane & 7)) whatever the warp, so each thread folds its slots per group,
+  // the four lanes sharing a row fold by shuffles, and each warp leaves one
+  // value per row; 64 threads then fold the 8 warps' values.
   auto stage = [&](int buf) {
+    constexpr int UPQ = LOADS / 8;
+    static_assert(LOADS % 8 == 0 && TR == 64, "eight row groups of eight rows per tile");
     uint8_t* B0 = Bt + buf * 4 * BPL;
-    if (t < TR) s_rmax[buf][t] = 0;
-    __syncthreads();
+    float rm[8];
 #pragma unroll
-    for (int u = 0; u < LOADS; ++u) {
-      const float m = fmaxf(fmaxf(fabsf(pre[u].x), fabsf(pre[u].y)), fmaxf(fabsf(pre[u].z), fabsf(pre[u].w)));
-      atomicMax(&s_rmax[buf][slot_row(u)], __float_as_int(m));  // non-negative floats order as ints
+    for (int q = 0; q < 8; ++q) rm[q] = 0.f;
+#pragma unroll
+    for (int u = 0; u < LOADS; ++u)
+      rm[u / UPQ] = fmaxf(rm[u / UPQ], fmaxf(fmaxf(fabsf(pre[u].x), fabsf(pre[u].y)),
+                                             fmaxf(fabsf(pre[u].z), fabsf(pre[u].w))));
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      rm[q] = fmaxf(rm[q], __shfl_xor_sync(0xffffffffu, rm[q], 8));
+      rm[q] = fmaxf(rm[q], __shfl_xor_sync(0xffffffffu, rm[q], 16));
+    }
+    if (lane < 8) {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) s_wmax[w][8 * q + lane] = rm[q];
     }
     __syncthreads();
     if (t < TR) {
-      const float m = __int_as_float(s_rmax[buf][t]);
+      float m = 0.f;
+#pragma unroll
+      for (int ww = 0; ww < 8; ++ww) m = fmaxf(m, s_wmax[ww][t]);
       int ex = 0;
       if (m > 0.f) frexpf(m, &ex);
       s_rexp[buf][t] = m > 0.f ? min(15 - ex, 100) : 0;
