@@ -1,6 +1,6 @@
 """GPU path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances (BASELINE targets): fields relative L2 <= 1e-4, populations abs
+Tolerances (the stated targets): fields relative L2 <= 1e-4, populations abs
 <= 1e-5 (plus relative 1e-3 on P_e where P_e > 1e-10), norm drift <= 1e-6.
 """
 import numpy as np
