@@ -1474,6 +1474,31 @@ CkHeader make_header(ms_sim* s, uint64_t nblobs) {
 }
 
 constexpr size_t kCkChunk = 64u << 20;  // host staging buffer
+
+// Two pinned staging buffers for checkpoint I/O: the copy between the device
+// and one buffer overlaps the file transfer of the other.  ok = false (the
+// pageable path is used) when pinned memory cannot be had.
+struct PinnedPair {
+  char* p[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  bool ok = false;
+  PinnedPair() {
+    ok = true;
+    for (int i = 0; i < 2 && ok; ++i)
+      ok = cudaHostAlloc(reinterpret_cast<void**>(&p[i]), kCkChunk, cudaHostAllocDefault) == cudaSuccess &&
+           cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+  }
+  ~PinnedPair() {
+    for (int i = 0; i < 2; ++i) {
+      if (ev[i]) {
+        cudaEventSynchronize(ev[i]);  // no copy still reads or writes the buffer
+        cudaEventDestroy(ev[i]);
+      }
+      if (p[i]) cudaFreeHost(p[i]);
+    }
+  }
+};
 }  // namespace
 
 ms_status ms_save(ms_sim* s, const char* path) {
@@ -1484,12 +1509,39 @@ ms_status ms_save(ms_sim* s, const char* path) {
   FILE* f = std::fopen(path, "wb");
   if (!f) return MS_EIO;
   ms_status st = std::fwrite(&h, sizeof(h), 1, f) == 1 ? MS_OK : MS_EIO;
+  PinnedPair pin;
   std::vector<char> buf;
   for (size_t k = 0; st == MS_OK && k < blobs.size(); ++k) {
     const uint64_t nb = blobs[k].bytes;
     if (std::fwrite(&nb, sizeof(nb), 1, f) != 1) {
       st = MS_EIO;
       break;
+    }
+    if (pin.ok) {  // chunk c copies into buffer c & 1 while chunk c - 1 is written out
+      size_t prev_len = 0;
+      int c = 0;
+      for (size_t off = 0; st == MS_OK && off < nb; off += kCkChunk, ++c) {
+        const size_t len = std::min(kCkChunk, (size_t)nb - off);
+        const int b = c & 1;
+        if (cudaEventSynchronize(pin.ev[b]) != cudaSuccess ||
+            cudaMemcpyAsync(pin.p[b], static_cast<char*>(blobs[k].ptr) + off, len, cudaMemcpyDeviceToHost,
+                            s->stream) != cudaSuccess ||
+            cudaEventRecord(pin.ev[b], s->stream) != cudaSuccess) {
+          st = MS_ECUDA;
+          break;
+        }
+        if (c > 0) {
+          if (cudaEventSynchronize(pin.ev[b ^ 1]) != cudaSuccess) st = MS_ECUDA;
+          else if (std::fwrite(pin.p[b ^ 1], 1, prev_len, f) != prev_len) st = MS_EIO;
+        }
+        prev_len = len;
+      }
+      if (st == MS_OK && c > 0) {
+        const int b = (c - 1) & 1;
+        if (cudaEventSynchronize(pin.ev[b]) != cudaSuccess) st = MS_ECUDA;
+        else if (std::fwrite(pin.p[b], 1, prev_len, f) != prev_len) st = MS_EIO;
+      }
+      continue;
     }
     for (size_t off = 0; off < nb; off += kCkChunk) {
       const size_t len = std::min(kCkChunk, (size_t)nb - off);
@@ -1525,6 +1577,7 @@ ms_status ms_load(ms_sim* s, const char* path) {
     a.steps = b.steps = 0;
     if (std::memcmp(&a, &b, sizeof(a)) != 0) st = MS_EINVAL;
   }
+  PinnedPair pin;
   std::vector<char> buf;
   for (size_t k = 0; st == MS_OK && k < blobs.size(); ++k) {
     uint64_t nb = 0;
@@ -1535,6 +1588,28 @@ ms_status ms_load(ms_sim* s, const char* path) {
     if (nb != blobs[k].bytes) {
       st = MS_EINVAL;
       break;
+    }
+    if (pin.ok) {  // chunk c is read into buffer c & 1 while chunk c - 1 copies to the device
+      int c = 0;
+      for (size_t off = 0; off < nb; off += kCkChunk, ++c) {
+        const size_t len = std::min(kCkChunk, (size_t)nb - off);
+        const int b = c & 1;
+        if (cudaEventSynchronize(pin.ev[b]) != cudaSuccess) {
+          st = MS_ECUDA;
+          break;
+        }
+        if (std::fread(pin.p[b], 1, len, f) != len) {
+          st = MS_EIO;
+          break;
+        }
+        if (cudaMemcpyAsync(static_cast<char*>(blobs[k].ptr) + off, pin.p[b], len, cudaMemcpyHostToDevice,
+                            s->stream) != cudaSuccess ||
+            cudaEventRecord(pin.ev[b], s->stream) != cudaSuccess) {
+          st = MS_ECUDA;
+          break;
+        }
+      }
+      continue;
     }
     for (size_t off = 0; off < nb; off += kCkChunk) {
       const size_t len = std::min(kCkChunk, (size_t)nb - off);
@@ -1551,6 +1626,7 @@ ms_status ms_load(ms_sim* s, const char* path) {
     }
   }
   std::fclose(f);
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess && st == MS_OK) st = MS_ECUDA;  // copies in flight
   if (st != MS_OK) return st;
   // the step counter, host and device
   const long long step = h.steps;
