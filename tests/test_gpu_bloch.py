@@ -133,3 +133,27 @@ def test_bloch_checkpoint_is_bitwise(B, tmp_path):
     assert e.value.code == B.MS_EINVAL
     b.close()
     c.close()
+
+
+@pytest.mark.parametrize("detune", [0.0, -2.0])
+def test_gpu_polarizable_sheet_reflects_as_closed_form(B, detune):
+    """The coupled loop on the GPU against the thin-sheet closed form (the
+    oracle's pin of the whole loop; see tests/test_oracle_coupled_loop_pins)."""
+    from oracle.constants import HBAR_EVS
+    from tests.test_oracle_coupled_loop_pins import E0, T2, W_EV, amplitudes, closed_form, sheet_workload
+    delta = detune * HBAR_EVS / T2
+    wl = sheet_workload(delta)
+    per = int(round(2 * np.pi / (W_EV / HBAR_EVS) / wl.dt))
+    sim = B.Simulation(wl)
+    sim.step(wl.nsteps - 2 * per)
+    tr, tt = [], []
+    for _ in range(2 * per):
+        sim.step(1)
+        E = sim.fields(B.MS_FIELD_E)
+        tr.append(E[0, 15, 0, 0])
+        tt.append(E[0, 80, 0, 0])
+    sim.close()
+    r_sim, t_sim = amplitudes(np.array(tr, np.float64), np.array(tt, np.float64))
+    r, t, _ = closed_form(delta, wl.dx)
+    assert abs(r_sim - abs(r)) < 6e-3 * abs(r), (r_sim, abs(r))
+    assert abs(t_sim - abs(t)) < 5e-4, (t_sim, abs(t))
