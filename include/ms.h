@@ -110,8 +110,8 @@ enum { MS_GRAPHS_AUTO = 0, MS_GRAPHS_OFF = 1 };
  * results differ by FP32 rounding.
  * Autotuning (ms_options.autotune = MS_TUNE_MEASURE): ms_create times every
  * plan a species can run on a sandbox copy of up to 2,048 of its molecules
- * under a strong prescribed field (three coupling-series terms, as at a
- * pulse peak) and keeps the fastest; ms_species_plan reports the choice and
+ * under a strong prescribed field (5e9 V/m, the coupling series' term count
+ * of a pulse peak) and keeps the fastest; ms_species_plan reports the choice and
  * ms_set_species_plan pins one, so a tuned choice can be replayed. */
 enum { MS_KERN_DEFAULT = 0, MS_KERN_POINT = 1, MS_KERN_TILE = 2, MS_KERN_CHUNK = 3 };
 enum { MS_TUNE_OFF = 0, MS_TUNE_MEASURE = 1 };
