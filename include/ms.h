@@ -102,7 +102,7 @@ enum { MS_GRAPHS_AUTO = 0, MS_GRAPHS_OFF = 1 };
  * kernel of its R-space pass.  MS_KERN_POINT: one CTA of 2 N_r threads per
  * molecule, thread = (radial point, surface) (J <= 4; fused at N_r 128).
  * MS_KERN_TILE: one CTA per molecule over 32-point tiles of all rows, staged
- * by tensor copies (J <= 7, streaming).  MS_KERN_CHUNK: one CTA per molecule
+ * by tensor copies (J <= 8, streaming).  MS_KERN_CHUNK: one CTA per molecule
  * over chunks of `chunk` radial points (4, 8, 16 or 32) of all rows (any J).
  * MS_KERN_DEFAULT: the static rule (the first that applies of point, tile,
  * chunk at the widest fitting chunk).  Parity-reduced and d(R) species run

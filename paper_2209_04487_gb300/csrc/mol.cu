@@ -1812,9 +1812,9 @@ static StepShape step_shape_ch(int nr, int nrot, bool fused, int ch) {
   return {ch, 24, 0, false};
 }
 
-// The streaming R-space kernel covers J <= 7 (rows <= 128) on radial grids of
+// The streaming R-space kernel covers J <= 8 (rows <= 162) on radial grids of
 // whole 32-point chunks.
-static bool rspace_ok(int nr, int jmax) { return nr % kTile == 0 && (nr / kTile) % 2 == 0 && jmax <= 7; }
+static bool rspace_ok(int nr, int jmax) { return nr % kTile == 0 && (nr / kTile) % 2 == 0 && jmax <= 8; }
 
 // The plans a species can run: (layout, kernel, chunk width).  Parity-reduced
 // and d(R) species have one (the point-resident kernel); the mixed kinetic
@@ -1863,6 +1863,7 @@ static void launch_rspace(const SpeciesDev& sp, const MolDev& md, const Grid& g,
     case 5: launch_rspace_j<5>(sp, md, g, prescribed, err, maps, s); break;
     case 6: launch_rspace_j<6>(sp, md, g, prescribed, err, maps, s); break;
     case 7: launch_rspace_j<7>(sp, md, g, prescribed, err, maps, s); break;
+    case 8: launch_rspace_j<8>(sp, md, g, prescribed, err, maps, s); break;
   }
 }
 

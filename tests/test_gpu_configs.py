@@ -66,6 +66,21 @@ def _inject(B, sim, wl, E0=5e9, seed=5):
         sim.write_fields(B.MS_FIELD_E, s, E)
 
 
+def _time_steps(sim, wl, n=5):
+    """Coupled steps after the check: wall time with the stream drained,
+    printed with the state's one-read-one-write bandwidth."""
+    import time
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.step(n)
+    sim.populations()            # drains the stream
+    dt = (time.perf_counter() - t0) / n
+    gbs = 2 * _state_bytes(wl) / dt / 1e9
+    print(f"{wl.name}: {dt * 1e3:.1f} ms per step, {wl.n_molecules / dt:.3e} molecule-steps/s, "
+          f"{wl.cells / dt:.3e} cell-updates/s, state read+write {gbs:.0f} GB/s")
+
+
 def _check_sample(wl, sim, sample, rec, nsteps):
     P = sim.populations()
     mu = sim.dipoles()
@@ -104,6 +119,7 @@ def test_nanohole_700k_molecules_mixed(B):
     nsteps = 12
     rec = sim.record_local_fields(sample, nsteps)
     _check_sample(wl, sim, sample, rec, nsteps)
+    _time_steps(sim, wl)
     sim.close()
 
 
@@ -121,6 +137,7 @@ def test_splitring_three_species_400k(B):
     nsteps = 8
     rec = sim.record_local_fields(sample, nsteps)
     _check_sample(wl, sim, sample, rec, nsteps)
+    _time_steps(sim, wl)
     sim.close()
 
 
@@ -135,4 +152,5 @@ def test_sixteen_nanohole_cells_in_one_launch(B):
     nsteps = 20
     rec = sim.record_local_fields(sample, nsteps)
     _check_sample(wl, sim, sample, rec, nsteps)
+    _time_steps(sim, wl)
     sim.close()

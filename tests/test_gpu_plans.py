@@ -91,11 +91,11 @@ def test_autotuned_three_species_coupled(B):
 
 
 def test_plan_validation(B):
-    wl = W.custom("plan checks", 8, 8, 48, n_per_sim=5, species=[W.Species(nr=64, jmax=8)], layer=(20, 24),
+    wl = W.custom("plan checks", 8, 8, 48, n_per_sim=5, species=[W.Species(nr=64, jmax=9)], layer=(20, 24),
                   nsteps=10)
     sim = B.Simulation(wl)
-    for bad in ((B.MS_MOL_STREAMING, B.MS_KERN_POINT, 0),    # J = 8: no point-resident kernel
-                (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 0),     # J = 8: no tile kernel
+    for bad in ((B.MS_MOL_STREAMING, B.MS_KERN_POINT, 0),    # J = 9: no point-resident kernel
+                (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 0),     # J = 9: no tile kernel
                 (B.MS_MOL_STREAMING, B.MS_KERN_CHUNK, 12),   # not a chunk width
                 (7, B.MS_KERN_CHUNK, 8)):
         with pytest.raises(B.MSError) as e:
