@@ -597,7 +597,11 @@ ms_status tune_species(ms_sim* s, int si) {
   ms::Grid g = s->g;
   g.step = step;  // stays 0: the prescribed sample 0 every step
   cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return MS_ECUDA;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return MS_ECUDA;
+  }
   float best = 0.f;
   int pick = -1;
   for (int c = 0; c < nc; ++c) {
