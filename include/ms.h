@@ -10,8 +10,10 @@
  *     wavepackets xi^{g,e}_{jm}(R) on a ground and an excited surface
  *     (Eq. 3), advanced by split-operator steps of Eq. 4 with the effective
  *     Hamiltonians of Eq. 5 (Morse ground surface Eq. 6, repulsive excited
- *     surface of the Eq. 7 family, constant transition dipole) under the
- *     local field E^n at the molecule's cell;
+ *     surface of the Eq. 7 family, constant transition dipole or a given
+ *     d(R)) under the local field E^n at the molecule's cell, every step or
+ *     every N-th step by N dt; or frozen two-level molecules (Bloch
+ *     equations, RK4; the scaling-experiments section);
  *   - the induced dipoles, multiplied by the molecular number density
  *     (one molecule per molecule: 1/dx^3 per cell), enter Ampere's law as
  *     the polarization current dP/dt (section "Efficient numerical
@@ -364,16 +366,18 @@ ms_status ms_read_dft(ms_sim* sim, int32_t plane, int32_t sim_index, int32_t com
  *   - the fields E and H;
  *   - the Drude current;
  *   - the CPML auxiliaries and the incident line;
- *   - every species' wavepackets;
+ *   - every species' wavepackets (Bloch vectors for frozen molecules);
  *   - the molecules' dipoles, populations and absorbed norm;
  *   - the detectors' running Fourier transforms (when set);
  *   - the step counter.
  * The inputs (geometry, materials, molecules, drive samples) are not saved.
  * ms_load restores such a file into a handle created from the same
- * descriptors; the sizes in the file must match (MS_EINVAL otherwise).  A
- * prescribed or replay drive is set again by the caller.  N steps equal
- * N/2 steps, save, load into a fresh handle, N/2 steps, bit for bit.  Both
- * calls are synchronous and stage through a bounded host buffer.  Errors:
+ * descriptors and options; the sizes, the sub-step count and the source
+ * kind in the file must match (MS_EINVAL otherwise).  A prescribed or replay
+ * drive is set again by the caller.  N steps equal N/2 steps, save, load
+ * into a fresh handle, N/2 steps, bit for bit.  Both calls are synchronous
+ * and stage through two pinned 64 MiB host buffers (pageable memory when
+ * pinned memory cannot be had).  Errors:
  * MS_EINVAL (NULL argument, size mismatch), MS_EIO (open, short read or
  * write, wrong magic or version), MS_ECUDA. */
 ms_status ms_save(ms_sim* sim, const char* path);
@@ -384,11 +388,14 @@ ms_status ms_load(ms_sim* sim, const char* path);
  * phases; ms_timing_end synchronises and writes the summed durations in
  * milliseconds: out[0] H half step (H update and incident line), out[1]
  * molecular step (all species), out[2] E half step (E update, incident
- * line, step counter), out[3] their sum, out[4] the molecular step's first
- * stage (streaming form: field records and kinetic pass), out[5] its second
- * stage (streaming form: R-space pass; fused form: the whole step); *steps
- * receives the number of steps timed and *launches the number of kernels
- * launched. */
+ * line, spectral detection when set), out[3] their sum (the one-thread step
+ * counter runs between steps, outside these spans), out[4] the molecular
+ * step's first stage (streaming form: field records and kinetic pass),
+ * out[5] its second stage (streaming form: R-space pass; fused form: the
+ * whole step); *steps receives the number of steps timed and *launches the
+ * number of kernels launched.  While timing is on, ms_step launches every
+ * kernel itself (no graph replay).  Errors: MS_EINVAL for a NULL handle or
+ * out, MS_ECUDA. */
 ms_status ms_timing_begin(ms_sim* sim);
 ms_status ms_timing_end(ms_sim* sim, double out[6], int64_t* steps, int64_t* launches);
 
@@ -423,7 +430,13 @@ ms_status ms_set_species_plan(ms_sim* sim, int32_t species, int32_t path, int32_
 /* Device memory held by the simulation, in bytes. */
 size_t ms_device_bytes(const ms_sim* sim);
 
+/* Release the handle: waits for its stream, frees every device block (through
+ * the caller's allocator when one was given), destroys the library's own
+ * stream and any captured graph.  NULL is a no-op. */
 void ms_destroy(ms_sim* sim);
+
+/* A static, NUL-terminated description of a status code ("unknown status" for
+ * a value that is not one). */
 const char* ms_status_string(ms_status s);
 
 #ifdef __cplusplus
