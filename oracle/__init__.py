@@ -14,7 +14,12 @@ NumPy, sharing no code with the CUDA path (the seeded input generators in
                   effective Hamiltonians, split-operator propagation,
                   dipole / population / absorbed-norm / Eq. 8 observables.
 * ``coupled``  -- the coupled time step (fields drive molecules, the
-                  molecular polarization current feeds back into Ampere's law).
+                  molecular polarization current feeds back into Ampere's law),
+                  with the every-N-th-step molecular cadence.
+* ``bloch``    -- frozen two-level molecules (Bloch equations, RK4; the
+                  scaling-experiments section, Fig. 5d).
+* ``spectra``  -- running DFTs on z-planes and Poynting flux spectra (the
+                  transmission / reflection spectra of Figs. 2, 4 and 6a).
 
 Every function cites the passage of the paper it follows.  Functions whose
 result has no independent check carry the words "parity unpinned".

@@ -1,5 +1,7 @@
 """The coupled Maxwell-Schroedinger time step, FP64, in the paper's order.
 
+Test infrastructure only (see the package header): the library never calls it.
+
 Section "Efficient numerical implementation of quantum dynamics ...": each
 molecule takes the local electric field at its grid point as input, returns
 its induced dipole, and the mean-field polarization (dipole times number

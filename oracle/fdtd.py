@@ -1,5 +1,7 @@
 """FP64 Yee FDTD with Drude metal, CPML in z, periodic x/y and a TF/SF source.
 
+Test infrastructure only (see the package header): the library never calls it.
+
 Follows the paper's field model: Maxwell's curl equations (Eq. 1) marched by
 the leap-frog Yee scheme with central differences (section "The domain
 decomposition methodology for FDTD"), a Drude current in metal cells

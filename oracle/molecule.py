@@ -1,5 +1,7 @@
 """FP64 ro-vibrational wavepackets on two coupled surfaces (Eqs. 3-8).
 
+Test infrastructure only (see the package header): the library never calls it.
+
 Each molecule carries xi^{(s)}_{jm}(R), s in {g, e}, j <= Jmax, |m| <= j,
 on a uniform radial grid (Eq. 3: expansion of chi_{g,e} in rotational
 functions).  One step of length dtau advances Eq. 4 with the effective
