@@ -1,5 +1,4 @@
-"""The other benchmark configurations at full size, through the C ABI, on
-sampled outputs the oracle computes one by one:
+"""The other benchmark configurations at full size, through the C ABI:
 
   * the 256^3 nanohole grid with 700,000 molecules at J <= 8 (116 GB of
     state), mixed kinetic pass;
@@ -9,20 +8,24 @@ sampled outputs the oracle computes one by one:
   * 16 independent 64x64x128 nanohole cells with 20,000 molecules each at
     J <= 8, stepped in one launch per kernel.
 
-Reaching the pulse peak takes thousands of steps of these grids, so each run
-starts from a seeded E field written into the molecular layer (5e9 V/m,
-smooth in x, y) and runs coupled for a few steps: the molecules are
-polarised by it and scatter back into the grid.  The local fields of a
-seeded sample are recorded at every step (the very E^n their kernels used)
-and the oracle integrates those molecules in FP64 under them.  Every
-molecule's populations are checked for finiteness and norm bookkeeping.
+The oracle cannot run these coupled systems, so each is checked in three
+parts whose oracle inputs come from the test, never from the CUDA path:
+  1. every molecule under a seeded prescribed drive (5e9 V/m through its
+     maximum) for a few steps, a seeded sample integrated one by one by the
+     oracle on the same drive;
+  2. the coupled run (molecules and fields, from a seeded E field written
+     into the molecular layer): properties that hold at any size -- every
+     molecule's norm bookkeeping and finite values -- and its step time;
+  3. the full field grid(s) without molecules from the same seeded field, a
+     few steps, against the oracle on the whole grid.
+Each part's device memory is returned before the next (the large states
+first).
 """
 import numpy as np
 import pytest
 
 import workloads as W
-from oracle.coupled import ensemble
-from oracle.molecule import dtau_au
+from oracle.coupled import CoupledOracle, PrescribedOracle
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -38,6 +41,16 @@ def B():
     return binding
 
 
+def _release():
+    """Return the closed handles' device memory to the device (the binding
+    allocates through PyTorch's caching allocator)."""
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+
+
 def _state_bytes(wl):
     return sum(16 * sp.nr * sp.nrot * int((wl.species_id == i).sum()) for i, sp in enumerate(wl.species))
 
@@ -50,77 +63,104 @@ def _need(nbytes):
         pytest.skip(f"needs {nbytes / 1e9:.0f} GB of free device memory, {free / 1e9:.0f} GB free")
 
 
-def _inject(B, sim, wl, E0=5e9, seed=5):
-    """A smooth seeded field in the molecular layer of every sim."""
+def _seeded_field(wl, E0=5e9, seed=5):
+    """A smooth seeded E field in the molecular layer of every sim, [nsim][3][nz][ny][nx]."""
     rng = np.random.default_rng(seed)
     k0, k1 = wl.meta["layer"]
     x = np.arange(wl.nx) * 2 * np.pi / wl.nx
     y = np.arange(wl.ny) * 2 * np.pi / wl.ny
+    out = np.zeros((wl.nsim, 3, wl.nz, wl.ny, wl.nx), np.float32)
     for s in range(wl.nsim):
-        E = np.zeros((3, wl.nz, wl.ny, wl.nx), np.float32)
         for c in range(3):
-            a, b, p, q = rng.uniform(0.5, 1.0), rng.uniform(0.5, 1.0), rng.uniform(0, 2 * np.pi, 2)[0], \
+            a, b, p, q = rng.uniform(0.5, 1.0), rng.uniform(0.5, 1.0), rng.uniform(0, 2 * np.pi), \
                 rng.uniform(0, 2 * np.pi)
             pat = a * np.cos(x[None, :] + p) + b * np.sin(2 * y[:, None] + q)
-            E[c, k0 - 2:k1 + 2] = (E0 / 2 * pat)[None].astype(np.float32)
-        sim.write_fields(B.MS_FIELD_E, s, E)
+            out[s, c, k0 - 2:k1 + 2] = (E0 / 2 * pat)[None].astype(np.float32)
+    return out
 
 
-def _time_steps(sim, wl, n=5):
-    """Coupled steps after the check: wall time with the stream drained,
-    printed with the state's one-read-one-write bandwidth."""
+def _molecules_prescribed(B, wl, precision, sample, nsteps=12):
+    """Part 1: all molecules under a seeded prescribed drive; the sample against the oracle."""
+    amp, wave = W.prescribed_drive(wl.n_molecules, nsteps, wl.dt, E0=5e9, carrier_ev=6.0, fwhm=0.02e-15,
+                                   t0=0.5 * nsteps * wl.dt, seed=79)
+    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, precision=precision)
+    sim.set_prescribed(amp, wave)
+    sim.step(nsteps)
+    P, mu = sim.populations(), sim.dipoles()
+    absb, _ = sim.dissociation()
+    sim.close()
+    del sim
+    _release()
+    o = PrescribedOracle(wl, amp, wave, select=sample).run(nsteps)
+    Po = o.populations()
+    worst = (np.abs(P[sample] - Po).max(), np.abs(mu[sample] - o.mu).max() / np.abs(o.mu).max())
+    print(f"{wl.name}: prescribed sample |dP| {worst[0]:.2e}, |dmu|/max {worst[1]:.2e}, P_e max {Po[:, 1].max():.2e}")
+    assert Po[:, 1].max() > 1e-8
+    assert worst[0] < 1e-5
+    sel = Po[:, 1] > 1e-10
+    assert np.max(np.abs(P[sample][sel, 1] - Po[sel, 1]) / Po[sel, 1]) < 1e-3
+    assert worst[1] < 1e-4
+    tot = P.sum(axis=1) + absb.sum(axis=1)
+    assert np.isfinite(P).all() and np.abs(tot - 1).max() < 1e-6
+
+
+def _fields_vs_oracle(B, wl, E, nsteps=6):
+    """Part 2: the full grid(s) without molecules from the seeded field, against the oracle."""
+    sim = B.Simulation(wl, with_molecules=False)
+    for s in range(wl.nsim):
+        sim.write_fields(B.MS_FIELD_E, s, E[s])
+    sim.step(nsteps)
+    o = CoupledOracle(wl, with_molecules=False)
+    Ef = E.astype(np.float64)
+    o.f.Ex[:], o.f.Ey[:], o.f.Ez[:] = Ef[:, 0], Ef[:, 1], Ef[:, 2]
+    o.run(nsteps)
+    for s in range(wl.nsim):
+        got = np.stack([sim.fields(B.MS_FIELD_E, s), sim.fields(B.MS_FIELD_H, s)])
+        want = np.stack([np.stack([o.f.Ex[s], o.f.Ey[s], o.f.Ez[s]]), np.stack([o.f.Hx[s], o.f.Hy[s], o.f.Hz[s]])])
+        for k in range(2):
+            rel = np.linalg.norm(got[k] - want[k]) / np.linalg.norm(want[k])
+            assert rel < 1e-4, (s, "EH"[k], rel)
+    sim.close()
+    del sim
+    _release()
+
+
+def _coupled_properties(B, wl, E, nsteps, **kw):
+    """Part 3: the coupled run from the seeded field: norm bookkeeping, finite values, step time."""
     import time
     import torch
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sim.step(n)
-    sim.populations()            # drains the stream
-    dt = (time.perf_counter() - t0) / n
-    gbs = 2 * _state_bytes(wl) / dt / 1e9
-    print(f"{wl.name}: {dt * 1e3:.1f} ms per step, {wl.n_molecules / dt:.3e} molecule-steps/s, "
-          f"{wl.cells / dt:.3e} cell-updates/s, state read+write {gbs:.0f} GB/s")
-
-
-def _check_sample(wl, sim, sample, rec, nsteps):
-    P = sim.populations()
-    mu = sim.dipoles()
+    sim = B.Simulation(wl, **kw)
+    if kw.get("autotune"):
+        print("tuned plans", [sim.plan(s) for s in range(len(wl.species))])
+    for s in range(wl.nsim):
+        sim.write_fields(B.MS_FIELD_E, s, E[s])
+    sim.step(nsteps)
+    P, mu = sim.populations(), sim.dipoles()
     absb, _ = sim.dissociation()
-    worst = {}
-    for si, sp in enumerate(wl.species):
-        sel = sample[wl.species_id[sample] == si]
-        if sel.size == 0:
-            continue
-        idx = np.searchsorted(sample, sel)
-        ens = ensemble(sp, wl.quat[sel], dtau_au(wl.dt * wl.mol_substeps))
-        for n in range(nsteps):
-            ens.step(rec[n][idx].astype(np.float64))
-        Po, mo = ens.populations(), ens.mu_lab
-        dP = np.abs(P[sel] - Po).max()
-        pe = Po[:, 1] > 1e-10
-        rel = np.max(np.abs(P[sel][pe, 1] - Po[pe, 1]) / Po[pe, 1]) if pe.any() else 0.0
-        dmu = np.abs(mu[sel] - mo).max() / max(np.abs(mo).max(), 1e-300)
-        worst[si] = (dP, rel, dmu, Po[:, 1].max())
-        assert Po[:, 1].max() > 1e-8, (si, "the injected field did not reach the sample")
-        assert dP < 1e-5, (si, dP)
-        assert rel < 1e-3, (si, rel)
-        assert dmu < 1e-4, (si, dmu)
     tot = P.sum(axis=1) + absb.sum(axis=1)
     assert np.isfinite(P).all() and np.isfinite(mu).all()
     assert np.abs(tot - 1).max() < 1e-6
-    print({k: tuple(f"{v:.2e}" for v in w) for k, w in worst.items()}, "norm", np.abs(tot - 1).max())
+    assert P[:, 1].max() > 1e-8                          # the field reached the molecules
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.step(5)
+    sim.populations()                                    # drains the stream
+    dt = (time.perf_counter() - t0) / 5
+    print(f"{wl.name}: {dt * 1e3:.1f} ms per coupled step (host clock), "
+          f"{wl.n_molecules / dt:.3e} molecule-steps/s, {wl.cells / dt:.3e} cell-updates/s")
+    sim.close()
+    del sim
+    _release()
 
 
 def test_nanohole_700k_molecules_mixed(B):
     wl = W.config2()
     _need(2 * _state_bytes(wl) + 8e9)          # state + streaming scratch + grid
-    sim = B.Simulation(wl, precision=B.MS_PREC_MIXED_F16X3)
-    _inject(B, sim, wl)
     sample = np.sort(np.random.default_rng(21).choice(wl.n_molecules, 8, replace=False))
-    nsteps = 12
-    rec = sim.record_local_fields(sample, nsteps)
-    _check_sample(wl, sim, sample, rec, nsteps)
-    _time_steps(sim, wl)
-    sim.close()
+    _molecules_prescribed(B, wl, B.MS_PREC_MIXED_F16X3, sample)
+    E = _seeded_field(wl)
+    _coupled_properties(B, wl, E, 8, precision=B.MS_PREC_MIXED_F16X3)
+    _fields_vs_oracle(B, wl, E)
 
 
 def test_splitring_three_species_400k(B):
@@ -128,29 +168,22 @@ def test_splitring_three_species_400k(B):
     scheduling), one per species."""
     wl = W.config3()
     _need(2 * _state_bytes(wl) + 12e9)
-    sim = B.Simulation(wl, autotune=B.MS_TUNE_MEASURE)
-    print("tuned plans", [sim.plan(s) for s in range(3)])
-    _inject(B, sim, wl)
     rng = np.random.default_rng(22)
     sample = np.sort(np.concatenate([rng.choice(np.nonzero(wl.species_id == s)[0], 3, replace=False)
                                      for s in range(3)]))
-    nsteps = 8
-    rec = sim.record_local_fields(sample, nsteps)
-    _check_sample(wl, sim, sample, rec, nsteps)
-    _time_steps(sim, wl)
-    sim.close()
+    _molecules_prescribed(B, wl, B.MS_PREC_FP32, sample, nsteps=8)
+    E = _seeded_field(wl)
+    _coupled_properties(B, wl, E, 8, autotune=B.MS_TUNE_MEASURE)
+    _fields_vs_oracle(B, wl, E)
 
 
 def test_sixteen_nanohole_cells_in_one_launch(B):
     wl = W.config4()
     _need(2 * _state_bytes(wl) + 4e9)
-    sim = B.Simulation(wl)
-    _inject(B, sim, wl)
     rng = np.random.default_rng(23)
     sample = np.sort(np.concatenate([rng.choice(np.nonzero(wl.sim_id == s)[0], 2, replace=False)
                                      for s in (0, 5, 10, 15)]))
-    nsteps = 20
-    rec = sim.record_local_fields(sample, nsteps)
-    _check_sample(wl, sim, sample, rec, nsteps)
-    _time_steps(sim, wl)
-    sim.close()
+    _molecules_prescribed(B, wl, B.MS_PREC_FP32, sample, nsteps=20)
+    E = _seeded_field(wl)
+    _coupled_properties(B, wl, E, 20)
+    _fields_vs_oracle(B, wl, E)
