@@ -522,11 +522,13 @@ def main():
                 "roofline_fdtd": roof_fdtd,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
                 "clocks": cl, "norm_bookkeeping_max_err": norm_err,
-                "error_vs_fp64": ("this workload at full size, coupled to step 6,046 (the pulse peak): populations "
-                                  "1.7e-6 abs, dipoles 2e-6 rel against the FP64 oracle fed the recorded local "
-                                  "fields of 8 molecules; fields rel L2 <= 1e-4 on the full grid "
-                                  "(tests/test_gpu_parity.py, test_splitring_coupled_pulse_peak_sampled, "
-                                  "test_splitring_full_grid_fields)"),
+                "error_vs_fp64": ("this workload's molecules at full size held to the FP64 oracle on a seeded sample "
+                                  "under prescribed drives (populations 1e-5 abs, P_e 1e-3 rel, dipoles 1e-4 rel; "
+                                  "test_splitring_full_size_molecules_sampled, "
+                                  "test_splitring_peak_regime_prescribed_sampled), the full grid's fields within "
+                                  "rel L2 1e-4 (test_splitring_full_grid_fields), and the coupled run to the pulse "
+                                  "peak within 6e-6 of norm bookkeeping for every molecule "
+                                  "(test_splitring_coupled_to_pulse_peak), in tests/test_gpu_parity.py"),
                 "forms": {"plain_fp32": {"value": value, "unit": UNIT, "ms_per_step": ms / a.steps,
                                          "molecular_step_ms": phases[1] / nsteps,
                                          "layout": "fused" if fused else "streaming"}, **other}}
