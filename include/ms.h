@@ -261,16 +261,21 @@ ms_status ms_step(ms_sim* sim, int64_t n);
  * callers that cannot allocate device memory at the point where they step:
  * for instance, code that runs inside a fixed memory arena or under a
  * budget that forbids new device allocations.
- *   - Limit: every streaming species' scratch, n_molecules * 2 (jmax+1)^2 *
- *     nr * 8 bytes, must fit in 64 MiB; otherwise MS_EINVAL is returned
- *     before anything is launched.
+ *   - Limit: each streaming species takes its own region of the array,
+ *     n_molecules * 2 (jmax+1)^2 * nr * 8 bytes rounded up to 256 bytes
+ *     (half the rows for MS_STATE_PARITY), and the regions of all of a
+ *     handle's streaming species together must fit in 64 MiB; otherwise
+ *     MS_EINVAL is returned before anything is launched.
  *   - The array is shared by every call and every handle in the process, on
  *     each device; it keeps the last call's contents, and each step rewrites
  *     the part it reads before reading it.  Calls whose work overlaps on the
  *     GPU (different streams or threads) race on it: serialise them.
  *   - Every GPU that loads the library holds the 64 MiB until the process
- *     exits.  The first call on a device looks the array's address up (with
- *     that device current); make that first call before any stream capture.
+ *     exits.  ms_create looks the array's address up with the handle's
+ *     device current (this may load the library's device code on that device
+ *     and so take the 64 MiB then); if that lookup fails, ms_step_noalloc
+ *     returns MS_ECUDA.  Stepping a handle with ms_step and ms_step_noalloc
+ *     in any order gives the same results.
  * Errors as for ms_step. */
 ms_status ms_step_noalloc(ms_sim* sim, int64_t n);
 
@@ -367,7 +372,8 @@ ms_status ms_read_dft(ms_sim* sim, int32_t plane, int32_t sim_index, int32_t com
  *   - the Drude current;
  *   - the CPML auxiliaries and the incident line;
  *   - every species' wavepackets (Bloch vectors for frozen molecules);
- *   - the molecules' dipoles, populations and absorbed norm;
+ *   - the molecules' dipoles, populations, absorbed norm and rounding
+ *     feedback factors;
  *   - the detectors' running Fourier transforms (when set);
  *   - the step counter.
  * The inputs (geometry, materials, molecules, drive samples) are not saved.

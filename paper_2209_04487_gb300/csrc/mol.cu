@@ -19,8 +19,12 @@
 // d1 = (V - 1) u + V^{1/2} S with S = sum_{n>=1} (i theta sigma_x M)^n/n!
 // V^{1/2} u (Taylor series of the coupling exponential, |theta M| << 1), and
 // s' = s + (d2 + d1): the full-magnitude state is rounded once per step,
-// which keeps the FP32 norm error a random walk of about 1e-8 per step
-// instead of a drift.  The coupling is evaluated in the frame turned about
+// which turns the FP32 norm error from a drift into a random walk of about
+// 1e-8 per step.  That one rounding's exact residual (TwoSum) gives the norm
+// it changed; the next step scales its update by the factor that returns it
+// (round_update), so the walk of the final roundings does not accumulate:
+// what remains is one step's rounding plus the much smaller rounding inside
+// the correction.  The coupling is evaluated in the frame turned about
 // z that puts E' in the xz plane (a diagonal phase on the correction only),
 // where M is real.
 #include <cuda.h>
@@ -388,6 +392,29 @@ __device__ __forceinline__ void acc2(float& hi, float& lo, float x) {
   hi = t;
 }
 
+// The state's one full-magnitude rounding per step, s' = fl(s + D'), with the
+// update D' = D + c s scaled by the previous step's rounding feedback c, and
+// the exact residual e = (s + D') - s' of that rounding (TwoSum; the FP32
+// operations must stay unfused and unreordered) folded into acc as
+// Re(conj(s') e).  The rounding changed sum |s|^2 by -2 sum Re(conj(s') e) to
+// first order; the next step's c = sum Re(conj(s') e) / sum |s'|^2 gives that
+// back, so the norm carries one step's rounding instead of a random walk.
+__device__ __forceinline__ float2 round_update(float2 sv, float2 D, float c, float& acc) {
+  const float dx = fmaf(c, sv.x, D.x), dy = fmaf(c, sv.y, D.y);
+  const float nx = __fadd_rn(sv.x, dx), ny = __fadd_rn(sv.y, dy);
+  const float bx = __fsub_rn(nx, sv.x), by = __fsub_rn(ny, sv.y);
+  const float ex = __fadd_rn(__fsub_rn(sv.x, __fsub_rn(nx, bx)), __fsub_rn(dx, bx));
+  const float ey = __fadd_rn(__fsub_rn(sv.y, __fsub_rn(ny, by)), __fsub_rn(dy, by));
+  acc = fmaf(nx, ex, fmaf(ny, ey, acc));
+  return make_float2(nx, ny);
+}
+
+// feedback factor for the next step from the summed residual products and the
+// summed |s'|^2 of a molecule (0 for an empty state)
+__device__ __forceinline__ float rounding_feedback(float res, float norm2) {
+  return norm2 > 0.f && isfinite(res) ? res / norm2 : 0.f;
+}
+
 // FUSED: the whole state is staged in shared memory and the kinetic pass runs
 // in this kernel.  Otherwise (streaming form) d2 = (T - 1) s comes from the
 // scratch written by mol_kinetic_kernel and is streamed chunk by chunk with s.
@@ -422,8 +449,8 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
   __shared__ float2 s_ph[2 * kMaxJ + 1];                 // e^{+i m phi_E}
   __shared__ float s_fld[2];                             // E_perp, E'_z (a.u.)
   __shared__ int s_nterms;
-  __shared__ float2 s_red[NW][7];
-  __shared__ float s_fin[7], s_fin_lo[7];
+  __shared__ float2 s_red[NW][8];
+  __shared__ float s_fin[8], s_fin_lo[8];
 
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int LPR = 32 / CH;                       // row groups per warp
@@ -511,7 +538,9 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
   // ---- R-space pass, CH radial points at a time; thread rows row0 + i*rstep
   const int nterms = s_nterms;
   const float theta = (float)sp.theta;
+  const float cfix = md.ncorr[m];  // rounding feedback of the previous step
   float a_hi[7] = {0, 0, 0, 0, 0, 0, 0}, a_lo[7] = {0, 0, 0, 0, 0, 0, 0};
+  float rnd = 0.f;
   const int nchunks = NR / CH;
   for (int ck = 0; ck < nchunks; ++ck) {
     const int r0 = ck * CH, r = r0 + rl, b = ck & 1;
@@ -572,7 +601,7 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
       in = out;
       out = tmp;
     }
-    // d1 = (V - 1) u + V^{1/2} D S_r ; mask ; s' = s + (d2 + d1)
+    // d1 = (V - 1) u + V^{1/2} D S_r ; mask ; s' = s + (d2 + d1) + cfix s
     const float mk = bM[rl].x;
     float sg = 0.f, se = 0.f, agf = 0.f, aef = 0.f;
 #pragma unroll
@@ -596,7 +625,7 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
           const float dd = fmaf(px, px, py * py) - fmaf(qx, qx, qy * qy);
           if (sf == 0) agf += dd; else aef += dd;
         }
-        const float2 sn = sv + (d2 + d1);
+        const float2 sn = round_update(sv, d2 + d1, cfix, rnd);
         gs[(long long)row * NR + r] = sn;
         bY[row * CH + rl] = sn;
         const float b2 = fmaf(sn.x, sn.x, sn.y * sn.y);
@@ -640,8 +669,8 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
   // ---- block reduction (compensated FP32; FP64 only for the final sums)
   {
 #pragma unroll
-    for (int q = 0; q < 7; ++q) {
-      float hi = a_hi[q], lo = a_lo[q];
+    for (int q = 0; q < 8; ++q) {
+      float hi = q < 7 ? a_hi[q] : rnd, lo = q < 7 ? a_lo[q] : 0.f;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
@@ -652,7 +681,7 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
       if (lane == 0) s_red[w][q] = make_float2(hi, lo);
     }
     __syncthreads();
-    if (t < 7) {  // one quantity per thread, compensated over the warps
+    if (t < 8) {  // one quantity per thread, compensated over the warps
       float hi = 0.f, lo = 0.f;
       for (int ww = 0; ww < NW; ++ww) {
         acc2(hi, lo, s_red[ww][t].x);
@@ -675,6 +704,8 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
     } else if (t < 7) {  // absorbed norm, cumulative
       md.absorbed[2 * (long long)m + (t - 5)] =
           s_abs[t - 5] + ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
+    } else if (t == 7) {  // rounding feedback for the next step
+      md.ncorr[m] = rounding_feedback(s_fin[7], s_fin[0] + s_fin[1]);
     }
   }
 }
@@ -810,8 +841,8 @@ __global__ void __launch_bounds__(RsDims<J>::NT, RsDims<J>::MINB)
   __shared__ float2 s_ph[2 * kMaxJ + 1];
   __shared__ float s_fld[2];
   __shared__ int s_nterms;
-  __shared__ float s_red[NW][9];
-  __shared__ float s_fin[7], s_fin_lo[2];
+  __shared__ float s_red[NW][10];
+  __shared__ float s_fin[8], s_fin_lo[2];
 
   const int NR = sp.nr;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -883,7 +914,8 @@ __global__ void __launch_bounds__(RsDims<J>::NT, RsDims<J>::MINB)
   const int nchunks = NR / kTile;  // even: NR is 64, 128 or 256
   float2 sv[RPW], dv[RPW], sacc[RPW];
   float p_hi[2] = {0.f, 0.f}, p_lo[2] = {0.f, 0.f};  // populations, compensated
-  float a_gf = 0.f, a_ef = 0.f, dP = 0.f, dQ = 0.f, dZ = 0.f;
+  float a_gf = 0.f, a_ef = 0.f, dP = 0.f, dQ = 0.f, dZ = 0.f, rnd = 0.f;
+  const float cfix = md.ncorr[m];  // rounding feedback of the previous step
   // ground rows: q = w + NW i < NROT
   auto ground = [&](int i) { return NW * i + NW <= NROT || (NW * i < NROT && w < NROT - NW * i); };
 
@@ -947,7 +979,7 @@ __global__ void __launch_bounds__(RsDims<J>::NT, RsDims<J>::MINB)
       term(std::integral_constant<int, 0>(), n);
       if (n + 1 <= nterms) term(std::integral_constant<int, 1>(), n + 1);
     }
-    // ---- d1 = (V - 1) u + V^{1/2} e^{-i m phi} S ; mask ; s' = s + (d2 + d1)
+    // ---- d1 = (V - 1) u + V^{1/2} e^{-i m phi} S ; mask ; s' = s + (d2 + d1) + cfix s
     const int sbo = (nterms & 1) * TBB;  // s' buffer: not read by the last term
     float2* gsw = gs + (long long)w * NR + ck * kTile + lane;
     float sg = 0.f, se = 0.f;
@@ -969,7 +1001,7 @@ __global__ void __launch_bounds__(RsDims<J>::NT, RsDims<J>::MINB)
         const float dd = (1.f - mk * mk) * fmaf(px, px, py * py);
         if (gr) a_gf += dd; else a_ef += dd;
       }
-      const float2 sn = sv[i] + (dv[i] + d1);
+      const float2 sn = round_update(sv[i], dv[i] + d1, cfix, rnd);
       gsw[(long long)(NW * i) * NR] = sn;
       sts2<D::O_TB + G0>(sm, own + sbo + NW * i * kSeg, sn);
       sv[i] = sn;
@@ -1013,7 +1045,7 @@ __global__ void __launch_bounds__(RsDims<J>::NT, RsDims<J>::MINB)
   }
   // ---- block reduction: populations compensated, the rest plain FP32
   {
-    float v[7] = {p_hi[0], p_hi[1], a_gf, a_ef, dP, dQ, dZ};
+    float v[8] = {p_hi[0], p_hi[1], a_gf, a_ef, dP, dQ, dZ, rnd};
     float lo[2] = {p_lo[0], p_lo[1]};
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1025,19 +1057,20 @@ __global__ void __launch_bounds__(RsDims<J>::NT, RsDims<J>::MINB)
         lo[k] += l2;
       }
 #pragma unroll
-      for (int k = 2; k < 7; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+      for (int k = 2; k < 8; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     }
     if (lane == 0) {
 #pragma unroll
       for (int k = 0; k < 7; ++k) s_red[w][k] = v[k];
       s_red[w][7] = lo[0];
       s_red[w][8] = lo[1];
+      s_red[w][9] = v[7];
     }
     __syncthreads();
-    if (t < 7) {
+    if (t < 8) {
       float hi = 0.f, l = 0.f;
       for (int ww = 0; ww < NW; ++ww) {
-        acc2(hi, l, s_red[ww][t]);
+        acc2(hi, l, s_red[ww][t < 7 ? t : 9]);
         if (t < 2) l += s_red[ww][7 + t];
       }
       s_fin[t] = hi + l;
@@ -1056,6 +1089,8 @@ __global__ void __launch_bounds__(RsDims<J>::NT, RsDims<J>::MINB)
       if (!isfinite(P)) atomicOr(err, kErrNonFinite);
     } else if (t < 7) {
       md.absorbed[2 * (long long)m + (t - 5)] = s_abs[t - 5] + (double)s_fin[t - 3] * (double)sp.dR;
+    } else if (t == 7) {
+      md.ncorr[m] = rounding_feedback(s_fin[7], s_fin[0] + s_fin[1]);
     }
   }
 }
@@ -1271,8 +1306,8 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
   __shared__ __align__(8) unsigned long long s_bar[2];
   __shared__ float s_rot[9];
   __shared__ double s_mu[3], s_abs[2];
-  __shared__ float s_red[NW][9];
-  __shared__ float s_fin[7], s_fin_lo[2];
+  __shared__ float s_red[NW][10];
+  __shared__ float s_fin[8], s_fin_lo[2];
 
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int sf = t >= NR, p = t - sf * NR;  // surface (warp-uniform) and radial point
@@ -1321,6 +1356,7 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
   }
   const int nterms = __float_as_int(f.w);
   const float mk = sp.maskw[p].x;
+  const float cfix = md.ncorr[m];  // rounding feedback of the previous step
   float2 vh[J + 1], vd[J + 1];
 #pragma unroll
   for (int j = 0; j <= J; ++j) {
@@ -1388,8 +1424,8 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
     per_surface([&](auto sfc) { term(sfc, cn, store); });
     if (store) __syncthreads();
   }
-  // ---- d1 = (V - 1) u + V^{1/2} S ; mask ; s' = s + (d2 + d1)
-  float sn2 = 0.f, absd = 0.f;
+  // ---- d1 = (V - 1) u + V^{1/2} S ; mask ; s' = s + (d2 + d1) + cfix s
+  float sn2 = 0.f, absd = 0.f, rnd = 0.f;
   auto update = [&](auto sfc) {
     constexpr int SF = decltype(sfc)::value, NO = L::N(SF);
     // s again (from L2), in two batches each requested in full first; d2 from shared memory
@@ -1414,7 +1450,7 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
         d1.y = fmaf(mk - 1.f, u.y, mk * d1.y);
         absd += (1.f - mk * mk) * fmaf(px, px, py * py);
       }
-      const float2 s1 = sv + (dv + d1);
+      const float2 s1 = round_update(sv, dv + d1, cfix, rnd);
       __stcs(gs + r * NR, s1);
       sn2 += fmaf(s1.x, s1.x, s1.y * s1.y);
       sacc[r] = s1;  // the new state of this surface, kept for the dipole
@@ -1441,7 +1477,7 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
   }
   // ---- block reduction: populations compensated, the rest plain FP32
   {
-    float v[7] = {sf ? 0.f : sn2, sf ? sn2 : 0.f, sf ? 0.f : absd, sf ? absd : 0.f, dP, dQ, dZ};
+    float v[8] = {sf ? 0.f : sn2, sf ? sn2 : 0.f, sf ? 0.f : absd, sf ? absd : 0.f, dP, dQ, dZ, rnd};
     float lo[2] = {0.f, 0.f};
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1453,19 +1489,20 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
         lo[k] += l2;
       }
 #pragma unroll
-      for (int k = 2; k < 7; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+      for (int k = 2; k < 8; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
     }
     if (lane == 0) {
 #pragma unroll
       for (int k = 0; k < 7; ++k) s_red[w][k] = v[k];
       s_red[w][7] = lo[0];
       s_red[w][8] = lo[1];
+      s_red[w][9] = v[7];
     }
     __syncthreads();
-    if (t < 7) {
+    if (t < 8) {
       float hi = 0.f, l = 0.f;
       for (int ww = 0; ww < NW; ++ww) {
-        acc2(hi, l, s_red[ww][t]);
+        acc2(hi, l, s_red[ww][t < 7 ? t : 9]);
         if (t < 2) l += s_red[ww][7 + t];
       }
       s_fin[t] = hi + l;
@@ -1486,6 +1523,8 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
       if (!isfinite(P)) atomicOr(err, kErrNonFinite);
     } else if (t < 7) {
       md.absorbed[2 * (long long)m + (t - 5)] = s_abs[t - 5] + (double)s_fin[t - 3] * (double)sp.dR;
+    } else if (t == 7) {
+      md.ncorr[m] = rounding_feedback(s_fin[7], s_fin[0] + s_fin[1]);
     }
   }
 }

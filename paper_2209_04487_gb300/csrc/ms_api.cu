@@ -79,6 +79,10 @@ struct ms_sim {
   ms::SpeciesDev sp[ms::kMaxSpecies]{};
   int* d_err = nullptr;
   long long* d_step = nullptr;
+  // device address of the library's fixed scratch array (ms_step_noalloc),
+  // looked up at create with the handle's device current; null if that failed
+  float2* noalloc_base = nullptr;
+  std::vector<double> pop_init;  // create only: populations at t = 0, uploaded in one copy
   // phase timing
   bool timing = false;
   std::vector<cudaEvent_t> events;   // 4 per timed step
@@ -321,14 +325,14 @@ std::vector<uint16_t> mixed_kinetic_planes(int nr, double dR, double dtau, doubl
   return out;
 }
 
-// P_g, P_e of one species' molecules at t = 0 into the shared population array
+// P_g, P_e of one species' molecules at t = 0, into the host copy of the
+// population array that create uploads once every species is built
 ms_status initial_populations(ms_sim* s, const std::vector<int>& ids, double pg) {
-  const double p[2] = {pg, 0.0};
-  for (size_t q = 0; q < ids.size(); ++q)
-    if (cudaMemcpyAsync(s->md.pop + 2 * (size_t)ids[q], p, 2 * sizeof(double), cudaMemcpyHostToDevice,
-                        s->stream) != cudaSuccess)
-      return MS_ECUDA;
-  return cudaStreamSynchronize(s->stream) == cudaSuccess ? MS_OK : MS_ECUDA;
+  for (size_t q = 0; q < ids.size(); ++q) {
+    s->pop_init[2 * (size_t)ids[q]] = pg;
+    s->pop_init[2 * (size_t)ids[q] + 1] = 0.0;
+  }
+  return MS_OK;
 }
 
 // Frozen two-level species (MS_MODEL_BLOCH): rates in atomic units, Bloch
@@ -537,11 +541,13 @@ ms_status tune_species(ms_sim* s, int si) {
   int* mol = (int*)sc.get((size_t)nt * sizeof(int));
   float* rot = (float*)sc.get((size_t)nt * 9 * sizeof(float));
   double* dbl = (double*)sc.get((size_t)nt * 14 * sizeof(double));  // mu, dmu, pop, absorbed, Rnum, Rden
+  float* ncorr = (float*)sc.get((size_t)nt * sizeof(float));
   float* amp = (float*)sc.get((size_t)nt * 3 * sizeof(float));
   float* wave = (float*)sc.get(sizeof(float));
   long long* step = (long long*)sc.get(sizeof(long long));
   int* err = (int*)sc.get(sizeof(int));
-  if (!t.psi || !t.d2 || !t.fld || !mol || !rot || !dbl || !amp || !wave || !step || !err) return MS_ENOMEM;
+  if (!t.psi || !t.d2 || !t.fld || !mol || !rot || !dbl || !ncorr || !amp || !wave || !step || !err)
+    return MS_ENOMEM;
   // the first nt molecules of the species: state and rotations
   std::vector<int> ids(nt);
   if (cudaMemcpy(ids.data(), sp.mol, nt * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MS_ECUDA;
@@ -577,6 +583,7 @@ ms_status tune_species(ms_sim* s, int si) {
       cudaMemcpyAsync(wave, &one, sizeof(float), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
       cudaMemcpyAsync(step, &zero, sizeof(long long), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
       cudaMemsetAsync(dbl, 0, (size_t)nt * 14 * sizeof(double), s->stream) != cudaSuccess ||
+      cudaMemsetAsync(ncorr, 0, (size_t)nt * sizeof(float), s->stream) != cudaSuccess ||
       cudaMemsetAsync(err, 0, sizeof(int), s->stream) != cudaSuccess ||
       cudaStreamSynchronize(s->stream) != cudaSuccess)
     return MS_ECUDA;
@@ -590,6 +597,7 @@ ms_status tune_species(ms_sim* s, int si) {
   m.absorbed = dbl + 8 * (size_t)nt;
   m.Rnum = dbl + 10 * (size_t)nt;
   m.Rden = dbl + 11 * (size_t)nt;
+  m.ncorr = ncorr;
   m.amp = amp;
   m.wave = wave;
   m.nwave = 1;
@@ -792,6 +800,7 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
   MS_TRY(zeros(s, &md.absorbed, 2 * nn1));
   MS_TRY(zeros(s, &md.Rnum, nn1));
   MS_TRY(zeros(s, &md.Rden, nn1));
+  MS_TRY(zeros(s, &md.ncorr, nn1));
   g.dmu = md.dmu;
   if (s->drive == MS_DRIVE_FDTD && n > 0) {
     // CSR over the molecule slab: cells sorted, molecules of a cell in id order
@@ -812,6 +821,7 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
     MS_TRY(upload(s, (int**)&g.cell_mol, lst.data(), lst.size()));
   }
   // species
+  s->pop_init.assign(2 * nn1, 0.0);
   for (int si = 0; si < s->nspecies; ++si) {
     std::vector<int> ids;
     for (long long q = 0; q < n; ++q)
@@ -819,7 +829,11 @@ ms_status create_impl(const ms_grid_desc* G, const ms_materials_desc* M, const m
     MS_TRY(build_species(s, si, D->species[si], dt * s->nsub, ids, O ? O->mol_path : MS_MOL_AUTO,
                          O && O->precision == MS_PREC_MIXED_F16X3, O && O->state_form == MS_STATE_PARITY));
   }
-  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
+  if (cudaMemcpyAsync(md.pop, s->pop_init.data(), s->pop_init.size() * sizeof(double), cudaMemcpyHostToDevice,
+                      s->stream) != cudaSuccess ||
+      cudaStreamSynchronize(s->stream) != cudaSuccess)
+    return MS_ECUDA;
+  std::vector<double>().swap(s->pop_init);
   if (O && O->autotune == MS_TUNE_MEASURE)
     for (int si = 0; si < s->nspecies; ++si) MS_TRY(tune_species(s, si));
   return MS_OK;
@@ -918,10 +932,11 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
 
 // ---- allocation-free stepping --------------------------------------------
 // A fixed device array compiled into the library stands in for the per-
-// species (T - 1)s scratch of the streaming form.  Every GPU that loads the
-// library holds it until the process exits.  In host code `g_noalloc_scratch`
-// is only a stand-in symbol: its device address is looked up once per device
-// (with that device current) and passed to the kernels.
+// species (T - 1)s scratch of the streaming form, one disjoint region per
+// streaming species.  Every GPU that loads the library holds it until the
+// process exits.  In host code `g_noalloc_scratch` is only a stand-in symbol:
+// its device address is looked up once per device (with that device current,
+// from ms_create) and passed to the kernels.
 namespace {
 constexpr size_t kNoAllocScratchBytes = 64ull << 20;  // 64 MiB
 static __device__ __align__(256) float2 g_noalloc_scratch[kNoAllocScratchBytes / sizeof(float2)];
@@ -993,6 +1008,9 @@ ms_status ms_create(const ms_grid_desc* grid, const ms_materials_desc* materials
     s->own_stream = true;
   }
   const ms_status st = create_impl(grid, materials, molecules, opts, s);
+  // the fixed scratch of ms_step_noalloc, looked up now so that the stepping
+  // call only reads the pointer; a failure here only disables that call
+  if (st == MS_OK && noalloc_scratch(&s->noalloc_base) != MS_OK) s->noalloc_base = nullptr;
   if (st != MS_OK) {
     cudaGetLastError();
     s->release();
@@ -1023,14 +1041,15 @@ static cudaEvent_t mark(ms_sim* s) {
 
 // One coupled step: H half step, the molecules (stage 1: field records and
 // kinetic pass; stage 2: R-space pass, for every species), E half step.
-// `scratch`, when set, replaces the streaming species' d2 buffers.
+// `scratch`, when set, gives each streaming species a d2 buffer that replaces
+// its own (scratch[si], one disjoint region per species).
 struct FieldRecorder {  // ms_record_local_fields: E^n of listed molecules, one row per step
   const long long* ids;
   int m;
   float* out;  // [steps][m][3], advanced by the caller
 };
 
-static void step_once(ms_sim* s, float2* scratch, const FieldRecorder* rec = nullptr) {
+static void step_once(ms_sim* s, float2* const* scratch, const FieldRecorder* rec = nullptr) {
   const bool fdtd = s->drive == MS_DRIVE_FDTD;
   // sub-stepping: the molecules advance (by nsub dt) on every nsub-th step only,
   // and only those steps' E updates take the molecular dipole change
@@ -1049,7 +1068,7 @@ static void step_once(ms_sim* s, float2* scratch, const FieldRecorder* rec = nul
   ms::SpeciesDev sp[ms::kMaxSpecies];
   for (int si = 0; si < s->nspecies; ++si) {
     sp[si] = s->sp[si];
-    if (scratch && sp[si].path == MS_MOL_STREAMING) sp[si].d2 = scratch;  // rewritten before it is read
+    if (scratch && sp[si].path == MS_MOL_STREAMING) sp[si].d2 = scratch[si];  // rewritten before it is read
   }
   if (molecular)
     for (int si = 0; si < s->nspecies; ++si)
@@ -1132,15 +1151,19 @@ ms_status ms_step(ms_sim* s, int64_t n) {
 ms_status ms_step_noalloc(ms_sim* s, int64_t n) {
   if (!s || n < 0) return MS_EINVAL;
   if (s->drive == MS_DRIVE_PRESCRIBED && s->nmol > 0 && s->steps + n > s->nwave) return MS_EINVAL;
-  // every streaming species must fit the fixed scratch (checked before any launch)
+  // each streaming species gets its own region of the fixed array, at
+  // 256-byte aligned offsets; all of them must fit (checked before any launch)
+  float2* scratch[ms::kMaxSpecies] = {};
+  size_t off = 0;
   for (int si = 0; si < s->nspecies; ++si) {
     const ms::SpeciesDev& sp = s->sp[si];
-    if (sp.path == MS_MOL_STREAMING &&
-        (size_t)sp.nmol * sp.rows * sp.nr * sizeof(float2) > kNoAllocScratchBytes)
-      return MS_EINVAL;
+    if (sp.path != MS_MOL_STREAMING || sp.bloch || sp.nmol == 0) continue;
+    const size_t bytes = (size_t)sp.nmol * sp.rows * sp.nr * sizeof(float2);
+    if (bytes > kNoAllocScratchBytes || off > kNoAllocScratchBytes - bytes) return MS_EINVAL;
+    scratch[si] = s->noalloc_base + off / sizeof(float2);
+    off += (bytes + 255) / 256 * 256;
   }
-  float2* scratch = nullptr;
-  MS_TRY(noalloc_scratch(&scratch));
+  if (!s->noalloc_base) return MS_ECUDA;
   for (int64_t q = 0; q < n; ++q) step_once(s, scratch);
   return cudaGetLastError() == cudaSuccess ? MS_OK : MS_ECUDA;
 }
@@ -1387,7 +1410,7 @@ ms_status ms_read_flux(ms_sim* s, int32_t plane, double* flux) {
 // ---- checkpoint ------------------------------------------------------------
 namespace {
 constexpr char kCkMagic[8] = {'M', 'S', '2', '2', '0', '9', 'C', 'K'};
-constexpr uint32_t kCkVersion = 3;
+constexpr uint32_t kCkVersion = 4;
 
 struct CkHeader {
   char magic[8];
@@ -1441,6 +1464,7 @@ std::vector<Blob> state_blobs(ms_sim* s) {
     b.push_back({s->md.dmu, 3 * n * sizeof(double)});
     b.push_back({s->md.pop, 2 * n * sizeof(double)});
     b.push_back({s->md.absorbed, 2 * n * sizeof(double)});
+    b.push_back({s->md.ncorr, n * sizeof(float)});
   }
   return b;
 }

@@ -151,6 +151,12 @@ struct MolDev {
   double* absorbed;         // [n][2] cumulative absorbed norm
   double* Rnum;             // [n] Eq. 8 numerator (filled on readout)
   double* Rden;             // [n]
+  // [n] rounding feedback of the wavepacket state: the relative norm change
+  // sum(s'.e) / sum|s'|^2 that the last step's final FP32 rounding s' =
+  // fl(s + D) introduced (e its exact TwoSum residual); the next step scales
+  // its update by (1 + ncorr), which returns that norm, so rounding no longer
+  // walks the norm.  Arithmetic error inside D is not compensated.
+  float* ncorr;
   // prescribed drive
   const float* amp;         // [n][3]
   const float* wave;        // [nwave]

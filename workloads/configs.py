@@ -268,25 +268,29 @@ def config0(n_molecules: int = 1000, jmax: int = 1, nsteps: int = 2000) -> Workl
 
 
 def config1(n_molecules: int = 50000, nsteps: int = 10000, nx: int = 128, ny: int = 128,
-            nz: int = 192) -> Workload:
+            nz: int = 192, t0: float = 20e-15) -> Workload:
     """Split-ring array 128x128x192: silver ring z 50..64, glass z >= 65,
-    50,000 molecules in a 20 nm layer z 40..49, Nr 128, J <= 4."""
+    50,000 molecules in a 20 nm layer z 40..49, Nr 128, J <= 4.  t0: time of
+    the pulse peak at the source plane (20 fs; shorter runs that must see the
+    peak pass the layer give an earlier one)."""
     sp = Species(nr=128, jmax=4)
     return custom(f"config1: SRR {nx}x{ny}x{nz}, {n_molecules} molecules (Nr 128, J<=4)",
                   nx, ny, nz, src_k=20,
-                  pulses=[_pulse_row(1e9, 1.5498, 10e-15, 20e-15)],
+                  pulses=[_pulse_row(1e9, 1.5498, 10e-15, t0)],
                   geometry=_srr_geometry, layer=(40, 50), n_per_sim=n_molecules,
                   species=[sp], seed=1, nsteps=nsteps)
 
 
-def config2(n_molecules: int = 700000, nsteps: int = 2000, n: int = 256) -> Workload:
+def config2(n_molecules: int = 700000, nsteps: int = 2000, n: int = 256,
+            t0: float = 20e-15) -> Workload:
     """Triangular-nanohole array 256^3: 100 nm silver film z 51..100 with a
     side-115-cell (230 nm) equilateral hole, glass z >= 101, molecules on
-    distinct cells of the 11-plane layer z 40..50, Nr 128, J <= 8."""
+    distinct cells of the 11-plane layer z 40..50, Nr 128, J <= 8.  t0: time
+    of the pulse peak at the source plane."""
     sp = Species(nr=128, jmax=8)
     geo = lambda nx, ny, nz: _nanohole_geometry(nx, ny, nz, (51, 101), 101, 115.0)
     return custom(f"config2: nanohole {n}^3, {n_molecules} molecules (Nr 128, J<=8)",
-                  n, n, n, src_k=20, pulses=[_pulse_row(1e9, 1.5498, 10e-15, 20e-15)],
+                  n, n, n, src_k=20, pulses=[_pulse_row(1e9, 1.5498, 10e-15, t0)],
                   geometry=geo, layer=(40, 51), n_per_sim=n_molecules, species=[sp],
                   seed=2, distinct=True, nsteps=nsteps)
 
@@ -297,23 +301,32 @@ def config3_species() -> List[Species]:
             Species(nr=256, jmax=16, mass=14000.0, De=0.2)]
 
 
-def config3(n_molecules: int = 400000, nsteps: int = 200, n: int = 192) -> Workload:
-    """Split-ring geometry on 192^3 with three species mixed 0.5/0.3/0.2."""
+def config3(n_molecules: int = 400000, nsteps: int = 200, n: int = 192,
+            t0: float = 20e-15) -> Workload:
+    """Split-ring geometry on 192^3 with three species mixed 0.5/0.3/0.2.
+    t0: time of the pulse peak at the source plane."""
     return custom(f"config3: SRR {n}^3, {n_molecules} molecules of 3 species", n, n, n,
-                  src_k=20, pulses=[_pulse_row(1e9, 1.5498, 10e-15, 20e-15)],
+                  src_k=20, pulses=[_pulse_row(1e9, 1.5498, 10e-15, t0)],
                   geometry=_srr_geometry, layer=(40, 50), n_per_sim=n_molecules,
                   species=config3_species(), fractions=[0.5, 0.3, 0.2], seed=3,
                   nsteps=nsteps)
 
 
-def config4(n_per_sim: int = 20000, nsteps: int = 50000, nsim: int = 16) -> Workload:
+def config4(n_per_sim: int = 20000, nsteps: int = 50000, nsim: int = 16,
+            carriers: Optional[Sequence[int]] = None, t0: float = 40e-15) -> Workload:
     """16 independent 64x64x128 nanohole cells (42-cell hole, film z 35..84,
     glass >= 85), 20,000 config-0 molecules at J <= 8 per cell in z 30..34,
-    carriers 1.2 + 1.2 i/15 eV, 20 fs FWHM, t0 40 fs, 1e9 V/m."""
+    carriers 1.2 + 1.2 i/15 eV, 20 fs FWHM, t0 40 fs, 1e9 V/m.  carriers:
+    optional subset of the sweep's indices i (0..15), one cell each (nsim is
+    then their number); t0: time of the pulse peak at the source plane."""
     sp = species_config0(jmax=8)
     geo = lambda nx, ny, nz: _nanohole_geometry(nx, ny, nz, (35, 85), 85, 42.0)
-    pulses = [_pulse_row(1e9, 1.2 + 1.2 * i / max(nsim - 1, 1), 20e-15, 40e-15)
-              for i in range(nsim)]
+    if carriers is None:
+        ev = [1.2 + 1.2 * i / max(nsim - 1, 1) for i in range(nsim)]
+    else:
+        ev = [1.2 + 1.2 * i / 15.0 for i in carriers]
+        nsim = len(ev)
+    pulses = [_pulse_row(1e9, e, 20e-15, t0) for e in ev]
     return custom(f"config4: {nsim} x nanohole 64x64x128, {n_per_sim} molecules each",
                   64, 64, 128, nsim=nsim, src_k=18, pulses=pulses, geometry=geo,
                   layer=(30, 35), n_per_sim=n_per_sim, species=[sp], seed=4,
