@@ -458,7 +458,8 @@ def main():
         if one and sp.jmax <= 4:
             kernel, traffic_key = f"mol_rpoint_kernel<{sp.jmax},{sp.nr}>", "mol_rpoint_kernel"
         elif one and sp.jmax <= 8:
-            kernel, traffic_key = f"mol_rspace_kernel<{sp.jmax}>", "mol_rspace_kernel"
+            tile = 16 if sp.jmax >= 5 else 32      # the tiled kernel's static rule
+            kernel, traffic_key = f"mol_rspace_kernel<{sp.jmax},{tile}>", "mol_rspace_kernel"
         else:
             kernel, traffic_key = "R-space passes of every species", None
         note = ("algorithmic bytes of the R-space pass: state and d2 = (T - 1)s read, new state written, 168 B of "

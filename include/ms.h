@@ -103,11 +103,13 @@ enum { MS_GRAPHS_AUTO = 0, MS_GRAPHS_OFF = 1 };
 /* A species' plan: its layout (MS_MOL_FUSED or MS_MOL_STREAMING) and the
  * kernel of its R-space pass.  MS_KERN_POINT: one CTA of 2 N_r threads per
  * molecule, thread = (radial point, surface) (J <= 4; fused at N_r 128).
- * MS_KERN_TILE: one CTA per molecule over 32-point tiles of all rows, staged
- * by tensor copies (J <= 8, streaming).  MS_KERN_CHUNK: one CTA per molecule
- * over chunks of `chunk` radial points (4, 8, 16 or 32) of all rows (any J).
- * MS_KERN_DEFAULT: the static rule (the first that applies of point, tile,
- * chunk at the widest fitting chunk).  Parity-reduced and d(R) species run
+ * MS_KERN_TILE: persistent CTAs that each walk a share of the molecules, one
+ * molecule at a time over tiles of `chunk` = 32 or 16 radial points of all
+ * rows, staged by tensor copies (J <= 8, streaming; chunk 0: 16 from J = 5 on,
+ * else 32).  MS_KERN_CHUNK: one CTA per molecule over chunks of `chunk`
+ * radial points (4, 8, 16 or 32) of all rows (any J).  MS_KERN_DEFAULT: the
+ * static rule (the first that applies of point, tile, chunk at the widest
+ * fitting chunk).  Parity-reduced and d(R) species run
  * the point-resident kernel only.  Every plan computes the same step; their
  * results differ by FP32 rounding.
  * Autotuning (ms_options.autotune = MS_TUNE_MEASURE): ms_create times every

@@ -712,12 +712,12 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
 
 
 // ----------------------------------------------------------------------------
-// R-space pass of the streaming form, one CTA per molecule, 32 radial points
-// per chunk (one per lane).  The rows (surface, channel) are spread over the
-// warps, RPW per warp: warp w owns rows w, w + NW, w + 2 NW, ...  The state s
-// and d2 = (T - 1) s of a chunk arrive by bulk copies (one 256-byte row
-// segment each) and stay in registers; the coupling series exchanges values
-// between rows through two term buffers in shared memory.
+// R-space pass of the streaming form, tiled: one CTA per molecule at a time,
+// TILE = 32 or 16 radial points per tile, every row of the state.  The rows
+// (surface, channel) are spread over the warps and stay in registers for a
+// tile: s and d2 = (T - 1) s arrive by 2-D tensor copies and the coupling
+// series exchanges values between rows through two term buffers in shared
+// memory.
 //
 // Neighbour structure: the angular couplings of channel (j, m) reach the
 // channels (j + 1, m - 1 .. m + 1) and (j - 1, m - 1 .. m + 1), two runs of
@@ -745,25 +745,25 @@ cudaError_t upload_triplet_tables(const CouplEntry* dip) {
   return cudaMemcpyToSymbol(g_tri_dn, dn.data(), sizeof(float4) * kMaxRot);
 }
 
-constexpr int kTile = 32;     // radial points per chunk
-constexpr int kSeg = kTile * (int)sizeof(float2);  // bytes of one row segment
 constexpr int kTriGuard = 3;  // zero rows ahead of each term buffer
 
-// Tensor maps of one species for the R-space kernel: 8-byte elements (one
-// complex FP32 value), boxes of kTile radial points by all rows of a block.
+// Tensor maps of one species for the tiled R-space kernel: 8-byte elements
+// (one complex FP32 value), boxes of TILE radial points by all rows of a
+// molecule.
 struct RspaceMaps {
-  CUtensorMap s, d2;  // [n_mol * rows][nr], box kTile x rows
-  CUtensorMap vd, vh; // [2 (J + 1)][nr], box kTile x 2 (J + 1)
-  CUtensorMap mk;     // [1][nr], box kTile x 1
+  CUtensorMap s, d2;  // [n_mol * rows][nr], box TILE x rows
+  CUtensorMap vd, vh; // [2 (J + 1)][nr], box TILE x 2 (J + 1)
+  CUtensorMap mk;     // [1][nr], box TILE x 1
 };
 
+// One row of the tiled kernel's row table (built per molecule).
 struct RowT {
   float4 cu, cd;  // theta x coupling on the runs (j + 1, .) and (j - 1, .)
   float4 du, dd;  // dipole coefficients on the runs
-  float2 ph, pad; // e^{i m phi_E}
+  float2 ph;      // e^{i m phi_E}
+  int ou, od;     // byte offsets of the two runs in a term buffer (from its base)
+  int vo, pad;    // byte offset of the row's (surface, j) potential row in a table tile
 };
-constexpr int kRtCu = (int)offsetof(RowT, cu), kRtCd = (int)offsetof(RowT, cd), kRtDu = (int)offsetof(RowT, du),
-              kRtDd = (int)offsetof(RowT, dd), kRtPh = (int)offsetof(RowT, ph);
 
 // Wait for phase `parity`, each try suspending up to hint_ns until the phase
 // completes; gives up after `tries` tries (by default about 2 s in all).
@@ -800,22 +800,32 @@ cudaError_t launch_wait_timeout_probe(int tries, int* flag, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Layout of the R-space kernel for basis size J: NW = 2 (J + 1) warps of
-// RPW = J + 1 rows cover the 2 (J + 1)^2 rows exactly (warp w owns rows
-// w + NW i), so every row index, buffer offset and stride is known at
-// compile time.  Shared memory, from a 128-byte aligned base:
-//   [2 ROWS] s and d2 of the chunk, [2][NV] e^{-iV dtau} - 1, [2][NV]
+// Layout of the tiled R-space kernel for basis size J and tile width TILE
+// (32 or 16 radial points).  A warp covers RPL = 32 / TILE rows of one tile
+// (lane = half * TILE + point, half = lane / TILE), so NW = 2 (J + 1) / RPL
+// warps of RPW = J + 1 row slots cover the 2 (J + 1)^2 rows exactly: warp w
+// owns rows RPL (w + NW i) + half.  Every row index, buffer offset and stride
+// is known at compile time.  A row of a tile is SEG = 8 TILE bytes; the two
+// rows of a 16-point slot are contiguous, so a warp's 32 lanes always read 256
+// contiguous bytes.  Shared memory, from a 128-byte aligned base:
+//   [2 ROWS] s and d2 of the tile, [2][NV] e^{-iV dtau} - 1, [2][NV]
 //   e^{-iV dtau/2} (double buffered), [1] mask, two term buffers of
-//   kTriGuard + ROWS rows, the row table.
-template <int J>
+//   kTriGuard + ROWS rows, the row table of the molecule.
+// With 16-point tiles the J = 8 kernel needs 109 KB, so two CTAs share an SM
+// and one's barriers and copies overlap the other's arithmetic.
+template <int J, int TILE>
 struct RsDims {
   static constexpr int NROT = (J + 1) * (J + 1), ROWS = 2 * NROT, NV = 2 * (J + 1);
-  static constexpr int NW = 2 * (J + 1), RPW = J + 1, NT = 32 * NW;
-  static constexpr int TBB = (kTriGuard + ROWS) * kSeg;  // bytes of a term buffer
-  static constexpr int O_STG = 0, O_VD = O_STG + 2 * ROWS * kSeg, O_VH = O_VD + 2 * NV * kSeg;
-  static constexpr int O_MK = O_VH + 2 * NV * kSeg, O_TB = O_MK + kSeg, O_RT = O_TB + 2 * TBB;
+  static constexpr int RPL = 32 / TILE;
+  static constexpr int NW = 2 * (J + 1) / RPL, RPW = J + 1, NT = 32 * NW;
+  static constexpr int SEG = TILE * (int)sizeof(float2);
+  static constexpr int TBB = (kTriGuard + ROWS) * SEG;  // bytes of a term buffer
+  static constexpr int O_STG = 0, O_VD = O_STG + 2 * ROWS * SEG, O_VH = O_VD + 2 * NV * SEG;
+  static constexpr int O_MK = O_VH + 2 * NV * SEG, O_TB = O_MK + SEG, O_RT = O_TB + 2 * TBB;
   static constexpr int BYTES = 128 + O_RT + ROWS * (int)sizeof(RowT);
-  static constexpr int MINB = J <= 4 ? 3 : 1;
+  static constexpr int MINB = TILE == 16 ? 2 : (J <= 4 ? 3 : 1);
+  static_assert(TILE == 16 || TILE == 32, "tile of 16 or 32 radial points");
+  static_assert(2 * (J + 1) % RPL == 0, "rows split evenly over the warps");
 };
 
 template <int OFF>
@@ -827,270 +837,293 @@ __device__ __forceinline__ void sts2(unsigned char* base, int off, float2 v) {
   *reinterpret_cast<float2*>(base + off + OFF) = v;
 }
 
-template <int J>
-__global__ void __launch_bounds__(RsDims<J>::NT, RsDims<J>::MINB)
-    mol_rspace_kernel(SpeciesDev sp, MolDev md, Grid g, int prescribed, int* err,
-                      const __grid_constant__ RspaceMaps maps) {
-  using D = RsDims<J>;
+// Persistent: CTA b runs molecules b, b + gridDim.x, ...; the first tile of
+// its next molecule is requested as soon as the last tile of the current one
+// has left the staging buffer.  The molecule's frame field and term count
+// come from its record (mol_field_kernel).
+template <int J, int TILE>
+__global__ void __launch_bounds__(RsDims<J, TILE>::NT, RsDims<J, TILE>::MINB)
+    mol_rspace_kernel(SpeciesDev sp, MolDev md, int* err, const __grid_constant__ RspaceMaps maps) {
+  using D = RsDims<J, TILE>;
   constexpr int NROT = D::NROT, ROWS = D::ROWS, NV = D::NV, NW = D::NW, RPW = D::RPW, NT = D::NT;
-  constexpr int TBB = D::TBB, G0 = kTriGuard * kSeg;
+  constexpr int RPL = D::RPL, SEG = D::SEG, TBB = D::TBB, G0 = kTriGuard * SEG;
+  constexpr int SLOT = RPL * SEG;                 // bytes of one warp's rows in a tile buffer
   extern __shared__ __align__(128) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long s_bar[1];
   __shared__ float s_rot[9];
   __shared__ double s_mu[3], s_abs[2];
   __shared__ float2 s_ph[2 * kMaxJ + 1];
-  __shared__ float s_fld[2];
-  __shared__ int s_nterms;
   __shared__ float s_red[NW][10];
   __shared__ float s_fin[8], s_fin_lo[2];
 
   const int NR = sp.nr;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int half = lane / TILE, pt = lane % TILE;
   const int pad = (int)((128u - (smem_u32(smem_raw) & 127u)) & 127u);
   unsigned char* const sm = smem_raw;
-  // this thread's byte offsets: own rows (w + NW i) at lane, and the row table
-  const int own = pad + w * kSeg + lane * 8;
-  const int rtw = pad + D::O_RT + w * (int)sizeof(RowT);
-  const int lm = blockIdx.x;
-  const int m = sp.mol[lm];
-  float2* gs = sp.psi + (long long)lm * ROWS * NR;
-  auto issue = [&](int ck) {
-    const int r0 = ck * kTile, b = ck & 1;
+  // this thread's byte offsets: own rows RPL (w + NW i) + half at point pt, and their row-table entries
+  const int own = pad + w * SLOT + lane * 8;
+  const int rtw = pad + D::O_RT + (RPL * w + half) * (int)sizeof(RowT);
+  auto issue = [&](int mol, int ck) {
+    const int r0 = ck * TILE, b = ck & 1;
     unsigned char* base = sm + pad;
-    tensor2d_g2s(base + D::O_STG, &maps.s, r0, lm * ROWS, &s_bar[0]);
-    tensor2d_g2s(base + D::O_STG + ROWS * kSeg, &maps.d2, r0, lm * ROWS, &s_bar[0]);
-    tensor2d_g2s(base + D::O_VD + b * NV * kSeg, &maps.vd, r0, 0, &s_bar[0]);
-    tensor2d_g2s(base + D::O_VH + b * NV * kSeg, &maps.vh, r0, 0, &s_bar[0]);
+    tensor2d_g2s(base + D::O_STG, &maps.s, r0, mol * ROWS, &s_bar[0]);
+    tensor2d_g2s(base + D::O_STG + ROWS * SEG, &maps.d2, r0, mol * ROWS, &s_bar[0]);
+    tensor2d_g2s(base + D::O_VD + b * NV * SEG, &maps.vd, r0, 0, &s_bar[0]);
+    tensor2d_g2s(base + D::O_VH + b * NV * SEG, &maps.vh, r0, 0, &s_bar[0]);
     tensor2d_g2s(base + D::O_MK, &maps.mk, r0, 0, &s_bar[0]);
   };
-  constexpr unsigned kChunkBytes = (2 * ROWS + 2 * NV + 1) * kSeg;
+  constexpr unsigned kChunkBytes = (2 * ROWS + 2 * NV + 1) * SEG;
+  const int nchunks = NR / TILE;  // even: NR is 64, 128 or 256
 
+  int lm = blockIdx.x;
   if (t == 0) {
     mbar_init(&s_bar[0], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     mbar_expect_tx(&s_bar[0], kChunkBytes);
+    issue(lm, 0);
   }
-  for (int q = t; q < kTriGuard * kTile; q += NT) {
+  for (int q = t; q < kTriGuard * TILE; q += NT) {
     reinterpret_cast<float2*>(sm + pad + D::O_TB)[q] = make_float2(0.f, 0.f);
     reinterpret_cast<float2*>(sm + pad + D::O_TB + TBB)[q] = make_float2(0.f, 0.f);
   }
-  __syncthreads();
-  if (t == 0) {
-    issue(0);
-    molecule_field(md, g, prescribed, m, J, sp.theta, s_fld, s_ph, &s_nterms, err);
-  } else if (t >= 32 && t < 41) {
-    s_rot[t - 32] = md.rot[9 * (long long)m + (t - 32)];
-  } else if (t >= 41 && t < 44) {
-    s_mu[t - 41] = md.mu[3 * (long long)m + (t - 41)];
-  } else if (t >= 44 && t < 46) {
-    s_abs[t - 44] = md.absorbed[2 * (long long)m + (t - 44)];
-  }
-  // neighbour runs and potential row of this thread's rows (bytes from sm)
-  int ou[RPW], od[RPW], vo[RPW];
-#pragma unroll
-  for (int i = 0; i < RPW; ++i) {
-    const int q = w + NW * i;
-    const int sf = q >= NROT, c = q - sf * NROT, j = j_of(c);
-    const int other = kTriGuard + (1 - sf) * NROT;
-    ou[i] = pad + D::O_TB + lane * 8 + (j < J ? (other + c + 2 * j + 1) * kSeg : 0);
-    od[i] = pad + D::O_TB + lane * 8 + (j > 0 ? (other + c - 2 * j - 1) * kSeg : 0);
-    vo[i] = pad + lane * 8 + (sf * (J + 1) + j) * kSeg;
-  }
-  __syncthreads();
-  if (t < ROWS) {  // the row table of this step
-    const float th = (float)sp.theta, ep = 0.5f * s_fld[0] * th, ez = s_fld[1] * th;
-    const int q = t, sf = q >= NROT, c = q - sf * NROT, j = j_of(c), mm = c - j * j - j;
-    RowT r;
-    r.ph = s_ph[mm + J];
-    r.pad = make_float2(0.f, 0.f);
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    r.du = j < J ? g_tri_up[c] : z4;
-    r.dd = j > 0 ? g_tri_dn[c] : z4;
-    r.cu = make_float4(ep * r.du.x, ez * r.du.y, ep * r.du.z, 0.f);
-    r.cd = make_float4(ep * r.dd.x, ez * r.dd.y, ep * r.dd.z, 0.f);
-    *reinterpret_cast<RowT*>(sm + pad + D::O_RT + q * (int)sizeof(RowT)) = r;
-  }
-  const int nterms = s_nterms;
-  const int nchunks = NR / kTile;  // even: NR is 64, 128 or 256
-  float2 sv[RPW], dv[RPW], sacc[RPW];
-  float p_hi[2] = {0.f, 0.f}, p_lo[2] = {0.f, 0.f};  // populations, compensated
-  float a_gf = 0.f, a_ef = 0.f, dP = 0.f, dQ = 0.f, dZ = 0.f, rnd = 0.f;
-  const float cfix = md.ncorr[m];  // rounding feedback of the previous step
-  // ground rows: q = w + NW i < NROT
-  auto ground = [&](int i) { return NW * i + NW <= NROT || (NW * i < NROT && w < NROT - NW * i); };
+  // ground rows: q = RPL (w + NW i) + half < NROT
+  auto ground = [&](int i) { return RPL * (w + NW * i) + half < NROT; };
 
-  // one coupling-series term reading term buffer P (compile-time), writing
-  // the other one unless it is the last
-  auto term = [&](auto Pc, int n) {
-    constexpr int P = decltype(Pc)::value;
-    const float cn = 1.f / (float)n;
-    const bool store = n < nterms;
-#pragma unroll
-    for (int i = 0; i < RPW; ++i) {
-      const float4 cu = *reinterpret_cast<const float4*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtCu);
-      const float4 cd = *reinterpret_cast<const float4*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtCd);
-      const float2 u0 = lds2<P * TBB>(sm, ou[i]), u1 = lds2<P * TBB + kSeg>(sm, ou[i]),
-                   u2 = lds2<P * TBB + 2 * kSeg>(sm, ou[i]);
-      const float2 d0 = lds2<P * TBB>(sm, od[i]), d1 = lds2<P * TBB + kSeg>(sm, od[i]),
-                   d2 = lds2<P * TBB + 2 * kSeg>(sm, od[i]);
-      float ax = cu.x * u0.x, ay = cu.x * u0.y;
-      ax = fmaf(cu.y, u1.x, ax); ay = fmaf(cu.y, u1.y, ay);
-      ax = fmaf(cu.z, u2.x, ax); ay = fmaf(cu.z, u2.y, ay);
-      ax = fmaf(cd.x, d0.x, ax); ay = fmaf(cd.x, d0.y, ay);
-      ax = fmaf(cd.y, d1.x, ax); ay = fmaf(cd.y, d1.y, ay);
-      ax = fmaf(cd.z, d2.x, ax); ay = fmaf(cd.z, d2.y, ay);
-      const float2 o = make_float2(-cn * ay, cn * ax);  // i (theta/n) M in
-      sacc[i].x += o.x;
-      sacc[i].y += o.y;
-      if (store) sts2<(1 - P) * TBB + G0>(sm, own + D::O_TB + NW * i * kSeg, o);
+  for (; lm < sp.nmol; lm += gridDim.x) {
+    const int m = sp.mol[lm];
+    __syncthreads();  // the previous molecule's outputs are written: its records may be replaced
+    const float4 f = __ldg(&sp.fld[lm]);  // (theta E'_z, theta E'_x/2, theta E'_y/2, terms)
+    const int nterms = __float_as_int(f.w);
+    if (t <= J) {  // e^{i t phi_E} by binary powers of e^{i phi_E} = (E'_x + i E'_y)/E_perp
+      const float ep = sqrtf(f.y * f.y + f.z * f.z);
+      float2 e1 = ep > 0.f ? make_float2(f.y / ep, f.z / ep) : make_float2(1.f, 0.f);
+      float2 pw = make_float2(1.f, 0.f);
+      for (int k = t; k > 0; k >>= 1) {
+        if (k & 1) pw = cmul(pw, e1);
+        e1 = cmul(e1, e1);
+      }
+      s_ph[J + t] = pw;
+      s_ph[J - t] = make_float2(pw.x, -pw.y);
     }
-    if (store) __syncthreads();
-  };
+    for (int q = t; q < 14; q += NT) {  // rotation, previous dipole, absorbed norm so far
+      if (q < 9) s_rot[q] = md.rot[9 * (long long)m + q];
+      else if (q < 12) s_mu[q - 9] = md.mu[3 * (long long)m + (q - 9)];
+      else s_abs[q - 12] = md.absorbed[2 * (long long)m + (q - 12)];
+    }
+    const float cfix = md.ncorr[m];  // rounding feedback of the previous step
+    __syncthreads();
+    for (int q = t; q < ROWS; q += NT) {  // the row table of this molecule
+      // theta E_perp / 2 on the X runs and theta E'_z on the Z runs (frame turned so E'_y = 0)
+      const float ep = sqrtf(f.y * f.y + f.z * f.z), ez = f.x;
+      const int sf = q >= NROT, c = q - sf * NROT, j = j_of(c), mm = c - j * j - j;
+      const int other = kTriGuard + (1 - sf) * NROT;
+      RowT r;
+      r.ph = s_ph[mm + J];
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      r.du = j < J ? g_tri_up[c] : z4;
+      r.dd = j > 0 ? g_tri_dn[c] : z4;
+      r.cu = make_float4(ep * r.du.x, ez * r.du.y, ep * r.du.z, 0.f);
+      r.cd = make_float4(ep * r.dd.x, ez * r.dd.y, ep * r.dd.z, 0.f);
+      r.ou = D::O_TB + (j < J ? (other + c + 2 * j + 1) * SEG : 0);
+      r.od = D::O_TB + (j > 0 ? (other + c - 2 * j - 1) * SEG : 0);
+      r.vo = (sf * (J + 1) + j) * SEG;
+      r.pad = 0;
+      *reinterpret_cast<RowT*>(sm + pad + D::O_RT + q * (int)sizeof(RowT)) = r;
+    }
+    float2 sv[RPW], dv[RPW], sacc[RPW];
+    float p_hi[2] = {0.f, 0.f}, p_lo[2] = {0.f, 0.f};  // populations, compensated
+    float a_gf = 0.f, a_ef = 0.f, dP = 0.f, dQ = 0.f, dZ = 0.f, rnd = 0.f;
+    float2* gs = sp.psi + (long long)lm * ROWS * NR;
 
-  // one chunk with the buffer parity B known at compile time; false on a timeout
-  auto chunk = [&](auto Bc, int ck) -> bool {
-    constexpr int B = decltype(Bc)::value;
-    constexpr int OVD = D::O_VD + B * NV * kSeg, OVH = D::O_VH + B * NV * kSeg;
-    const bool ok = mbar_wait_sleep(&s_bar[0], (unsigned)B);
-    if (!__syncthreads_and(ok)) {
-      if (t == 0) atomicOr(err, kErrTimeout);
-      if (!ok) mbar_wait_sleep(&s_bar[0], (unsigned)B);
-      return false;
-    }
-    const float mk = reinterpret_cast<const float2*>(sm + pad + D::O_MK)[lane].x;
-    // ---- s, d2; eta = e^{i m phi} V^{1/2} u into term buffer 0
+    // one coupling-series term reading term buffer P (compile-time), writing
+    // the other one unless it is the last
+    auto term = [&](auto Pc, int n) {
+      constexpr int P = decltype(Pc)::value;
+      const float cn = 1.f / (float)n;
+      const bool store = n < nterms;
 #pragma unroll
-    for (int i = 0; i < RPW; ++i) {
-      sv[i] = lds2<D::O_STG>(sm, own + NW * i * kSeg);
-      dv[i] = lds2<D::O_STG + ROWS * kSeg>(sm, own + NW * i * kSeg);
-      sacc[i] = make_float2(0.f, 0.f);
-      if (nterms > 0) {
-        const float2 vh = lds2<OVH>(sm, vo[i]);
-        const float2 ph = *reinterpret_cast<const float2*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtPh);
-        sts2<D::O_TB + G0>(sm, own + NW * i * kSeg, cmul(ph, cmul(vh, sv[i] + dv[i])));
+      for (int i = 0; i < RPW; ++i) {
+        const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowT);
+        const float4 cu = *reinterpret_cast<const float4*>(rt + offsetof(RowT, cu));
+        const float4 cd = *reinterpret_cast<const float4*>(rt + offsetof(RowT, cd));
+        const int2 oo = *reinterpret_cast<const int2*>(rt + offsetof(RowT, ou));
+        const int ou = pad + pt * 8 + oo.x, od = pad + pt * 8 + oo.y;
+        const float2 u0 = lds2<P * TBB>(sm, ou), u1 = lds2<P * TBB + SEG>(sm, ou),
+                     u2 = lds2<P * TBB + 2 * SEG>(sm, ou);
+        const float2 d0 = lds2<P * TBB>(sm, od), d1 = lds2<P * TBB + SEG>(sm, od),
+                     d2 = lds2<P * TBB + 2 * SEG>(sm, od);
+        float ax = cu.x * u0.x, ay = cu.x * u0.y;
+        ax = fmaf(cu.y, u1.x, ax); ay = fmaf(cu.y, u1.y, ay);
+        ax = fmaf(cu.z, u2.x, ax); ay = fmaf(cu.z, u2.y, ay);
+        ax = fmaf(cd.x, d0.x, ax); ay = fmaf(cd.x, d0.y, ay);
+        ax = fmaf(cd.y, d1.x, ax); ay = fmaf(cd.y, d1.y, ay);
+        ax = fmaf(cd.z, d2.x, ax); ay = fmaf(cd.z, d2.y, ay);
+        const float2 o = make_float2(-cn * ay, cn * ax);  // i (theta/n) M in
+        sacc[i].x += o.x;
+        sacc[i].y += o.y;
+        if (store) sts2<(1 - P) * TBB + G0>(sm, own + D::O_TB + NW * i * SLOT, o);
       }
-    }
-    __syncthreads();
-    if (t == 0 && ck + 1 < nchunks) {  // the staging buffer is free
-      mbar_expect_tx(&s_bar[0], kChunkBytes);
-      issue(ck + 1);
-    }
-    for (int n = 1; n <= nterms; n += 2) {
-      term(std::integral_constant<int, 0>(), n);
-      if (n + 1 <= nterms) term(std::integral_constant<int, 1>(), n + 1);
-    }
-    // ---- d1 = (V - 1) u + V^{1/2} e^{-i m phi} S ; mask ; s' = s + (d2 + d1) + cfix s
-    const int sbo = (nterms & 1) * TBB;  // s' buffer: not read by the last term
-    float2* gsw = gs + (long long)w * NR + ck * kTile + lane;
-    float sg = 0.f, se = 0.f;
-#pragma unroll
-    for (int i = 0; i < RPW; ++i) {
-      const float2 u = sv[i] + dv[i];
-      const float2 vd = lds2<OVD>(sm, vo[i]);
-      float2 d1 = cmul(vd, u);
-      if (nterms > 0) {
-        const float2 vh = lds2<OVH>(sm, vo[i]);
-        const float2 ph = *reinterpret_cast<const float2*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtPh);
-        d1 = d1 + cmul(vh, cmul(make_float2(ph.x, -ph.y), sacc[i]));
-      }
-      const bool gr = ground(i);
-      if (mk < 1.f) {
-        const float px = u.x + d1.x, py = u.y + d1.y;
-        d1.x = fmaf(mk - 1.f, u.x, mk * d1.x);
-        d1.y = fmaf(mk - 1.f, u.y, mk * d1.y);
-        const float dd = (1.f - mk * mk) * fmaf(px, px, py * py);
-        if (gr) a_gf += dd; else a_ef += dd;
-      }
-      const float2 sn = round_update(sv[i], dv[i] + d1, cfix, rnd);
-      gsw[(long long)(NW * i) * NR] = sn;
-      sts2<D::O_TB + G0>(sm, own + sbo + NW * i * kSeg, sn);
-      sv[i] = sn;
-      const float b2 = fmaf(sn.x, sn.x, sn.y * sn.y);
-      if (gr) sg += b2; else se += b2;
-    }
-    acc2(p_hi[0], p_lo[0], sg);
-    acc2(p_hi[1], p_lo[1], se);
-    __syncthreads();
-    // ---- dipole in the molecule frame: sum_c conj(g_c) (A e)_c for A = Z, S+, S-
-    float2 accP = make_float2(0.f, 0.f), accM = accP, accZ = accP;
-#pragma unroll
-    for (int i = 0; i < RPW; ++i) {
-      if (ground(i)) {
-        const float2 gc = sv[i];
-        const float4 du = *reinterpret_cast<const float4*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtDu);
-        const float4 dd = *reinterpret_cast<const float4*>(sm + rtw + NW * i * (int)sizeof(RowT) + kRtDd);
-        const int a = ou[i] + sbo, c = od[i] + sbo;
-        const float2 u0 = lds2<0>(sm, a), u1 = lds2<kSeg>(sm, a), u2 = lds2<2 * kSeg>(sm, a);
-        const float2 e0 = lds2<0>(sm, c), e1 = lds2<kSeg>(sm, c), e2 = lds2<2 * kSeg>(sm, c);
-        const float2 wP = make_float2(fmaf(du.x, u0.x, dd.x * e0.x), fmaf(du.x, u0.y, dd.x * e0.y));
-        const float2 wZ = make_float2(fmaf(du.y, u1.x, dd.y * e1.x), fmaf(du.y, u1.y, dd.y * e1.y));
-        const float2 wM = make_float2(fmaf(du.z, u2.x, dd.z * e2.x), fmaf(du.z, u2.y, dd.z * e2.y));
-        accZ.x += fmaf(gc.x, wZ.x, gc.y * wZ.y);
-        accZ.y += fmaf(gc.x, wZ.y, -gc.y * wZ.x);
-        accP.x += fmaf(gc.x, wP.x, gc.y * wP.y);
-        accP.y += fmaf(gc.x, wP.y, -gc.y * wP.x);
-        accM.x += fmaf(gc.x, wM.x, gc.y * wM.y);
-        accM.y += fmaf(gc.x, wM.y, -gc.y * wM.x);
-      }
-    }
-    dP += accP.x + accM.x;
-    dQ += accP.y - accM.y;
-    dZ += 2.f * accZ.x;
-    return true;
-  };
+      if (store) __syncthreads();
+    };
 
-  for (int ck = 0; ck < nchunks; ck += 2) {
-    if (!chunk(std::integral_constant<int, 0>(), ck)) return;
-    if (!chunk(std::integral_constant<int, 1>(), ck + 1)) return;
-  }
-  // ---- block reduction: populations compensated, the rest plain FP32
-  {
-    float v[8] = {p_hi[0], p_hi[1], a_gf, a_ef, dP, dQ, dZ, rnd};
-    float lo[2] = {p_lo[0], p_lo[1]};
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        const float h2 = __shfl_xor_sync(0xffffffffu, v[k], o);
-        const float l2 = __shfl_xor_sync(0xffffffffu, lo[k], o);
-        acc2(v[k], lo[k], h2);
-        lo[k] += l2;
+    // one tile with the buffer parity B known at compile time; false on a timeout
+    auto chunk = [&](auto Bc, int ck) -> bool {
+      constexpr int B = decltype(Bc)::value;
+      constexpr int OVD = D::O_VD + B * NV * SEG, OVH = D::O_VH + B * NV * SEG;
+      const bool ok = mbar_wait_sleep(&s_bar[0], (unsigned)B);
+      if (!__syncthreads_and(ok)) {
+        if (t == 0) atomicOr(err, kErrTimeout);
+        if (!ok) mbar_wait_sleep(&s_bar[0], (unsigned)B);
+        return false;
       }
+      const float mk = reinterpret_cast<const float2*>(sm + pad + D::O_MK)[pt].x;
+      // ---- s, d2; eta = e^{i m phi} V^{1/2} u into term buffer 0
 #pragma unroll
-      for (int k = 2; k < 8; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int k = 0; k < 7; ++k) s_red[w][k] = v[k];
-      s_red[w][7] = lo[0];
-      s_red[w][8] = lo[1];
-      s_red[w][9] = v[7];
-    }
-    __syncthreads();
-    if (t < 8) {
-      float hi = 0.f, l = 0.f;
-      for (int ww = 0; ww < NW; ++ww) {
-        acc2(hi, l, s_red[ww][t < 7 ? t : 9]);
-        if (t < 2) l += s_red[ww][7 + t];
+      for (int i = 0; i < RPW; ++i) {
+        sv[i] = lds2<D::O_STG>(sm, own + NW * i * SLOT);
+        dv[i] = lds2<D::O_STG + ROWS * SEG>(sm, own + NW * i * SLOT);
+        sacc[i] = make_float2(0.f, 0.f);
+        if (nterms > 0) {
+          const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowT);
+          const int vo = pad + pt * 8 + *reinterpret_cast<const int*>(rt + offsetof(RowT, vo));
+          const float2 vh = lds2<OVH>(sm, vo);
+          const float2 ph = *reinterpret_cast<const float2*>(rt + offsetof(RowT, ph));
+          sts2<D::O_TB + G0>(sm, own + NW * i * SLOT, cmul(ph, cmul(vh, sv[i] + dv[i])));
+        }
       }
-      s_fin[t] = hi + l;
-      if (t < 2) s_fin_lo[t] = l - (s_fin[t] - hi);
+      __syncthreads();
+      if (t == 0) {  // the staging buffer is free: the next tile, or the next molecule's first
+        if (ck + 1 < nchunks) {
+          mbar_expect_tx(&s_bar[0], kChunkBytes);
+          issue(lm, ck + 1);
+        } else if (lm + (int)gridDim.x < sp.nmol) {
+          mbar_expect_tx(&s_bar[0], kChunkBytes);
+          issue(lm + (int)gridDim.x, 0);
+        }
+      }
+      for (int n = 1; n <= nterms; n += 2) {
+        term(std::integral_constant<int, 0>(), n);
+        if (n + 1 <= nterms) term(std::integral_constant<int, 1>(), n + 1);
+      }
+      // ---- d1 = (V - 1) u + V^{1/2} e^{-i m phi} S ; mask ; s' = s + (d2 + d1) + cfix s
+      const int sbo = (nterms & 1) * TBB;  // s' buffer: not read by the last term
+      float2* gsw = gs + (long long)(RPL * w + half) * NR + ck * TILE + pt;
+      float sg = 0.f, se = 0.f;
+#pragma unroll
+      for (int i = 0; i < RPW; ++i) {
+        const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowT);
+        const int vo = pad + pt * 8 + *reinterpret_cast<const int*>(rt + offsetof(RowT, vo));
+        const float2 u = sv[i] + dv[i];
+        const float2 vd = lds2<OVD>(sm, vo);
+        float2 d1 = cmul(vd, u);
+        if (nterms > 0) {
+          const float2 vh = lds2<OVH>(sm, vo);
+          const float2 ph = *reinterpret_cast<const float2*>(rt + offsetof(RowT, ph));
+          d1 = d1 + cmul(vh, cmul(make_float2(ph.x, -ph.y), sacc[i]));
+        }
+        const bool gr = ground(i);
+        if (mk < 1.f) {
+          const float px = u.x + d1.x, py = u.y + d1.y;
+          d1.x = fmaf(mk - 1.f, u.x, mk * d1.x);
+          d1.y = fmaf(mk - 1.f, u.y, mk * d1.y);
+          const float dd = (1.f - mk * mk) * fmaf(px, px, py * py);
+          if (gr) a_gf += dd; else a_ef += dd;
+        }
+        const float2 sn = round_update(sv[i], dv[i] + d1, cfix, rnd);
+        gsw[(long long)(RPL * NW * i) * NR] = sn;
+        sts2<D::O_TB + G0>(sm, own + sbo + NW * i * SLOT, sn);
+        sv[i] = sn;
+        const float b2 = fmaf(sn.x, sn.x, sn.y * sn.y);
+        if (gr) sg += b2; else se += b2;
+      }
+      acc2(p_hi[0], p_lo[0], sg);
+      acc2(p_hi[1], p_lo[1], se);
+      __syncthreads();
+      // ---- dipole in the molecule frame: sum_c conj(g_c) (A e)_c for A = Z, S+, S-
+      float2 accP = make_float2(0.f, 0.f), accM = accP, accZ = accP;
+#pragma unroll
+      for (int i = 0; i < RPW; ++i) {
+        if (ground(i)) {
+          const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowT);
+          const float2 gc = sv[i];
+          const float4 du = *reinterpret_cast<const float4*>(rt + offsetof(RowT, du));
+          const float4 dd = *reinterpret_cast<const float4*>(rt + offsetof(RowT, dd));
+          const int2 oo = *reinterpret_cast<const int2*>(rt + offsetof(RowT, ou));
+          const int a = pad + pt * 8 + oo.x + sbo, c = pad + pt * 8 + oo.y + sbo;
+          const float2 u0 = lds2<0>(sm, a), u1 = lds2<SEG>(sm, a), u2 = lds2<2 * SEG>(sm, a);
+          const float2 e0 = lds2<0>(sm, c), e1 = lds2<SEG>(sm, c), e2 = lds2<2 * SEG>(sm, c);
+          const float2 wP = make_float2(fmaf(du.x, u0.x, dd.x * e0.x), fmaf(du.x, u0.y, dd.x * e0.y));
+          const float2 wZ = make_float2(fmaf(du.y, u1.x, dd.y * e1.x), fmaf(du.y, u1.y, dd.y * e1.y));
+          const float2 wM = make_float2(fmaf(du.z, u2.x, dd.z * e2.x), fmaf(du.z, u2.y, dd.z * e2.y));
+          accZ.x += fmaf(gc.x, wZ.x, gc.y * wZ.y);
+          accZ.y += fmaf(gc.x, wZ.y, -gc.y * wZ.x);
+          accP.x += fmaf(gc.x, wP.x, gc.y * wP.y);
+          accP.y += fmaf(gc.x, wP.y, -gc.y * wP.x);
+          accM.x += fmaf(gc.x, wM.x, gc.y * wM.y);
+          accM.y += fmaf(gc.x, wM.y, -gc.y * wM.x);
+        }
+      }
+      dP += accP.x + accM.x;
+      dQ += accP.y - accM.y;
+      dZ += 2.f * accZ.x;
+      return true;
+    };
+
+    for (int ck = 0; ck < nchunks; ck += 2) {
+      if (!chunk(std::integral_constant<int, 0>(), ck)) return;
+      if (!chunk(std::integral_constant<int, 1>(), ck + 1)) return;
     }
-    __syncthreads();
-    if (t < 3) {  // lab dipole: mu = O mu', mu' = d dR (Re(S+ + S-), Im(S+ - S-), 2 Re Z)
-      const float sc = (float)sp.dipole * sp.dR;
-      const float lab = sc * (s_rot[3 * t] * s_fin[4] + s_rot[3 * t + 1] * s_fin[5] + s_rot[3 * t + 2] * s_fin[6]);
-      const double nl = (double)lab;
-      md.dmu[3 * (long long)m + t] = nl - s_mu[t];
-      md.mu[3 * (long long)m + t] = nl;
-    } else if (t < 5) {
-      const double P = ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
-      md.pop[2 * (long long)m + (t - 3)] = P;
-      if (!isfinite(P)) atomicOr(err, kErrNonFinite);
-    } else if (t < 7) {
-      md.absorbed[2 * (long long)m + (t - 5)] = s_abs[t - 5] + (double)s_fin[t - 3] * (double)sp.dR;
-    } else if (t == 7) {
-      md.ncorr[m] = rounding_feedback(s_fin[7], s_fin[0] + s_fin[1]);
+    // ---- block reduction: populations compensated, the rest plain FP32
+    {
+      float v[8] = {p_hi[0], p_hi[1], a_gf, a_ef, dP, dQ, dZ, rnd};
+      float lo[2] = {p_lo[0], p_lo[1]};
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const float h2 = __shfl_xor_sync(0xffffffffu, v[k], o);
+          const float l2 = __shfl_xor_sync(0xffffffffu, lo[k], o);
+          acc2(v[k], lo[k], h2);
+          lo[k] += l2;
+        }
+#pragma unroll
+        for (int k = 2; k < 8; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < 7; ++k) s_red[w][k] = v[k];
+        s_red[w][7] = lo[0];
+        s_red[w][8] = lo[1];
+        s_red[w][9] = v[7];
+      }
+      __syncthreads();
+      if (t < 8) {
+        float hi = 0.f, l = 0.f;
+        for (int ww = 0; ww < NW; ++ww) {
+          acc2(hi, l, s_red[ww][t < 7 ? t : 9]);
+          if (t < 2) l += s_red[ww][7 + t];
+        }
+        s_fin[t] = hi + l;
+        if (t < 2) s_fin_lo[t] = l - (s_fin[t] - hi);
+      }
+      __syncthreads();
+      if (t < 3) {  // lab dipole: mu = O mu', mu' = d dR (Re(S+ + S-), Im(S+ - S-), 2 Re Z)
+        const float sc = (float)sp.dipole * sp.dR;
+        const float lab =
+            sc * (s_rot[3 * t] * s_fin[4] + s_rot[3 * t + 1] * s_fin[5] + s_rot[3 * t + 2] * s_fin[6]);
+        const double nl = (double)lab;
+        md.dmu[3 * (long long)m + t] = nl - s_mu[t];
+        md.mu[3 * (long long)m + t] = nl;
+      } else if (t < 5) {
+        const double P = ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
+        md.pop[2 * (long long)m + (t - 3)] = P;
+        if (!isfinite(P)) atomicOr(err, kErrNonFinite);
+      } else if (t < 7) {
+        md.absorbed[2 * (long long)m + (t - 5)] = s_abs[t - 5] + (double)s_fin[t - 3] * (double)sp.dR;
+      } else if (t == 7) {
+        md.ncorr[m] = rounding_feedback(s_fin[7], s_fin[0] + s_fin[1]);
+      }
     }
   }
 }
@@ -1666,6 +1699,13 @@ static bool use_point(const SpeciesDev& sp) {
   if (sp.jmax > 4 || (sp.path == MS_MOL_FUSED && sp.nr != 128)) return false;
   return sp.kern == MS_KERN_DEFAULT || sp.kern == MS_KERN_POINT;
 }
+static bool rspace_ok(int nr, int jmax);
+// The tiled kernel runs a streaming species' R-space pass where the point-
+// resident one does not and it applies, unless the plan names another kernel.
+static bool use_tile(const SpeciesDev& sp) {
+  if (sp.path != MS_MOL_STREAMING || use_point(sp) || !rspace_ok(sp.nr, sp.jmax)) return false;
+  return sp.kern == MS_KERN_DEFAULT || sp.kern == MS_KERN_TILE;
+}
 }  // namespace ms
 
 // ----------------------------------------------------------------------------
@@ -1851,9 +1891,14 @@ static StepShape step_shape_ch(int nr, int nrot, bool fused, int ch) {
   return {ch, 24, 0, false};
 }
 
-// The streaming R-space kernel covers J <= 8 (rows <= 162) on radial grids of
-// whole 32-point chunks.
-static bool rspace_ok(int nr, int jmax) { return nr % kTile == 0 && (nr / kTile) % 2 == 0 && jmax <= 8; }
+// The tiled R-space kernel covers J <= 8 (rows <= 162) at tile widths of 32
+// and 16 radial points (N_r 64, 128 and 256 hold an even number of tiles).
+// Its static rule: 16-point tiles from J = 5 on (two CTAs per SM), else 32.
+static bool rspace_ok(int nr, int jmax) { return (nr == 64 || nr == 128 || nr == 256) && jmax <= 8; }
+static int rspace_tile(const SpeciesDev& sp) {
+  if (sp.kern == MS_KERN_TILE && (sp.ch == 16 || sp.ch == 32)) return sp.ch;
+  return sp.jmax >= 5 ? 16 : 32;
+}
 
 // The plans a species can run: (layout, kernel, chunk width).  Parity-reduced
 // and d(R) species have one (the point-resident kernel); the mixed kinetic
@@ -1875,34 +1920,51 @@ int mol_plan_candidates(const SpeciesDev& sp, int (*out)[3], int max) {
       if (step_shape_ch(sp.nr, sp.nrot, true, ch).ok) add(MS_MOL_FUSED, MS_KERN_CHUNK, ch);
   }
   if (sp.jmax <= 4) add(MS_MOL_STREAMING, MS_KERN_POINT, 0);
-  if (rspace_ok(sp.nr, sp.jmax)) add(MS_MOL_STREAMING, MS_KERN_TILE, 0);
+  if (rspace_ok(sp.nr, sp.jmax)) {
+    add(MS_MOL_STREAMING, MS_KERN_TILE, 32);
+    add(MS_MOL_STREAMING, MS_KERN_TILE, 16);
+  }
   for (int ch : {32, 16, 8, 4})
     if (step_shape_ch(sp.nr, sp.nrot, false, ch).ok) add(MS_MOL_STREAMING, MS_KERN_CHUNK, ch);
   return n < max ? n : max;
 }
 
-template <int J>
-static void launch_rspace_j(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
-                            const RspaceMaps& maps, cudaStream_t s) {
-  using D = RsDims<J>;
-  auto k = mol_rspace_kernel<J>;
+template <int J, int TILE>
+static void launch_rspace_jt(const SpeciesDev& sp, const MolDev& md, int* err, const RspaceMaps& maps,
+                             cudaStream_t s) {
+  using D = RsDims<J, TILE>;
+  auto k = mol_rspace_kernel<J, TILE>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, D::BYTES);
   cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  k<<<sp.nmol, D::NT, D::BYTES, s>>>(sp, md, g, prescribed, err, maps);
+  // persistent: as many CTAs as fit at once, each walks molecules b, b + grid, ...
+  int dev = 0, nsm = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, D::NT, D::BYTES);
+  const long long fit = (long long)std::max(nsm, 1) * std::max(per, 1);
+  const int grid = (int)std::min<long long>(sp.nmol, fit);
+  k<<<grid, D::NT, D::BYTES, s>>>(sp, md, err, maps);
 }
 
-static void launch_rspace(const SpeciesDev& sp, const MolDev& md, const Grid& g, int prescribed, int* err,
-                          const RspaceMaps& maps, cudaStream_t s) {
+template <int J>
+static void launch_rspace_j(const SpeciesDev& sp, const MolDev& md, int* err, const RspaceMaps& maps,
+                            int tile, cudaStream_t s) {
+  if (tile == 16) launch_rspace_jt<J, 16>(sp, md, err, maps, s);
+  else launch_rspace_jt<J, 32>(sp, md, err, maps, s);
+}
+
+static void launch_rspace(const SpeciesDev& sp, const MolDev& md, int* err, const RspaceMaps& maps, int tile,
+                          cudaStream_t s) {
   switch (sp.jmax) {
-    case 0: launch_rspace_j<0>(sp, md, g, prescribed, err, maps, s); break;
-    case 1: launch_rspace_j<1>(sp, md, g, prescribed, err, maps, s); break;
-    case 2: launch_rspace_j<2>(sp, md, g, prescribed, err, maps, s); break;
-    case 3: launch_rspace_j<3>(sp, md, g, prescribed, err, maps, s); break;
-    case 4: launch_rspace_j<4>(sp, md, g, prescribed, err, maps, s); break;
-    case 5: launch_rspace_j<5>(sp, md, g, prescribed, err, maps, s); break;
-    case 6: launch_rspace_j<6>(sp, md, g, prescribed, err, maps, s); break;
-    case 7: launch_rspace_j<7>(sp, md, g, prescribed, err, maps, s); break;
-    case 8: launch_rspace_j<8>(sp, md, g, prescribed, err, maps, s); break;
+    case 0: launch_rspace_j<0>(sp, md, err, maps, tile, s); break;
+    case 1: launch_rspace_j<1>(sp, md, err, maps, tile, s); break;
+    case 2: launch_rspace_j<2>(sp, md, err, maps, tile, s); break;
+    case 3: launch_rspace_j<3>(sp, md, err, maps, tile, s); break;
+    case 4: launch_rspace_j<4>(sp, md, err, maps, tile, s); break;
+    case 5: launch_rspace_j<5>(sp, md, err, maps, tile, s); break;
+    case 6: launch_rspace_j<6>(sp, md, err, maps, tile, s); break;
+    case 7: launch_rspace_j<7>(sp, md, err, maps, tile, s); break;
+    case 8: launch_rspace_j<8>(sp, md, err, maps, tile, s); break;
   }
 }
 
@@ -1923,14 +1985,14 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// [nrows][nr] array of complex FP32 values (8-byte elements), box kTile x box_rows
+// [nrows][nr] array of complex FP32 values (8-byte elements), box tile x box_rows
 static bool encode_rows(CUtensorMap* m, const void* base, unsigned long long nr, unsigned long long nrows,
-                        unsigned box_rows) {
+                        unsigned box_rows, unsigned tile) {
   const PFN_cuTensorMapEncodeTiled_v12000 fn = tensor_map_encoder();
   if (!fn || !base) return false;
   const cuuint64_t dims[2] = {nr, nrows};
   const cuuint64_t strides[1] = {nr * sizeof(float2)};
-  const cuuint32_t box[2] = {(cuuint32_t)kTile, box_rows};
+  const cuuint32_t box[2] = {(cuuint32_t)tile, box_rows};
   const cuuint32_t es[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_INT64, 2, const_cast<void*>(base), dims, strides, box, es,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -1939,10 +2001,10 @@ static bool encode_rows(CUtensorMap* m, const void* base, unsigned long long nr,
 
 // The species' tensor maps, encoded on first use of a given set of arrays
 // (a few entries are kept: each handle, and the allocation-free scratch).
-static bool rspace_maps(const SpeciesDev& sp, RspaceMaps* out) {
+static bool rspace_maps(const SpeciesDev& sp, int tile, RspaceMaps* out) {
   struct Entry {
     const void *psi, *d2, *vd, *vh, *mk;
-    int nmol, nr, nrot;
+    int nmol, nr, nrot, tile;
     RspaceMaps maps;
   };
   static std::mutex mu;
@@ -1950,17 +2012,17 @@ static bool rspace_maps(const SpeciesDev& sp, RspaceMaps* out) {
   std::lock_guard<std::mutex> lock(mu);
   for (const Entry& e : cache)
     if (e.psi == sp.psi && e.d2 == sp.d2 && e.vd == sp.vdelta && e.vh == sp.vhalf && e.mk == sp.maskw &&
-        e.nmol == sp.nmol && e.nr == sp.nr && e.nrot == sp.nrot) {
+        e.nmol == sp.nmol && e.nr == sp.nr && e.nrot == sp.nrot && e.tile == tile) {
       *out = e.maps;
       return true;
     }
-  Entry e{sp.psi, sp.d2, sp.vdelta, sp.vhalf, sp.maskw, sp.nmol, sp.nr, sp.nrot, {}};
+  Entry e{sp.psi, sp.d2, sp.vdelta, sp.vhalf, sp.maskw, sp.nmol, sp.nr, sp.nrot, tile, {}};
   const unsigned rows = 2 * sp.nrot, nv = 2 * (sp.jmax + 1);
   const unsigned long long nr = sp.nr;
-  if (!encode_rows(&e.maps.s, sp.psi, nr, (unsigned long long)sp.nmol * rows, rows) ||
-      !encode_rows(&e.maps.d2, sp.d2, nr, (unsigned long long)sp.nmol * rows, rows) ||
-      !encode_rows(&e.maps.vd, sp.vdelta, nr, nv, nv) || !encode_rows(&e.maps.vh, sp.vhalf, nr, nv, nv) ||
-      !encode_rows(&e.maps.mk, sp.maskw, nr, 1, 1))
+  if (!encode_rows(&e.maps.s, sp.psi, nr, (unsigned long long)sp.nmol * rows, rows, tile) ||
+      !encode_rows(&e.maps.d2, sp.d2, nr, (unsigned long long)sp.nmol * rows, rows, tile) ||
+      !encode_rows(&e.maps.vd, sp.vdelta, nr, nv, nv, tile) || !encode_rows(&e.maps.vh, sp.vhalf, nr, nv, nv, tile) ||
+      !encode_rows(&e.maps.mk, sp.maskw, nr, 1, 1, tile))
     return false;
   if (cache.size() >= 32) cache.erase(cache.begin());
   cache.push_back(e);
@@ -2256,7 +2318,7 @@ static int launch_stage1_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
     return 1;
   }
   int n = 0;
-  if (use_point(sp)) {
+  if (use_point(sp) || use_tile(sp)) {  // the per-molecule frame-field records those kernels read
     mol_field_kernel<<<(sp.nmol + 127) / 128, 128, 0, s>>>(sp, md, g, prescribed, err);
     ++n;
   }
@@ -2310,8 +2372,8 @@ static int launch_stage2_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
     return 1;
   }
   RspaceMaps maps;
-  if ((sp.kern == MS_KERN_DEFAULT || sp.kern == MS_KERN_TILE) && rspace_ok(NR, sp.jmax) && rspace_maps(sp, &maps)) {
-    launch_rspace(sp, md, g, prescribed, err, maps, s);
+  if (use_tile(sp) && rspace_maps(sp, rspace_tile(sp), &maps)) {
+    launch_rspace(sp, md, err, maps, rspace_tile(sp), s);
     return 1;
   }
   if (sh.maxr == 4) launch_step_tt<NR, false, 4>(sp, md, g, prescribed, err, sh, s);

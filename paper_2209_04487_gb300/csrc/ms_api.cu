@@ -1705,7 +1705,9 @@ ms_status ms_set_species_plan(ms_sim* s, int32_t species, int32_t path, int32_t 
     for (int c = 0; c < nc; ++c) ok = ok || cand[c][0] == path;
     ok = ok || path == sp.path;  // the layout it already runs
   } else {
-    for (int c = 0; c < nc; ++c) ok = ok || (cand[c][0] == path && cand[c][1] == kernel && cand[c][2] == chunk);
+    for (int c = 0; c < nc; ++c)  // a tiled plan with chunk 0 follows the kernel's tile-width rule
+      ok = ok || (cand[c][0] == path && cand[c][1] == kernel &&
+                  (cand[c][2] == chunk || (kernel == MS_KERN_TILE && chunk == 0)));
   }
   if (!ok) return MS_EINVAL;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;

@@ -24,7 +24,8 @@ def B():
 
 
 def _plans(B):
-    kc = [(B.MS_KERN_POINT, 0), (B.MS_KERN_TILE, 0)] + [(B.MS_KERN_CHUNK, c) for c in (32, 16, 8, 4)]
+    kc = [(B.MS_KERN_POINT, 0), (B.MS_KERN_TILE, 32), (B.MS_KERN_TILE, 16)] + \
+        [(B.MS_KERN_CHUNK, c) for c in (32, 16, 8, 4)]
     return [(p, k, c) for p in (B.MS_MOL_FUSED, B.MS_MOL_STREAMING) for k, c in kc]
 
 
@@ -60,8 +61,8 @@ def test_every_plan_matches_oracle(B, nr, jmax, nmol):
     assert B.MS_KERN_CHUNK in kinds and len(ran) >= 3, ran
     if jmax <= 4:
         assert B.MS_KERN_POINT in kinds
-    if jmax <= 7:
-        assert B.MS_KERN_TILE in kinds
+    tiles = {c for _, k, c in ran if k == B.MS_KERN_TILE}
+    assert tiles == {16, 32}, ran          # both tile widths, J <= 8
 
 
 def test_autotuned_three_species_coupled(B):
@@ -96,6 +97,7 @@ def test_plan_validation(B):
     sim = B.Simulation(wl)
     for bad in ((B.MS_MOL_STREAMING, B.MS_KERN_POINT, 0),    # J = 9: no point-resident kernel
                 (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 0),     # J = 9: no tile kernel
+                (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 16),
                 (B.MS_MOL_STREAMING, B.MS_KERN_CHUNK, 12),   # not a chunk width
                 (7, B.MS_KERN_CHUNK, 8)):
         with pytest.raises(B.MSError) as e:
