@@ -368,7 +368,7 @@ def main():
         the library's stream, max over ranks) and its phase timings."""
         sim = B.Simulation(w, mol_path=mol_path, precision=precision, state_form=state_form,
                            autotune=B.MS_TUNE_MEASURE if tune else B.MS_TUNE_OFF)
-        plans = [sim.plan(i) for i in range(len(w.species))]
+        plans = [sim.plan_ex(i) for i in range(len(w.species))]
         if detectors is not None:
             sim.set_detectors(*detectors)
         form_path = sim.species_path(0)
@@ -528,7 +528,8 @@ def main():
                 "phases_ms_per_step": {"h": phases[0] / nsteps, "molecules": phases[1] / nsteps,
                                        "e": phases[2] / nsteps, "molecules_stage1": phases[4] / nsteps,
                                        "molecules_stage2": phases[5] / nsteps},
-                "plans": [{"layout": p[0], "kernel": p[1], "chunk": p[2]} for p in main_form["plans"]],
+                "plans": [{"layout": p[0], "kernel": p[1], "chunk": p[2], "ctas_per_sm": p[3]}
+                          for p in main_form["plans"]],
                 "roofline": roof, "roofline_kinetic": roof_kin, "roofline_molecular_step": roof_step,
                 "roofline_fdtd": roof_fdtd,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,
@@ -609,7 +610,8 @@ def splitring_forms(a, B, np, torch, dist, world, time_form, form_entry, main=No
     out["splitring_bloch_frozen"] = bl
     ft = time_form(w1, B.MS_MOL_AUTO, B.MS_PREC_FP32, pre, tune=True)
     tuned = form_entry(ft, w1, P1)
-    tuned["plan"] = {"layout": ft["plans"][0][0], "kernel": ft["plans"][0][1], "chunk": ft["plans"][0][2]}
+    tuned["plan"] = {"layout": ft["plans"][0][0], "kernel": ft["plans"][0][1], "chunk": ft["plans"][0][2],
+                     "ctas_per_sm": ft["plans"][0][3]}
     tuned["note"] = ("ms_options.autotune: every plan the species can run timed on a sandbox of 2,048 "
                      "molecules at create (kernel 1 point-resident, 2 tiled, 3 chunked)")
     out["splitring_autotuned"] = tuned

@@ -285,18 +285,25 @@ ms_status ms_step_noalloc(ms_sim* sim, int64_t n);
 int64_t ms_step_count(const ms_sim* sim);
 
 /* Copy the E (which = MS_FIELD_E) or H field of one sim to host_dst,
- * 3 * nz*ny*nx floats: all x components, then y, then z.  n is the
- * capacity of host_dst in floats. */
+ * 3 * nz*ny*nx floats: all x components, then y, then z, in the Yee
+ * positions of the header's layout note (the fields of Eq. 1 as the FDTD
+ * section stores them).  n is the capacity of host_dst in floats; MS_EINVAL
+ * for a smaller n, a bad `which` or sim, or a handle without a field grid.
+ * Synchronous. */
 ms_status ms_read_fields(ms_sim* sim, int32_t which, int32_t sim_index, float* host_dst,
                          size_t n);
 
-/* Overwrite the E or H field of one sim (same layout); for tests. */
+/* Overwrite the E or H field of one sim (same layout and errors as
+ * ms_read_fields); sets the initial or a test field of Eq. 1's leap-frog.
+ * Synchronous; src is copied. */
 ms_status ms_write_fields(ms_sim* sim, int32_t which, int32_t sim_index, const float* src,
                           size_t n);
 
 /* Per-molecule populations P_g, P_e (FP64) of molecules [first, first+count)
- * in the caller's molecule order, at the current time.  Either output may
- * be NULL. */
+ * in the caller's molecule order, at the current time: the norms
+ * sum_{j,m} integral |xi^{g,e}_{jm}(R)|^2 dR of the two surfaces' wavepackets
+ * of Eq. 3 (for frozen two-level molecules, rho_gg and rho_ee).  Either
+ * output may be NULL.  MS_EINVAL for a range outside the molecules. */
 ms_status ms_read_populations(ms_sim* sim, int64_t first, int64_t count, double* Pg,
                               double* Pe);
 
@@ -308,7 +315,11 @@ ms_status ms_read_dissociation(ms_sim* sim, int64_t first, int64_t count, double
                                double* absorbed_e, double* R_e_num, double* R_e_den);
 
 /* Per-molecule lab-frame induced dipole (a.u., FP64, [count][3]) at the
- * current time. */
+ * current time: the expectation value of the transition dipole between the
+ * two surfaces' wavepackets (Eq. 4's coupling operator), rotated from the
+ * molecule frame to the lab frame; the dipole density that enters Eq. 1's
+ * polarization current is this divided by the cell volume.  MS_EINVAL for a
+ * NULL mu or a range outside the molecules. */
 ms_status ms_read_dipoles(ms_sim* sim, int64_t first, int64_t count, double* mu);
 
 /* Prescribed drive (MS_DRIVE_PRESCRIBED): molecule k sees the lab field
@@ -434,6 +445,20 @@ ms_status ms_species_plan(const ms_sim* sim, int32_t species, int32_t* path, int
  * given layout.  A switch to the streaming layout allocates its (T - 1)s
  * scratch (MS_ENOMEM if that fails).  Takes effect from the next step. */
 ms_status ms_set_species_plan(ms_sim* sim, int32_t species, int32_t path, int32_t kernel, int32_t chunk);
+
+/* Extended plan (no counterpart in the paper): plan[0] layout, plan[1]
+ * kernel, plan[2] chunk, as for ms_species_plan, and plan[3] the grid of the
+ * persistent tiled kernel (MS_KERN_TILE): resident CTAs per SM (1..32, fewer
+ * if fewer fit), so each CTA walks about n_molecules / (plan[3] x SMs)
+ * molecules; 0 = as many CTAs as fit at once; -1 = one CTA per molecule.
+ * Other kernels take plan[3] = 0.  Every grid computes each molecule with the
+ * same arithmetic, so results are identical bit for bit; the autotuner
+ * (MS_TUNE_MEASURE) times the grids with the tile widths.  Setting a plan as
+ * ms_set_species_plan does, plus the grid; ms_set_species_plan sets grid 0.
+ * MS_EINVAL for a NULL handle or plan, a species out of range, a grid out of
+ * range or given to another kernel, or a plan the species cannot run. */
+ms_status ms_species_plan_ex(const ms_sim* sim, int32_t species, int32_t plan[4]);
+ms_status ms_set_species_plan_ex(ms_sim* sim, int32_t species, const int32_t plan[4]);
 
 /* Device memory held by the simulation, in bytes. */
 size_t ms_device_bytes(const ms_sim* sim);

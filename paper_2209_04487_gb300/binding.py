@@ -96,6 +96,8 @@ def _load() -> C.CDLL:
         "ms_species_path": (C.c_int32, [C.c_void_p, C.c_int32]),
         "ms_species_plan": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_int32), P(C.c_int32), P(C.c_int32)]),
         "ms_set_species_plan": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+        "ms_species_plan_ex": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_int32)]),
+        "ms_set_species_plan_ex": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_int32)]),
         "ms_set_detectors": (C.c_int, [C.c_void_p, P(C.c_int32), C.c_int32, P(C.c_double), C.c_int32]),
         "ms_read_flux": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_double)]),
         "ms_read_dft": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32, P(C.c_double)]),
@@ -119,7 +121,9 @@ LIB = _load()
 EXPORTED = ("ms_create", "ms_step", "ms_step_noalloc", "ms_step_count", "ms_read_fields", "ms_write_fields",
             "ms_read_populations", "ms_read_dissociation", "ms_read_dipoles",
             "ms_set_prescribed_field", "ms_set_replay_field", "ms_record_local_fields", "ms_save", "ms_load",
-            "ms_check_bounded_wait", "ms_species_path", "ms_species_plan", "ms_set_species_plan", "ms_set_detectors", "ms_read_flux", "ms_read_dft", "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
+            "ms_check_bounded_wait", "ms_species_path", "ms_species_plan", "ms_set_species_plan",
+            "ms_species_plan_ex", "ms_set_species_plan_ex", "ms_set_detectors", "ms_read_flux", "ms_read_dft",
+            "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
             "ms_destroy", "ms_status_string")
 
 
@@ -355,8 +359,15 @@ class Simulation:
         _check(LIB.ms_species_plan(self.h, species, C.byref(p), C.byref(k), C.byref(c)), "ms_species_plan")
         return p.value, k.value, c.value
 
-    def set_plan(self, species: int, path: int, kernel: int, chunk: int = 0):
-        _check(LIB.ms_set_species_plan(self.h, species, path, kernel, chunk), "ms_set_species_plan")
+    def set_plan(self, species: int, path: int, kernel: int, chunk: int = 0, ctas_per_sm: int = 0):
+        p = (C.c_int32 * 4)(path, kernel, chunk, ctas_per_sm)
+        _check(LIB.ms_set_species_plan_ex(self.h, species, p), "ms_set_species_plan_ex")
+
+    def plan_ex(self, species: int = 0):
+        """(layout, kernel, chunk width, resident CTAs per SM of the persistent tiled kernel)."""
+        p = (C.c_int32 * 4)()
+        _check(LIB.ms_species_plan_ex(self.h, species, p), "ms_species_plan_ex")
+        return tuple(p)
 
     @property
     def device_bytes(self) -> int:

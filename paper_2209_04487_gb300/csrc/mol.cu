@@ -1903,13 +1903,14 @@ static int rspace_tile(const SpeciesDev& sp) {
 // The plans a species can run: (layout, kernel, chunk width).  Parity-reduced
 // and d(R) species have one (the point-resident kernel); the mixed kinetic
 // pass needs the streaming layout.
-int mol_plan_candidates(const SpeciesDev& sp, int (*out)[3], int max) {
+int mol_plan_candidates(const SpeciesDev& sp, int (*out)[4], int max) {
   int n = 0;
-  auto add = [&](int path, int kern, int ch) {
+  auto add = [&](int path, int kern, int ch, int cps = 0) {
     if (n < max) {
       out[n][0] = path;
       out[n][1] = kern;
       out[n][2] = ch;
+      out[n][3] = cps;
     }
     ++n;
   };
@@ -1920,9 +1921,9 @@ int mol_plan_candidates(const SpeciesDev& sp, int (*out)[3], int max) {
       if (step_shape_ch(sp.nr, sp.nrot, true, ch).ok) add(MS_MOL_FUSED, MS_KERN_CHUNK, ch);
   }
   if (sp.jmax <= 4) add(MS_MOL_STREAMING, MS_KERN_POINT, 0);
-  if (rspace_ok(sp.nr, sp.jmax)) {
-    add(MS_MOL_STREAMING, MS_KERN_TILE, 32);
-    add(MS_MOL_STREAMING, MS_KERN_TILE, 16);
+  if (rspace_ok(sp.nr, sp.jmax)) {  // tile width x grid: as many CTAs as fit, one per SM, one per molecule
+    for (int tile : {32, 16})
+      for (int cps : {0, 1, -1}) add(MS_MOL_STREAMING, MS_KERN_TILE, tile, cps);
   }
   for (int ch : {32, 16, 8, 4})
     if (step_shape_ch(sp.nr, sp.nrot, false, ch).ok) add(MS_MOL_STREAMING, MS_KERN_CHUNK, ch);
@@ -1936,12 +1937,16 @@ static void launch_rspace_jt(const SpeciesDev& sp, const MolDev& md, int* err, c
   auto k = mol_rspace_kernel<J, TILE>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, D::BYTES);
   cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  // persistent: as many CTAs as fit at once, each walks molecules b, b + grid, ...
+  // persistent: CTA b walks molecules b, b + grid, ...; the grid is the
+  // plan's resident CTAs per SM (0: as many as fit) times the SMs, or one
+  // CTA per molecule (cps < 0)
   int dev = 0, nsm = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, D::NT, D::BYTES);
-  const long long fit = (long long)std::max(nsm, 1) * std::max(per, 1);
+  per = std::max(per, 1);
+  if (sp.cps > 0) per = std::min(per, sp.cps);
+  const long long fit = sp.cps < 0 ? (long long)sp.nmol : (long long)std::max(nsm, 1) * per;
   const int grid = (int)std::min<long long>(sp.nmol, fit);
   k<<<grid, D::NT, D::BYTES, s>>>(sp, md, err, maps);
 }

@@ -526,8 +526,8 @@ struct Scratch {
 // along a seeded direction per molecule, and keep the fastest plan.
 ms_status tune_species(ms_sim* s, int si) {
   ms::SpeciesDev& sp = s->sp[si];
-  int cand[16][3];
-  const int nc = ms::mol_plan_candidates(sp, cand, 16);
+  int cand[24][4];
+  const int nc = ms::mol_plan_candidates(sp, cand, 24);
   if (nc < 2 || sp.nmol == 0) return MS_OK;
   const int nt = std::min(sp.nmol, 2048);
   const size_t per = (size_t)sp.rows * sp.nr;
@@ -616,6 +616,7 @@ ms_status tune_species(ms_sim* s, int si) {
     t.path = cand[c][0];
     t.kern = cand[c][1];
     t.ch = cand[c][2];
+    t.cps = cand[c][3];
     auto run = [&]() {
       ms::launch_mol_stage1(t, m, g, 1, err, s->stream);
       ms::launch_mol_stage2(t, m, g, 1, err, s->stream);
@@ -646,6 +647,7 @@ ms_status tune_species(ms_sim* s, int si) {
   sp = trial;
   sp.kern = cand[pick][1];
   sp.ch = cand[pick][2];
+  sp.cps = cand[pick][3];
   return MS_OK;
 }
 
@@ -1694,12 +1696,21 @@ ms_status ms_species_plan(const ms_sim* s, int32_t species, int32_t* path, int32
   return MS_OK;
 }
 
-ms_status ms_set_species_plan(ms_sim* s, int32_t species, int32_t path, int32_t kernel, int32_t chunk) {
-  if (!s || species < 0 || species >= s->nspecies) return MS_EINVAL;
+ms_status ms_species_plan_ex(const ms_sim* s, int32_t species, int32_t plan[4]) {
+  if (!plan) return MS_EINVAL;
+  MS_TRY(ms_species_plan(s, species, &plan[0], &plan[1], &plan[2]));
+  plan[3] = s->sp[species].cps;
+  return MS_OK;
+}
+
+ms_status ms_set_species_plan_ex(ms_sim* s, int32_t species, const int32_t plan[4]) {
+  if (!s || !plan || species < 0 || species >= s->nspecies) return MS_EINVAL;
+  const int32_t path = plan[0], kernel = plan[1], chunk = plan[2], cps = plan[3];
   ms::SpeciesDev& sp = s->sp[species];
   if (sp.bloch) return MS_EINVAL;
-  int cand[16][3];
-  const int nc = ms::mol_plan_candidates(sp, cand, 16);
+  if (cps < -1 || cps > 32 || (cps != 0 && kernel != MS_KERN_TILE)) return MS_EINVAL;
+  int cand[24][4];
+  const int nc = ms::mol_plan_candidates(sp, cand, 24);
   bool ok = false;
   if (kernel == MS_KERN_DEFAULT && chunk == 0) {
     for (int c = 0; c < nc; ++c) ok = ok || cand[c][0] == path;
@@ -1717,8 +1728,14 @@ ms_status ms_set_species_plan(ms_sim* s, int32_t species, int32_t path, int32_t 
   sp = trial;
   sp.kern = kernel;
   sp.ch = chunk;
+  sp.cps = cps;
   s->gdirty = true;
   return MS_OK;
+}
+
+ms_status ms_set_species_plan(ms_sim* s, int32_t species, int32_t path, int32_t kernel, int32_t chunk) {
+  const int32_t plan[4] = {path, kernel, chunk, 0};
+  return ms_set_species_plan_ex(s, species, plan);
 }
 
 size_t ms_device_bytes(const ms_sim* s) { return s ? s->bytes : 0; }

@@ -111,6 +111,8 @@ struct SpeciesDev {
   int kpl_exp;
   int path;                 // MS_MOL_FUSED or MS_MOL_STREAMING
   int kern, ch;             // plan: MS_KERN_* of the R-space pass, chunk width of the chunked kernel (0: its rule)
+  int cps;                  // plan: grid of the persistent tiled kernel: resident CTAs per SM (> 0), 0 = as
+                            // many as fit, -1 = one molecule per CTA
   // per (s, j, r): e^{-i V dtau} - 1 and e^{-i V dtau/2}
   const float2* vdelta;     // [2][jmax+1][nr]
   const float2* vhalf;      // [2][jmax+1][nr]
@@ -208,8 +210,8 @@ int launch_bloch_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int
                       cudaStream_t s);
 void launch_bloch_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s);
 bool mol_step_supported(int nr, int nrot, int path);
-// the (layout, kernel, chunk width) plans a species can run; returns how many
-int mol_plan_candidates(const SpeciesDev& sp, int (*out)[3], int max);
+// the (layout, kernel, chunk width, CTAs per SM) plans a species can run; returns how many
+int mol_plan_candidates(const SpeciesDev& sp, int (*out)[4], int max);
 cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip);
 cudaError_t upload_triplet_tables(const CouplEntry* dip);
 cudaError_t launch_wait_timeout_probe(int tries, int* flag, cudaStream_t s);

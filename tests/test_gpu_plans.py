@@ -24,9 +24,11 @@ def B():
 
 
 def _plans(B):
-    kc = [(B.MS_KERN_POINT, 0), (B.MS_KERN_TILE, 32), (B.MS_KERN_TILE, 16)] + \
-        [(B.MS_KERN_CHUNK, c) for c in (32, 16, 8, 4)]
-    return [(p, k, c) for p in (B.MS_MOL_FUSED, B.MS_MOL_STREAMING) for k, c in kc]
+    """(layout, kernel, chunk, grid): the tiled kernel at both tile widths and
+    three grids (as many CTAs as fit, one per SM, one per molecule)."""
+    kc = [(B.MS_KERN_POINT, 0, 0)] + [(B.MS_KERN_TILE, t, g) for t in (32, 16) for g in (0, 1, -1)] + \
+        [(B.MS_KERN_CHUNK, c, 0) for c in (32, 16, 8, 4)]
+    return [(p, k, c, g) for p in (B.MS_MOL_FUSED, B.MS_MOL_STREAMING) for k, c, g in kc]
 
 
 @pytest.mark.parametrize("nr,jmax,nmol", [(64, 1, 23), (128, 4, 9), (128, 6, 5), (64, 8, 4)])
@@ -39,6 +41,7 @@ def test_every_plan_matches_oracle(B, nr, jmax, nmol):
     Po = o.populations()
     assert Po[:, 1].max() > 1e-6
     ran = []
+    results = {}
     for plan in _plans(B):
         sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, mol_path=B.MS_MOL_STREAMING)
         try:
@@ -47,22 +50,29 @@ def test_every_plan_matches_oracle(B, nr, jmax, nmol):
             assert e.code == B.MS_EINVAL
             sim.close()
             continue
-        assert sim.plan(0) == plan
+        assert sim.plan_ex(0) == plan
         sim.set_prescribed(amp, wave)
         sim.step(nsteps)
         P, mu = sim.populations(), sim.dipoles()
         sim.close()
+        results[plan] = (P, mu)
         assert np.abs(P - Po).max() < 1e-5, plan
         sel = Po[:, 1] > 1e-10
         assert np.max(np.abs(P[sel, 1] - Po[sel, 1]) / Po[sel, 1]) < 1e-3, plan
         assert np.abs(mu - o.mu).max() < 1e-4 * np.abs(o.mu).max(), plan
         ran.append(plan)
-    kinds = {k for _, k, _ in ran}
+    kinds = {k for _, k, _, _ in ran}
     assert B.MS_KERN_CHUNK in kinds and len(ran) >= 3, ran
     if jmax <= 4:
         assert B.MS_KERN_POINT in kinds
-    tiles = {c for _, k, c in ran if k == B.MS_KERN_TILE}
+    tiles = {c for _, k, c, _ in ran if k == B.MS_KERN_TILE}
     assert tiles == {16, 32}, ran          # both tile widths, J <= 8
+    # the grid only changes which CTA runs a molecule: identical results
+    for t in (16, 32):
+        runs = [results[p] for p in ran if p[1] == B.MS_KERN_TILE and p[2] == t]
+        assert len(runs) == 3
+        for P, mu in runs[1:]:
+            assert np.array_equal(P, runs[0][0]) and np.array_equal(mu, runs[0][1])
 
 
 def test_autotuned_three_species_coupled(B):
@@ -72,7 +82,7 @@ def test_autotuned_three_species_coupled(B):
     wl = W.custom("tuned", 16, 16, 48, src_k=14, pulses=[[2e10, 1.5498, 2e-15, 2e-15]], layer=(22, 26),
                   n_per_sim=120, species=species, fractions=[0.4, 0.3, 0.3], seed=31, nsteps=300)
     a = B.Simulation(wl, autotune=B.MS_TUNE_MEASURE)
-    plans = [a.plan(s) for s in range(3)]
+    plans = [a.plan_ex(s) for s in range(3)]
     print("tuned plans", plans)
     a.step(wl.nsteps)
     got = (a.populations(), a.dipoles(), a.fields(B.MS_FIELD_E))
@@ -99,6 +109,7 @@ def test_plan_validation(B):
                 (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 0),     # J = 9: no tile kernel
                 (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 16),
                 (B.MS_MOL_STREAMING, B.MS_KERN_CHUNK, 12),   # not a chunk width
+                (B.MS_MOL_STREAMING, B.MS_KERN_CHUNK, 8, 1),  # a grid for a kernel that has none
                 (7, B.MS_KERN_CHUNK, 8)):
         with pytest.raises(B.MSError) as e:
             sim.set_plan(0, *bad)

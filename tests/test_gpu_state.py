@@ -4,6 +4,8 @@ The coupled step has no atomics (the polarization scatter is a CSR segmented
 sum, the molecular reductions run in a fixed order), so repeated runs, a
 resumed run and a replayed molecular run are compared bit for bit.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -207,3 +209,52 @@ def test_graph_replay_prescribed_recaptures_after_new_drive(B):
         sim.close()
         return out
     _assert_identical(run(True), run(False))
+
+
+_C = ctypes
+
+
+class _CkHeader(ctypes.Structure):
+    """The checkpoint header of csrc/ms_api.cu (version 4), for reading a
+    saved state on the host."""
+    _fields_ = [("magic", _C.c_char * 8), ("version", _C.c_uint32), ("drive", _C.c_uint32),
+                ("steps", _C.c_int64), ("nx", _C.c_int32), ("ny", _C.c_int32), ("nz", _C.c_int32),
+                ("nsim", _C.c_int32), ("nmol", _C.c_int64), ("nspecies", _C.c_int32), ("pml", _C.c_int32),
+                ("ks", _C.c_int32), ("jk0", _C.c_int32), ("jk1", _C.c_int32), ("aux_len", _C.c_int32),
+                ("ndet", _C.c_int32), ("nfreq", _C.c_int32), ("state_rows", _C.c_int32 * 8),
+                ("mol_substeps", _C.c_int32), ("src_kind", _C.c_int32), ("species", _C.c_int32 * 24),
+                ("nblobs", _C.c_uint64)]
+
+
+def test_population_sums_equal_fp64_sums_of_the_state(B, tmp_path):
+    """The per-molecule populations come from compensated FP32 sums over each
+    molecule's state (FP64 at the store).  Read the state itself from a
+    checkpoint and sum |s|^2 dR in FP64 on the host: the two agree to 1e-12
+    relative, so the compensated sums stand in for FP64 accumulation."""
+    sp = W.Species(nr=128, jmax=4, A=0.05)
+    n = 40
+    wl = W.custom("fp64 sums", 8, 8, 48, n_per_sim=n, species=[sp], layer=(20, 24), seed=17, nsteps=300)
+    amp, wave = W.prescribed_drive(n, 300, wl.dt, E0=3e10, carrier_ev=6.0, fwhm=0.5e-15, t0=0.5e-15)
+    for path in (B.MS_MOL_FUSED, B.MS_MOL_STREAMING):
+        sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, mol_path=path)
+        sim.set_prescribed(amp, wave)
+        sim.step(300)
+        P = sim.populations()
+        ck = str(tmp_path / f"state{path}.ck")
+        sim.save(ck)
+        sim.close()
+        raw = open(ck, "rb").read()
+        h = _CkHeader.from_buffer_copy(raw)
+        assert h.version == 4 and h.nspecies == 1 and h.nmol == n
+        off = ctypes.sizeof(_CkHeader)
+        nb = int(np.frombuffer(raw, np.uint64, 1, off)[0])        # first blob: the species' state
+        rows = 2 * sp.nrot
+        assert nb == n * rows * sp.nr * 8
+        psi = np.frombuffer(raw, np.complex64, n * rows * sp.nr, off + 8).reshape(n, 2, sp.nrot, sp.nr)
+        dR = np.float32((sp.rmax - sp.rmin) / (sp.nr - 1))       # the kernels' FP32 grid step
+        P64 = (np.abs(psi.astype(np.complex128)) ** 2).sum(axis=(2, 3)) * np.float64(dR)
+        # molecule order: the state is stored by species, in molecule-id order within it
+        rel = np.abs(P - P64) / np.maximum(P64, 1e-300)
+        print(f"layout {path}: populations vs FP64 sums of the state, max rel {rel.max():.2e}")
+        assert P[:, 1].max() > 1e-6
+        assert rel.max() < 1e-12
