@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
     }
     // d1 = (V - 1) u + V^{1/2} D S_r ; mask ; s' = s + (d2 + d1) + cfix s
     const float mk = bM[rl].x;
-    float sg = 0.f, se = 0.f, agf = 0.f, aef = 0.f;
+    float agf = 0.f, aef = 0.f;
 #pragma unroll
     for (int i = 0; i < MAXR; ++i) {
       const int row = row0 + i * rstep;
@@ -629,11 +629,10 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
         gs[(long long)row * NR + r] = sn;
         bY[row * CH + rl] = sn;
         const float b2 = fmaf(sn.x, sn.x, sn.y * sn.y);
-        if (sf == 0) sg += b2; else se += b2;
+        if (sf == 0) acc2(a_hi[0], a_lo[0], b2);  // compensated from the first term on
+        else acc2(a_hi[1], a_lo[1], b2);
       }
     }
-    acc2(a_hi[0], a_lo[0], sg);
-    acc2(a_hi[1], a_lo[1], se);
     acc2(a_hi[2], a_lo[2], agf);
     acc2(a_hi[3], a_lo[3], aef);
     __syncthreads();
@@ -1009,7 +1008,6 @@ __global__ void __launch_bounds__(RsDims<J, TILE>::NT, RsDims<J, TILE>::MINB)
       // ---- d1 = (V - 1) u + V^{1/2} e^{-i m phi} S ; mask ; s' = s + (d2 + d1) + cfix s
       const int sbo = (nterms & 1) * TBB;  // s' buffer: not read by the last term
       float2* gsw = gs + (long long)(RPL * w + half) * NR + ck * TILE + pt;
-      float sg = 0.f, se = 0.f;
 #pragma unroll
       for (int i = 0; i < RPW; ++i) {
         const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowT);
@@ -1035,10 +1033,9 @@ __global__ void __launch_bounds__(RsDims<J, TILE>::NT, RsDims<J, TILE>::MINB)
         sts2<D::O_TB + G0>(sm, own + sbo + NW * i * SLOT, sn);
         sv[i] = sn;
         const float b2 = fmaf(sn.x, sn.x, sn.y * sn.y);
-        if (gr) sg += b2; else se += b2;
+        if (gr) acc2(p_hi[0], p_lo[0], b2);  // compensated from the first term on
+        else acc2(p_hi[1], p_lo[1], b2);
       }
-      acc2(p_hi[0], p_lo[0], sg);
-      acc2(p_hi[1], p_lo[1], se);
       __syncthreads();
       // ---- dipole in the molecule frame: sum_c conj(g_c) (A e)_c for A = Z, S+, S-
       float2 accP = make_float2(0.f, 0.f), accM = accP, accZ = accP;
@@ -1458,7 +1455,7 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
     if (store) __syncthreads();
   }
   // ---- d1 = (V - 1) u + V^{1/2} S ; mask ; s' = s + (d2 + d1) + cfix s
-  float sn2 = 0.f, absd = 0.f, rnd = 0.f;
+  float sn2 = 0.f, sn2_lo = 0.f, absd = 0.f, rnd = 0.f;  // |s'|^2 compensated from the first term on
   auto update = [&](auto sfc) {
     constexpr int SF = decltype(sfc)::value, NO = L::N(SF);
     // s again (from L2), in two batches each requested in full first; d2 from shared memory
@@ -1485,7 +1482,7 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
       }
       const float2 s1 = round_update(sv, dv + d1, cfix, rnd);
       __stcs(gs + r * NR, s1);
-      sn2 += fmaf(s1.x, s1.x, s1.y * s1.y);
+      acc2(sn2, sn2_lo, fmaf(s1.x, s1.x, s1.y * s1.y));
       sacc[r] = s1;  // the new state of this surface, kept for the dipole
       Xo[r * NR] = s1;
     });
@@ -1511,7 +1508,7 @@ __global__ void __launch_bounds__(2 * NR, NR <= 64 ? 4 : (NR <= 128 ? (PAR ? 3 :
   // ---- block reduction: populations compensated, the rest plain FP32
   {
     float v[8] = {sf ? 0.f : sn2, sf ? sn2 : 0.f, sf ? 0.f : absd, sf ? absd : 0.f, dP, dQ, dZ, rnd};
-    float lo[2] = {0.f, 0.f};
+    float lo[2] = {sf ? 0.f : sn2_lo, sf ? sn2_lo : 0.f};
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
