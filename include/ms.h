@@ -104,9 +104,9 @@ enum { MS_GRAPHS_AUTO = 0, MS_GRAPHS_OFF = 1 };
  * kernel of its R-space pass.  MS_KERN_POINT: one CTA of 2 N_r threads per
  * molecule, thread = (radial point, surface) (J <= 4; fused at N_r 128).
  * MS_KERN_TILE: persistent CTAs that each walk a share of the molecules, one
- * molecule at a time over tiles of `chunk` = 32 or 16 radial points of all
- * rows, staged by tensor copies (J <= 8, streaming; chunk 0: 16 from J = 5 on,
- * else 32).  MS_KERN_CHUNK: one CTA per molecule over chunks of `chunk`
+ * molecule at a time over tiles of `chunk` radial points of all rows, staged
+ * by tensor copies (streaming; chunk 32 or 16 for J <= 8, 8 for J 9..16;
+ * chunk 0: 8 from J = 9 on, 16 from J = 5 on, else 32).  MS_KERN_CHUNK: one CTA per molecule over chunks of `chunk`
  * radial points (4, 8, 16 or 32) of all rows (any J).  MS_KERN_DEFAULT: the
  * static rule (the first that applies of point, tile, chunk at the widest
  * fitting chunk).  Parity-reduced and d(R) species run

@@ -747,12 +747,14 @@ cudaError_t upload_triplet_tables(const CouplEntry* dip) {
 constexpr int kTriGuard = 3;  // zero rows ahead of each term buffer
 
 // Tensor maps of one species for the tiled R-space kernel: 8-byte elements
-// (one complex FP32 value), boxes of TILE radial points by all rows of a
-// molecule.
+// (one complex FP32 value), boxes of TILE radial points by the rows of a
+// molecule, at most 256 rows a box (a box dimension's limit): a molecule's
+// rows arrive as full boxes (s, d2) and one remainder box (s_r, d2_r).
 struct RspaceMaps {
-  CUtensorMap s, d2;  // [n_mol * rows][nr], box TILE x rows
-  CUtensorMap vd, vh; // [2 (J + 1)][nr], box TILE x 2 (J + 1)
-  CUtensorMap mk;     // [1][nr], box TILE x 1
+  CUtensorMap s, d2;      // [n_mol * rows][nr], box TILE x min(rows, 256)
+  CUtensorMap s_r, d2_r;  // same arrays, box TILE x the remainder rows (rows > 256 only)
+  CUtensorMap vd, vh;     // [2 (J + 1)][nr], box TILE x 2 (J + 1)
+  CUtensorMap mk;         // [1][nr], box TILE x 1
 };
 
 // One row of the tiled kernel's row table (built per molecule).
@@ -800,31 +802,44 @@ cudaError_t launch_wait_timeout_probe(int tries, int* flag, cudaStream_t s) {
 }
 
 // Layout of the tiled R-space kernel for basis size J and tile width TILE
-// (32 or 16 radial points).  A warp covers RPL = 32 / TILE rows of one tile
-// (lane = half * TILE + point, half = lane / TILE), so NW = 2 (J + 1) / RPL
-// warps of RPW = J + 1 row slots cover the 2 (J + 1)^2 rows exactly: warp w
-// owns rows RPL (w + NW i) + half.  Every row index, buffer offset and stride
-// is known at compile time.  A row of a tile is SEG = 8 TILE bytes; the two
-// rows of a 16-point slot are contiguous, so a warp's 32 lanes always read 256
-// contiguous bytes.  Shared memory, from a 128-byte aligned base:
-//   [2 ROWS] s and d2 of the tile, [2][NV] e^{-iV dtau} - 1, [2][NV]
+// (32, 16 or 8 radial points).  A warp covers RPL = 32 / TILE rows of one tile
+// (lane = part * TILE + point, part = lane / TILE) and NW warps of RPW row
+// slots each cover the 2 (J + 1)^2 rows: warp w owns rows RPL (w + NW i) +
+// part.  Up to J = 8 (tiles of 32 or 16) RPW = J + 1 and the rows split
+// exactly, so every row index, buffer offset and stride is known at compile
+// time.  From J = 9 on (tiles of 8, 578 rows at J = 16) RPW = 6 and the last
+// slots run past the rows: those padded rows stay zero, their row-table
+// entries point at the zero guard rows, and they are neither summed nor
+// written.  A row of a tile is SEG = 8 TILE bytes; the RPL rows of a slot
+// are contiguous, so a warp's 32 lanes always read 256 contiguous bytes.
+// Shared memory, from a 128-byte aligned base:
+//   [2 RP] s and d2 of the tile, [2][NV] e^{-iV dtau} - 1, [2][NV]
 //   e^{-iV dtau/2} (double buffered), [1] mask, two term buffers of
-//   kTriGuard + ROWS rows, the row table of the molecule.
+//   kTriGuard + RP rows, the row table of the molecule (RP = padded rows).
 // With 16-point tiles the J = 8 kernel needs 109 KB, so two CTAs share an SM
-// and one's barriers and copies overlap the other's arithmetic.
+// and one's barriers and copies overlap the other's arithmetic; the J = 16
+// kernel needs 211 KB at 800 threads.
 template <int J, int TILE>
 struct RsDims {
   static constexpr int NROT = (J + 1) * (J + 1), ROWS = 2 * NROT, NV = 2 * (J + 1);
   static constexpr int RPL = 32 / TILE;
-  static constexpr int NW = 2 * (J + 1) / RPL, RPW = J + 1, NT = 32 * NW;
+  static constexpr int RPW = TILE == 8 ? 6 : J + 1;
+  static constexpr int NW = ((ROWS + RPL - 1) / RPL + RPW - 1) / RPW, NT = 32 * NW;
+  static constexpr int RP = NW * RPW * RPL;  // rows with padding
+  static constexpr bool EXACT = RP == ROWS;
   static constexpr int SEG = TILE * (int)sizeof(float2);
-  static constexpr int TBB = (kTriGuard + ROWS) * SEG;  // bytes of a term buffer
-  static constexpr int O_STG = 0, O_VD = O_STG + 2 * ROWS * SEG, O_VH = O_VD + 2 * NV * SEG;
-  static constexpr int O_MK = O_VH + 2 * NV * SEG, O_TB = O_MK + SEG, O_RT = O_TB + 2 * TBB;
-  static constexpr int BYTES = 128 + O_RT + ROWS * (int)sizeof(RowT);
+  static constexpr int BOXR = ROWS < 256 ? ROWS : 256, NBOX = (ROWS + BOXR - 1) / BOXR;
+  static constexpr int LASTR = ROWS - (NBOX - 1) * BOXR;  // rows of the last box
+  static constexpr int TBB = (kTriGuard + RP) * SEG;      // bytes of a term buffer
+  static constexpr int O_STG = 0, O_VD = O_STG + 2 * RP * SEG, O_VH = O_VD + 2 * NV * SEG;
+  static constexpr int O_MK = O_VH + 2 * NV * SEG, O_TB = O_MK + (SEG < 128 ? 128 : SEG), O_RT = O_TB + 2 * TBB;
+  static constexpr int BYTES = 128 + O_RT + RP * (int)sizeof(RowT);
   static constexpr int MINB = TILE == 16 ? 2 : (J <= 4 ? 3 : 1);
-  static_assert(TILE == 16 || TILE == 32, "tile of 16 or 32 radial points");
-  static_assert(2 * (J + 1) % RPL == 0, "rows split evenly over the warps");
+  static_assert(TILE == 8 || TILE == 16 || TILE == 32, "tile of 8, 16 or 32 radial points");
+  static_assert(TILE == 8 || 2 * (J + 1) % RPL == 0, "rows split evenly over the warps");
+  static_assert(NT <= 1024 && BYTES <= 227 * 1024, "one CTA per molecule fits");
+  static_assert((RP * SEG) % 128 == 0 && (NV * SEG) % 128 == 0 && (BOXR * SEG) % 128 == 0,
+                "tensor-copy destinations 128-byte aligned");
 };
 
 template <int OFF>
@@ -866,13 +881,19 @@ __global__ void __launch_bounds__(RsDims<J, TILE>::NT, RsDims<J, TILE>::MINB)
   auto issue = [&](int mol, int ck) {
     const int r0 = ck * TILE, b = ck & 1;
     unsigned char* base = sm + pad;
-    tensor2d_g2s(base + D::O_STG, &maps.s, r0, mol * ROWS, &s_bar[0]);
-    tensor2d_g2s(base + D::O_STG + ROWS * SEG, &maps.d2, r0, mol * ROWS, &s_bar[0]);
+#pragma unroll
+    for (int k = 0; k < D::NBOX; ++k) {  // the molecule's rows, in boxes of at most 256
+      const bool last = k == D::NBOX - 1 && D::NBOX > 1;
+      tensor2d_g2s(base + D::O_STG + k * D::BOXR * SEG, last ? &maps.s_r : &maps.s, r0, mol * ROWS + k * D::BOXR,
+                   &s_bar[0]);
+      tensor2d_g2s(base + D::O_STG + (D::RP + k * D::BOXR) * SEG, last ? &maps.d2_r : &maps.d2, r0,
+                   mol * ROWS + k * D::BOXR, &s_bar[0]);
+    }
     tensor2d_g2s(base + D::O_VD + b * NV * SEG, &maps.vd, r0, 0, &s_bar[0]);
     tensor2d_g2s(base + D::O_VH + b * NV * SEG, &maps.vh, r0, 0, &s_bar[0]);
     tensor2d_g2s(base + D::O_MK, &maps.mk, r0, 0, &s_bar[0]);
   };
-  constexpr unsigned kChunkBytes = (2 * ROWS + 2 * NV + 1) * SEG;
+  constexpr unsigned kChunkBytes = (2 * ROWS + 2 * NV + 1) * SEG;  // what the copies of one tile deliver
   const int nchunks = NR / TILE;  // even: NR is 64, 128 or 256
 
   int lm = blockIdx.x;
@@ -886,8 +907,15 @@ __global__ void __launch_bounds__(RsDims<J, TILE>::NT, RsDims<J, TILE>::MINB)
     reinterpret_cast<float2*>(sm + pad + D::O_TB)[q] = make_float2(0.f, 0.f);
     reinterpret_cast<float2*>(sm + pad + D::O_TB + TBB)[q] = make_float2(0.f, 0.f);
   }
-  // ground rows: q = RPL (w + NW i) + half < NROT
+  if constexpr (!D::EXACT) {  // padded staging rows: zero, and never written by the copies
+    for (int q = t; q < (D::RP - ROWS) * TILE; q += NT) {
+      reinterpret_cast<float2*>(sm + pad + D::O_STG + ROWS * SEG)[q] = make_float2(0.f, 0.f);
+      reinterpret_cast<float2*>(sm + pad + D::O_STG + (D::RP + ROWS) * SEG)[q] = make_float2(0.f, 0.f);
+    }
+  }
+  // ground rows: q = RPL (w + NW i) + part < NROT; rows past ROWS are padding
   auto ground = [&](int i) { return RPL * (w + NW * i) + half < NROT; };
+  auto valid = [&](int i) { return D::EXACT || RPL * (w + NW * i) + half < ROWS; };
 
   for (; lm < sp.nmol; lm += gridDim.x) {
     const int m = sp.mol[lm];
@@ -912,7 +940,17 @@ __global__ void __launch_bounds__(RsDims<J, TILE>::NT, RsDims<J, TILE>::MINB)
     }
     const float cfix = md.ncorr[m];  // rounding feedback of the previous step
     __syncthreads();
-    for (int q = t; q < ROWS; q += NT) {  // the row table of this molecule
+    for (int q = t; q < D::RP; q += NT) {  // the row table of this molecule (padding: zero, guard rows)
+      if (!D::EXACT && q >= ROWS) {
+        RowT r;
+        r.cu = r.cd = r.du = r.dd = make_float4(0.f, 0.f, 0.f, 0.f);
+        r.ph = make_float2(1.f, 0.f);
+        r.ou = r.od = D::O_TB;
+        r.vo = 0;
+        r.pad = 0;
+        *reinterpret_cast<RowT*>(sm + pad + D::O_RT + q * (int)sizeof(RowT)) = r;
+        continue;
+      }
       // theta E_perp / 2 on the X runs and theta E'_z on the Z runs (frame turned so E'_y = 0)
       const float ep = sqrtf(f.y * f.y + f.z * f.z), ez = f.x;
       const int sf = q >= NROT, c = q - sf * NROT, j = j_of(c), mm = c - j * j - j;
@@ -981,7 +1019,7 @@ __global__ void __launch_bounds__(RsDims<J, TILE>::NT, RsDims<J, TILE>::MINB)
 #pragma unroll
       for (int i = 0; i < RPW; ++i) {
         sv[i] = lds2<D::O_STG>(sm, own + NW * i * SLOT);
-        dv[i] = lds2<D::O_STG + ROWS * SEG>(sm, own + NW * i * SLOT);
+        dv[i] = lds2<D::O_STG + D::RP * SEG>(sm, own + NW * i * SLOT);
         sacc[i] = make_float2(0.f, 0.f);
         if (nterms > 0) {
           const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowT);
@@ -1029,7 +1067,7 @@ __global__ void __launch_bounds__(RsDims<J, TILE>::NT, RsDims<J, TILE>::MINB)
           if (gr) a_gf += dd; else a_ef += dd;
         }
         const float2 sn = round_update(sv[i], dv[i] + d1, cfix, rnd);
-        gsw[(long long)(RPL * NW * i) * NR] = sn;
+        if (valid(i)) gsw[(long long)(RPL * NW * i) * NR] = sn;  // padded rows: zero, not stored
         sts2<D::O_TB + G0>(sm, own + sbo + NW * i * SLOT, sn);
         sv[i] = sn;
         const float b2 = fmaf(sn.x, sn.x, sn.y * sn.y);
@@ -1891,8 +1929,9 @@ static StepShape step_shape_ch(int nr, int nrot, bool fused, int ch) {
 // The tiled R-space kernel covers J <= 8 (rows <= 162) at tile widths of 32
 // and 16 radial points (N_r 64, 128 and 256 hold an even number of tiles).
 // Its static rule: 16-point tiles from J = 5 on (two CTAs per SM), else 32.
-static bool rspace_ok(int nr, int jmax) { return (nr == 64 || nr == 128 || nr == 256) && jmax <= 8; }
+static bool rspace_ok(int nr, int jmax) { return (nr == 64 || nr == 128 || nr == 256) && jmax <= 16; }
 static int rspace_tile(const SpeciesDev& sp) {
+  if (sp.jmax >= 9) return 8;
   if (sp.kern == MS_KERN_TILE && (sp.ch == 16 || sp.ch == 32)) return sp.ch;
   return sp.jmax >= 5 ? 16 : 32;
 }
@@ -1919,8 +1958,12 @@ int mol_plan_candidates(const SpeciesDev& sp, int (*out)[4], int max) {
   }
   if (sp.jmax <= 4) add(MS_MOL_STREAMING, MS_KERN_POINT, 0);
   if (rspace_ok(sp.nr, sp.jmax)) {  // tile width x grid: as many CTAs as fit, one per SM, one per molecule
-    for (int tile : {32, 16})
-      for (int cps : {0, 1, -1}) add(MS_MOL_STREAMING, MS_KERN_TILE, tile, cps);
+    if (sp.jmax >= 9) {
+      for (int cps : {0, -1}) add(MS_MOL_STREAMING, MS_KERN_TILE, 8, cps);
+    } else {
+      for (int tile : {32, 16})
+        for (int cps : {0, 1, -1}) add(MS_MOL_STREAMING, MS_KERN_TILE, tile, cps);
+    }
   }
   for (int ch : {32, 16, 8, 4})
     if (step_shape_ch(sp.nr, sp.nrot, false, ch).ok) add(MS_MOL_STREAMING, MS_KERN_CHUNK, ch);
@@ -1951,8 +1994,12 @@ static void launch_rspace_jt(const SpeciesDev& sp, const MolDev& md, int* err, c
 template <int J>
 static void launch_rspace_j(const SpeciesDev& sp, const MolDev& md, int* err, const RspaceMaps& maps,
                             int tile, cudaStream_t s) {
-  if (tile == 16) launch_rspace_jt<J, 16>(sp, md, err, maps, s);
-  else launch_rspace_jt<J, 32>(sp, md, err, maps, s);
+  if constexpr (J >= 9) {
+    launch_rspace_jt<J, 8>(sp, md, err, maps, s);
+  } else {
+    if (tile == 16) launch_rspace_jt<J, 16>(sp, md, err, maps, s);
+    else launch_rspace_jt<J, 32>(sp, md, err, maps, s);
+  }
 }
 
 static void launch_rspace(const SpeciesDev& sp, const MolDev& md, int* err, const RspaceMaps& maps, int tile,
@@ -1967,6 +2014,14 @@ static void launch_rspace(const SpeciesDev& sp, const MolDev& md, int* err, cons
     case 6: launch_rspace_j<6>(sp, md, err, maps, tile, s); break;
     case 7: launch_rspace_j<7>(sp, md, err, maps, tile, s); break;
     case 8: launch_rspace_j<8>(sp, md, err, maps, tile, s); break;
+    case 9: launch_rspace_j<9>(sp, md, err, maps, tile, s); break;
+    case 10: launch_rspace_j<10>(sp, md, err, maps, tile, s); break;
+    case 11: launch_rspace_j<11>(sp, md, err, maps, tile, s); break;
+    case 12: launch_rspace_j<12>(sp, md, err, maps, tile, s); break;
+    case 13: launch_rspace_j<13>(sp, md, err, maps, tile, s); break;
+    case 14: launch_rspace_j<14>(sp, md, err, maps, tile, s); break;
+    case 15: launch_rspace_j<15>(sp, md, err, maps, tile, s); break;
+    case 16: launch_rspace_j<16>(sp, md, err, maps, tile, s); break;
   }
 }
 
@@ -2020,9 +2075,11 @@ static bool rspace_maps(const SpeciesDev& sp, int tile, RspaceMaps* out) {
     }
   Entry e{sp.psi, sp.d2, sp.vdelta, sp.vhalf, sp.maskw, sp.nmol, sp.nr, sp.nrot, tile, {}};
   const unsigned rows = 2 * sp.nrot, nv = 2 * (sp.jmax + 1);
-  const unsigned long long nr = sp.nr;
-  if (!encode_rows(&e.maps.s, sp.psi, nr, (unsigned long long)sp.nmol * rows, rows, tile) ||
-      !encode_rows(&e.maps.d2, sp.d2, nr, (unsigned long long)sp.nmol * rows, rows, tile) ||
+  const unsigned boxr = rows < 256 ? rows : 256, lastr = rows - (rows + boxr - 1) / boxr * boxr + boxr;
+  const unsigned long long nr = sp.nr, nrows = (unsigned long long)sp.nmol * rows;
+  if (!encode_rows(&e.maps.s, sp.psi, nr, nrows, boxr, tile) || !encode_rows(&e.maps.d2, sp.d2, nr, nrows, boxr, tile) ||
+      !encode_rows(&e.maps.s_r, sp.psi, nr, nrows, lastr, tile) ||
+      !encode_rows(&e.maps.d2_r, sp.d2, nr, nrows, lastr, tile) ||
       !encode_rows(&e.maps.vd, sp.vdelta, nr, nv, nv, tile) || !encode_rows(&e.maps.vh, sp.vhalf, nr, nv, nv, tile) ||
       !encode_rows(&e.maps.mk, sp.maskw, nr, 1, 1, tile))
     return false;

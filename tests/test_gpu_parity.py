@@ -92,7 +92,7 @@ def test_periodic_z_ragged_tiles_match_oracle(B, nx, ny, nz, nsim):
 @pytest.mark.parametrize("nr,jmax,nmol,path", [
     (64, 1, 37, "fused"), (64, 1, 37, "streaming"), (128, 4, 19, "fused"), (128, 4, 19, "streaming"),
     (64, 8, 9, "fused"), (64, 8, 9, "streaming"), (256, 2, 5, "streaming"), (128, 8, 4, "streaming"),
-    (256, 12, 2, "streaming"), (64, 3, 11, "streaming"), (128, 6, 5, "streaming"),
+    (256, 12, 2, "streaming"), (64, 3, 11, "streaming"), (128, 6, 5, "streaming"), (256, 16, 1, "streaming"),
 ])
 def test_prescribed_molecules_match_oracle(B, nr, jmax, nmol, path):
     sp = W.Species(nr=nr, jmax=jmax, A=0.05)       # nearer resonance: visible P_e

@@ -26,12 +26,12 @@ def B():
 def _plans(B):
     """(layout, kernel, chunk, grid): the tiled kernel at both tile widths and
     three grids (as many CTAs as fit, one per SM, one per molecule)."""
-    kc = [(B.MS_KERN_POINT, 0, 0)] + [(B.MS_KERN_TILE, t, g) for t in (32, 16) for g in (0, 1, -1)] + \
+    kc = [(B.MS_KERN_POINT, 0, 0)] + [(B.MS_KERN_TILE, t, g) for t in (32, 16, 8) for g in (0, 1, -1)] + \
         [(B.MS_KERN_CHUNK, c, 0) for c in (32, 16, 8, 4)]
     return [(p, k, c, g) for p in (B.MS_MOL_FUSED, B.MS_MOL_STREAMING) for k, c, g in kc]
 
 
-@pytest.mark.parametrize("nr,jmax,nmol", [(64, 1, 23), (128, 4, 9), (128, 6, 5), (64, 8, 4)])
+@pytest.mark.parametrize("nr,jmax,nmol", [(64, 1, 23), (128, 4, 9), (128, 6, 5), (64, 8, 4), (64, 10, 3)])
 def test_every_plan_matches_oracle(B, nr, jmax, nmol):
     sp = W.Species(nr=nr, jmax=jmax, A=0.05)
     nsteps = 200
@@ -66,9 +66,9 @@ def test_every_plan_matches_oracle(B, nr, jmax, nmol):
     if jmax <= 4:
         assert B.MS_KERN_POINT in kinds
     tiles = {c for _, k, c, _ in ran if k == B.MS_KERN_TILE}
-    assert tiles == {16, 32}, ran          # both tile widths, J <= 8
+    assert tiles == ({8} if jmax >= 9 else {16, 32}), ran   # the tile widths of the basis size
     # the grid only changes which CTA runs a molecule: identical results
-    for t in (16, 32):
+    for t in tiles:
         runs = [results[p] for p in ran if p[1] == B.MS_KERN_TILE and p[2] == t]
         assert len(runs) == 3
         for P, mu in runs[1:]:
@@ -106,7 +106,7 @@ def test_plan_validation(B):
                   nsteps=10)
     sim = B.Simulation(wl)
     for bad in ((B.MS_MOL_STREAMING, B.MS_KERN_POINT, 0),    # J = 9: no point-resident kernel
-                (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 0),     # J = 9: no tile kernel
+                (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 32),    # J = 9: tiles of 8 points only
                 (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 16),
                 (B.MS_MOL_STREAMING, B.MS_KERN_CHUNK, 12),   # not a chunk width
                 (B.MS_MOL_STREAMING, B.MS_KERN_CHUNK, 8, 1),  # a grid for a kernel that has none
@@ -117,3 +117,26 @@ def test_plan_validation(B):
     sim.set_plan(0, B.MS_MOL_STREAMING, B.MS_KERN_DEFAULT, 0)
     sim.step(2)
     sim.close()
+
+
+@pytest.mark.parametrize("nr,jmax,nmol", [(64, 6, 7), (128, 8, 5), (64, 10, 3)])
+def test_tiled_plans_are_deterministic(B, nr, jmax, nmol):
+    """Every tile width and grid of the tiled kernel, run twice from the same
+    start: identical results bit for bit (the kernel's shared-memory regions,
+    its tensor copies and the prefetch of the next molecule must not race)."""
+    sp = W.Species(nr=nr, jmax=jmax, A=0.05)
+    wl = W.custom("tiled determinism", 8, 8, 48, n_per_sim=nmol, species=[sp], layer=(20, 24),
+                  seed=nr + jmax, nsteps=120)
+    amp, wave = W.prescribed_drive(nmol, 120, wl.dt, E0=3e10, carrier_ev=6.0, fwhm=0.5e-15, t0=0.4e-15)
+    tiles = (8,) if jmax >= 9 else (32, 16)
+    for t in tiles:
+        for g in (0, 1, -1):
+            runs = []
+            for _ in range(2):
+                sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, mol_path=B.MS_MOL_STREAMING)
+                sim.set_plan(0, B.MS_MOL_STREAMING, B.MS_KERN_TILE, t, g)
+                sim.set_prescribed(amp, wave)
+                sim.step(wl.nsteps)
+                runs.append((sim.populations(), sim.dipoles()))
+                sim.close()
+            assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1]), (t, g)
