@@ -59,6 +59,12 @@ def _args(argv=None):
                         "configuration's own pulse (peak at 40 fs) on a reduced copy of --sweep-molecules per cell, "
                         "and add the dissociation yield and Eq. 8's <R>_e per carrier to the line")
     p.add_argument("--sweep-molecules", type=int, default=2000)
+    p.add_argument("--batches", type=int, default=0,
+                   help="pipelined molecular step: runs per species (ms_set_mol_batches; 0 = stages in sequence)")
+    p.add_argument("--plan", default=None, metavar="KERNEL:CHUNK[:CTAS][,...]",
+                   help="pin the species' R-space plans in the streaming layout (tile, pair or chunk), e.g. "
+                        "pair:16 for every species or keep,pair:16,pair:8 per species (keep: the library's "
+                        "rule); default: the library's rule")
     p.add_argument("--oracle-sample", default=None, help=argparse.SUPPRESS)
     return p.parse_args(argv)
 
@@ -368,11 +374,26 @@ def main():
     path = {"auto": B.MS_MOL_AUTO, "fused": B.MS_MOL_FUSED, "streaming": B.MS_MOL_STREAMING}[a.mol_path]
     preroll = peak_preroll(wl, a.warmup, a.steps) if a.preroll is None else a.preroll
 
-    def time_form(w, mol_path, precision, pre, clocks=False, state_form=0, detectors=None, tune=False):
+    def pin(sim, w):
+        """--plan: a streaming plan for every species, or one per species."""
+        if a.plan:
+            specs = a.plan.split(",")
+            for i in range(len(w.species)):
+                f = (specs[i] if len(specs) > 1 else specs[0]).split(":")
+                if f[0] == "keep":
+                    continue
+                kern = {"tile": B.MS_KERN_TILE, "pair": B.MS_KERN_PAIR, "chunk": B.MS_KERN_CHUNK}[f[0]]
+                sim.set_plan(i, B.MS_MOL_STREAMING, kern, int(f[1]), int(f[2]) if len(f) > 2 else 0)
+
+    def time_form(w, mol_path, precision, pre, clocks=False, state_form=0, detectors=None, tune=False,
+                  pinned=False):
         """Preroll, warm-up, then a.steps timed steps of one form (CUDA events on
         the library's stream, max over ranks) and its phase timings."""
         sim = B.Simulation(w, mol_path=mol_path, precision=precision, state_form=state_form,
                            autotune=B.MS_TUNE_MEASURE if tune else B.MS_TUNE_OFF)
+        if pinned:
+            pin(sim, w)
+            sim.set_batches(a.batches)
         plans = [sim.plan_ex(i) for i in range(len(w.species))]
         if detectors is not None:
             sim.set_detectors(*detectors)
@@ -404,7 +425,7 @@ def main():
         return {"ms": ms_, "phases": ph, "nsteps": nst, "launches": nlaunch, "clocks": cl, "P": Pf,
                 "norm_err": nerr, "path": form_path, "plans": plans}
 
-    main_form = time_form(wl, path, B.MS_PREC_FP32, preroll, clocks=True)
+    main_form = time_form(wl, path, B.MS_PREC_FP32, preroll, clocks=True, pinned=True)
     ms, phases, nsteps, launches = main_form["ms"], main_form["phases"], main_form["nsteps"], main_form["launches"]
     cl, P, norm_err = main_form["clocks"], main_form["P"], main_form["norm_err"]
     fused = main_form["path"] == B.MS_MOL_FUSED
@@ -465,8 +486,11 @@ def main():
         rs_bytes = 3 * st_bytes + STATE_RECORDS * wl.n_molecules
         if one and sp.jmax <= 4:
             kernel, traffic_key = f"mol_rpoint_kernel<{sp.jmax},{sp.nr}>", "mol_rpoint_kernel"
+        elif one and main_form["plans"][0][1] in (B.MS_KERN_PAIR, B.MS_KERN_DEFAULT) and sp.jmax >= 5:
+            tile = 8 if sp.jmax >= 9 else (main_form["plans"][0][2] or 16)    # the pair kernel's rule
+            kernel, traffic_key = f"mol_rspace_pair_kernel<{sp.jmax},{tile}>", "mol_rspace_pair_kernel"
         elif one and sp.jmax <= 8:
-            tile = 16 if sp.jmax >= 5 else 32      # the tiled kernel's static rule
+            tile = main_form["plans"][0][2] or (16 if sp.jmax >= 5 else 32)   # the tiled kernel's rule
             kernel, traffic_key = f"mol_rspace_kernel<{sp.jmax},{tile}>", "mol_rspace_kernel"
         else:
             kernel, traffic_key = "R-space passes of every species", None
@@ -503,6 +527,8 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = B.Simulation(wl, mol_path=path)
+        pin(s2, wl)
+        s2.set_batches(a.batches)
         torch.cuda.synchronize()
         t_create = time.perf_counter() - t0
         host_in = (wl.mat_id.nbytes + wl.pos.nbytes + wl.quat.nbytes + wl.species_id.nbytes
@@ -538,6 +564,7 @@ def main():
                                        "molecules_stage2": phases[5] / nsteps},
                 "plans": [{"layout": p[0], "kernel": p[1], "chunk": p[2], "ctas_per_sm": p[3]}
                           for p in main_form["plans"]],
+                "mol_batches": a.batches,
                 "roofline": roof, "roofline_kinetic": roof_kin, "roofline_molecular_step": roof_step,
                 "roofline_fdtd": roof_fdtd,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,

@@ -107,9 +107,14 @@ enum { MS_GRAPHS_AUTO = 0, MS_GRAPHS_OFF = 1 };
  * molecule at a time over tiles of `chunk` radial points of all rows, staged
  * by tensor copies (streaming; chunk 32 or 16 for J <= 8, 8 for J 9..16;
  * chunk 0: 8 from J = 9 on, 16 from J = 5 on, else 32).  MS_KERN_CHUNK: one CTA per molecule over chunks of `chunk`
- * radial points (4, 8, 16 or 32) of all rows (any J).  MS_KERN_DEFAULT: the
- * static rule (the first that applies of point, tile, chunk at the widest
- * fitting chunk).  Parity-reduced and d(R) species run
+ * radial points (4, 8, 16 or 32) of all rows (any J).  MS_KERN_PAIR: the
+ * tiled kernel's schedule with two neighbouring radial points per thread and
+ * packed FP32x2 arithmetic (streaming; chunk 32 or 16 for J <= 4, 16 or 8
+ * for J 5..8, 8 for J 9..16; chunk 0: 8 from J = 9 on, 16 from J = 5 on,
+ * else 32).  MS_KERN_DEFAULT: the
+ * static rule (the first that applies of point for J <= 4, pair from J = 5
+ * on in the streaming layout, tile, chunk at the widest fitting chunk).
+ * Parity-reduced and d(R) species run
  * the point-resident kernel only.  Every plan computes the same step; their
  * results differ by FP32 rounding.
  * Autotuning (ms_options.autotune = MS_TUNE_MEASURE): ms_create times every
@@ -117,7 +122,7 @@ enum { MS_GRAPHS_AUTO = 0, MS_GRAPHS_OFF = 1 };
  * under a strong prescribed field (5e9 V/m, the coupling series' term count
  * of a pulse peak) and keeps the fastest; ms_species_plan reports the choice and
  * ms_set_species_plan pins one, so a tuned choice can be replayed. */
-enum { MS_KERN_DEFAULT = 0, MS_KERN_POINT = 1, MS_KERN_TILE = 2, MS_KERN_CHUNK = 3 };
+enum { MS_KERN_DEFAULT = 0, MS_KERN_POINT = 1, MS_KERN_TILE = 2, MS_KERN_CHUNK = 3, MS_KERN_PAIR = 4 };
 enum { MS_TUNE_OFF = 0, MS_TUNE_MEASURE = 1 };
 
 /* Grid and source.  dt must satisfy dt <= dx/(sqrt(3) c) (checked).
@@ -446,9 +451,30 @@ ms_status ms_species_plan(const ms_sim* sim, int32_t species, int32_t* path, int
  * scratch (MS_ENOMEM if that fails).  Takes effect from the next step. */
 ms_status ms_set_species_plan(ms_sim* sim, int32_t species, int32_t path, int32_t kernel, int32_t chunk);
 
+/* Pipelined molecular step (no counterpart in the paper; a scheduling
+ * choice).  batches = 0 (the default): the molecular step runs stage 1 (the
+ * frame-field records and the kinetic pass) of every species, then stage 2
+ * (the R-space pass) of every species, on the handle's stream.  batches = n
+ * >= 1: every streaming-layout species is cut into n runs of consecutive
+ * molecules (other species: one run each); stage 1 of each run is issued on
+ * the handle's stream and stage 2 of the same run on a second stream after
+ * it, so the kinetic pass of run k + 1 (bound by HBM bandwidth) can execute
+ * while the R-space pass of run k (bound by the SMs' shared-memory pipe)
+ * does; the handle's stream waits for the last run before the E half step.
+ * Runs hold disjoint molecules and every molecule gets the same kernels on
+ * the same data, so results are identical bit for bit for every n.  With
+ * n >= 1 the phase timing (ms_timing_begin) reports the molecular step as a
+ * whole: stage 1's phase then holds all of it and stage 2's is empty.
+ * Takes effect from the next
+ * step.  MS_EINVAL for a NULL handle or batches outside 0..16; MS_ECUDA if
+ * the second stream or its events cannot be created. */
+ms_status ms_set_mol_batches(ms_sim* sim, int32_t batches);
+/* The handle's batches (ms_set_mol_batches); -1 for a NULL handle. */
+int32_t ms_mol_batches(const ms_sim* sim);
+
 /* Extended plan (no counterpart in the paper): plan[0] layout, plan[1]
  * kernel, plan[2] chunk, as for ms_species_plan, and plan[3] the grid of the
- * persistent tiled kernel (MS_KERN_TILE): resident CTAs per SM (1..32, fewer
+ * persistent tiled kernels (MS_KERN_TILE, MS_KERN_PAIR): resident CTAs per SM (1..32, fewer
  * if fewer fit), so each CTA walks about n_molecules / (plan[3] x SMs)
  * molecules; 0 = as many CTAs as fit at once; -1 = one CTA per molecule.
  * Other kernels take plan[3] = 0.  Every grid computes each molecule with the

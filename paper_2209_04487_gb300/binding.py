@@ -25,7 +25,7 @@ MS_STATE_FULL, MS_STATE_PARITY = 0, 1
 MS_SRC_PULSE, MS_SRC_CW = 0, 1
 MS_MODEL_WAVEPACKET, MS_MODEL_BLOCH = 0, 1
 MS_GRAPHS_AUTO, MS_GRAPHS_OFF = 0, 1
-MS_KERN_DEFAULT, MS_KERN_POINT, MS_KERN_TILE, MS_KERN_CHUNK = 0, 1, 2, 3
+MS_KERN_DEFAULT, MS_KERN_POINT, MS_KERN_TILE, MS_KERN_CHUNK, MS_KERN_PAIR = 0, 1, 2, 3, 4
 MS_TUNE_OFF, MS_TUNE_MEASURE = 0, 1
 MS_MOL_AUTO, MS_MOL_FUSED, MS_MOL_STREAMING = 0, 1, 2
 
@@ -95,6 +95,8 @@ def _load() -> C.CDLL:
         "ms_check_bounded_wait": (C.c_int, [C.c_int32]),
         "ms_species_path": (C.c_int32, [C.c_void_p, C.c_int32]),
         "ms_species_plan": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_int32), P(C.c_int32), P(C.c_int32)]),
+        "ms_set_mol_batches": (C.c_int, [C.c_void_p, C.c_int32]),
+        "ms_mol_batches": (C.c_int32, [C.c_void_p]),
         "ms_set_species_plan": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
         "ms_species_plan_ex": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_int32)]),
         "ms_set_species_plan_ex": (C.c_int, [C.c_void_p, C.c_int32, P(C.c_int32)]),
@@ -122,7 +124,8 @@ EXPORTED = ("ms_create", "ms_step", "ms_step_noalloc", "ms_step_count", "ms_read
             "ms_read_populations", "ms_read_dissociation", "ms_read_dipoles",
             "ms_set_prescribed_field", "ms_set_replay_field", "ms_record_local_fields", "ms_save", "ms_load",
             "ms_check_bounded_wait", "ms_species_path", "ms_species_plan", "ms_set_species_plan",
-            "ms_species_plan_ex", "ms_set_species_plan_ex", "ms_set_detectors", "ms_read_flux", "ms_read_dft",
+            "ms_species_plan_ex", "ms_set_species_plan_ex", "ms_set_mol_batches", "ms_mol_batches",
+            "ms_set_detectors", "ms_read_flux", "ms_read_dft",
             "ms_timing_begin", "ms_timing_end", "ms_device_bytes",
             "ms_destroy", "ms_status_string")
 
@@ -362,6 +365,14 @@ class Simulation:
     def set_plan(self, species: int, path: int, kernel: int, chunk: int = 0, ctas_per_sm: int = 0):
         p = (C.c_int32 * 4)(path, kernel, chunk, ctas_per_sm)
         _check(LIB.ms_set_species_plan_ex(self.h, species, p), "ms_set_species_plan_ex")
+
+    def set_batches(self, batches: int):
+        """ms_set_mol_batches: 0 = stages in sequence, n >= 1 = pipelined runs."""
+        _check(LIB.ms_set_mol_batches(self.h, batches), "ms_set_mol_batches")
+
+    @property
+    def batches(self) -> int:
+        return int(LIB.ms_mol_batches(self.h))
 
     def plan_ex(self, species: int = 0):
         """(layout, kernel, chunk width, resident CTAs per SM of the persistent tiled kernel)."""

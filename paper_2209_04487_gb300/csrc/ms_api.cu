@@ -55,6 +55,8 @@ struct Alloc {
 
 }  // namespace
 
+constexpr int kMaxMolBatches = 16;  // runs per species of the pipelined molecular step
+
 struct ms_sim {
   Alloc al;
   std::vector<void*> blocks;
@@ -87,6 +89,11 @@ struct ms_sim {
   bool timing = false;
   std::vector<cudaEvent_t> events;   // 4 per timed step
   int64_t timed_steps = 0, launches = 0;
+  // pipelined molecular step (ms_set_mol_batches): runs per streaming species,
+  // the second stream the R-space passes run on, and the events that order them
+  int batches = 0;
+  cudaStream_t stream2 = nullptr;
+  std::vector<cudaEvent_t> bev;
 
   void* alloc(size_t n) {
     if (n == 0) n = 16;
@@ -109,6 +116,11 @@ struct ms_sim {
     gexec = nullptr;
     for (cudaEvent_t e : events) cudaEventDestroy(e);
     events.clear();
+    if (stream2) cudaStreamSynchronize(stream2);
+    for (cudaEvent_t e : bev) cudaEventDestroy(e);
+    bev.clear();
+    if (stream2) cudaStreamDestroy(stream2);
+    stream2 = nullptr;
     for (void* p : blocks) {
       if (al.fr) al.fr(p, al.ctx);
       else cudaFree(p);
@@ -483,6 +495,21 @@ ms_status build_species(ms_sim* s, int si, const ms_species& d, double dt, const
   MS_TRY(upload(s, (float2**)&sp.khalf, kphi.data(), kphi.size()));
   MS_TRY(upload(s, (float2**)&sp.twiddle, tw.data(), tw.size()));
   MS_TRY(upload(s, (float2**)&sp.maskw, mw.data(), mw.size()));
+  {  // pair layout of the potential and mask tables: (Re 2p, Re 2p+1, Im 2p, Im 2p+1) per point pair
+    auto pairs = [nr](const std::vector<float2>& v) {
+      std::vector<float2> o(v.size());
+      for (size_t b = 0; b + 1 < v.size(); b += 2) {  // rows hold an even number of points
+        o[b] = make_float2(v[b].x, v[b + 1].x);
+        o[b + 1] = make_float2(v[b].y, v[b + 1].y);
+      }
+      (void)nr;
+      return o;
+    };
+    const std::vector<float2> vdp = pairs(vdelta), vhp = pairs(vhalf), mwp = pairs(mw);
+    MS_TRY(upload(s, (float2**)&sp.vdelta_pp, vdp.data(), vdp.size()));
+    MS_TRY(upload(s, (float2**)&sp.vhalf_pp, vhp.data(), vhp.size()));
+    MS_TRY(upload(s, (float2**)&sp.maskw_pp, mwp.data(), mwp.size()));
+  }
   MS_TRY(upload(s, (float**)&sp.r, rf.data(), rf.size()));
   MS_TRY(upload(s, (int**)&sp.mol, ids.data(), ids.size()));
   // populations at t = 0
@@ -526,8 +553,8 @@ struct Scratch {
 // along a seeded direction per molecule, and keep the fastest plan.
 ms_status tune_species(ms_sim* s, int si) {
   ms::SpeciesDev& sp = s->sp[si];
-  int cand[24][4];
-  const int nc = ms::mol_plan_candidates(sp, cand, 24);
+  int cand[32][4];
+  const int nc = ms::mol_plan_candidates(sp, cand, 32);
   if (nc < 2 || sp.nmol == 0) return MS_OK;
   const int nt = std::min(sp.nmol, 2048);
   const size_t per = (size_t)sp.rows * sp.nr;
@@ -1051,6 +1078,46 @@ struct FieldRecorder {  // ms_record_local_fields: E^n of listed molecules, one 
   float* out;  // [steps][m][3], advanced by the caller
 };
 
+// The pipelined molecular step (ms_set_mol_batches): every streaming species'
+// molecules in s->batches runs of consecutive molecules (other species: one
+// run), ordered species by species.  Stage 1 (field records, kinetic pass) of
+// run k + 1 is issued on the handle's stream right after that of run k; stage
+// 2 (R-space pass) of run k waits for its stage 1 on the second stream.  The
+// runs touch disjoint molecules, so stage 1 of one run may overlap stage 2 of
+// the previous one; the handle's stream then waits for the last stage 2.
+// Every molecule gets the same kernels on the same data: results do not
+// depend on the batching.
+static int pipelined_molecules(ms_sim* s, const ms::SpeciesDev* sp, int prescribed) {
+  ms::SpeciesDev runs[ms::kMaxSpecies * kMaxMolBatches];
+  int nrun = 0;
+  for (int si = 0; si < s->nspecies; ++si) {
+    const ms::SpeciesDev& a = sp[si];
+    const int nb = a.path == MS_MOL_STREAMING && !a.bloch ? std::min(s->batches, std::max(a.nmol, 1)) : 1;
+    const size_t per = (size_t)a.rows * a.nr;
+    for (int b = 0; b < nb; ++b) {
+      const int lo = (int)((long long)a.nmol * b / nb), hi = (int)((long long)a.nmol * (b + 1) / nb);
+      ms::SpeciesDev r = a;
+      r.nmol = hi - lo;
+      r.mol = a.mol + lo;
+      r.psi = a.psi + per * lo;
+      if (a.d2) r.d2 = a.d2 + per * lo;
+      r.fld = a.fld + lo;
+      if (a.bloch_y) r.bloch_y = a.bloch_y + 3 * (size_t)lo;
+      runs[nrun++] = r;
+    }
+  }
+  int launched = 0;
+  for (int k = 0; k < nrun; ++k) {
+    launched += ms::launch_mol_stage1(runs[k], s->md, s->g, prescribed, s->d_err, s->stream);
+    cudaEventRecord(s->bev[k], s->stream);  // this run's stage 1 and everything before it
+    cudaStreamWaitEvent(s->stream2, s->bev[k], 0);
+    launched += ms::launch_mol_stage2(runs[k], s->md, s->g, prescribed, s->d_err, s->stream2);
+  }
+  cudaEventRecord(s->bev[nrun], s->stream2);
+  cudaStreamWaitEvent(s->stream, s->bev[nrun], 0);
+  return launched;
+}
+
 static void step_once(ms_sim* s, float2* const* scratch, const FieldRecorder* rec = nullptr) {
   const bool fdtd = s->drive == MS_DRIVE_FDTD;
   // sub-stepping: the molecules advance (by nsub dt) on every nsub-th step only,
@@ -1072,13 +1139,18 @@ static void step_once(ms_sim* s, float2* const* scratch, const FieldRecorder* re
     sp[si] = s->sp[si];
     if (scratch && sp[si].path == MS_MOL_STREAMING) sp[si].d2 = scratch[si];  // rewritten before it is read
   }
-  if (molecular)
-    for (int si = 0; si < s->nspecies; ++si)
-      launched += ms::launch_mol_stage1(sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
-  if (s->timing) mark(s);
-  if (molecular)
-    for (int si = 0; si < s->nspecies; ++si)
-      launched += ms::launch_mol_stage2(sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
+  if (molecular && s->batches > 0) {
+    launched += pipelined_molecules(s, sp, fdtd ? 0 : 1);
+    if (s->timing) mark(s);  // stages overlap: only the molecular phase as a whole is timed
+  } else {
+    if (molecular)
+      for (int si = 0; si < s->nspecies; ++si)
+        launched += ms::launch_mol_stage1(sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
+    if (s->timing) mark(s);
+    if (molecular)
+      for (int si = 0; si < s->nspecies; ++si)
+        launched += ms::launch_mol_stage2(sp[si], s->md, s->g, fdtd ? 0 : 1, s->d_err, s->stream);
+  }
   if (s->timing) mark(s);
   if (fdtd) {
     ms::Grid ge = s->g;
@@ -1708,9 +1780,10 @@ ms_status ms_set_species_plan_ex(ms_sim* s, int32_t species, const int32_t plan[
   const int32_t path = plan[0], kernel = plan[1], chunk = plan[2], cps = plan[3];
   ms::SpeciesDev& sp = s->sp[species];
   if (sp.bloch) return MS_EINVAL;
-  if (cps < -1 || cps > 32 || (cps != 0 && kernel != MS_KERN_TILE)) return MS_EINVAL;
-  int cand[24][4];
-  const int nc = ms::mol_plan_candidates(sp, cand, 24);
+  const bool tiled = kernel == MS_KERN_TILE || kernel == MS_KERN_PAIR;
+  if (cps < -1 || cps > 32 || (cps != 0 && !tiled)) return MS_EINVAL;
+  int cand[32][4];
+  const int nc = ms::mol_plan_candidates(sp, cand, 32);
   bool ok = false;
   if (kernel == MS_KERN_DEFAULT && chunk == 0) {
     for (int c = 0; c < nc; ++c) ok = ok || cand[c][0] == path;
@@ -1718,7 +1791,7 @@ ms_status ms_set_species_plan_ex(ms_sim* s, int32_t species, const int32_t plan[
   } else {
     for (int c = 0; c < nc; ++c)  // a tiled plan with chunk 0 follows the kernel's tile-width rule
       ok = ok || (cand[c][0] == path && cand[c][1] == kernel &&
-                  (cand[c][2] == chunk || (kernel == MS_KERN_TILE && chunk == 0)));
+                  (cand[c][2] == chunk || (tiled && chunk == 0)));
   }
   if (!ok) return MS_EINVAL;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
@@ -1737,6 +1810,32 @@ ms_status ms_set_species_plan(ms_sim* s, int32_t species, int32_t path, int32_t 
   const int32_t plan[4] = {path, kernel, chunk, 0};
   return ms_set_species_plan_ex(s, species, plan);
 }
+
+ms_status ms_set_mol_batches(ms_sim* s, int32_t batches) {
+  if (!s || batches < 0 || batches > kMaxMolBatches) return MS_EINVAL;
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
+  if (batches > 0 && !s->stream2) {
+    if (cudaStreamCreateWithFlags(&s->stream2, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      s->stream2 = nullptr;
+      return MS_ECUDA;
+    }
+    const int nev = ms::kMaxSpecies * kMaxMolBatches + 1;  // one per run, one for the join
+    for (int k = 0; k < nev; ++k) {
+      cudaEvent_t e = nullptr;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return MS_ECUDA;
+      }
+      s->bev.push_back(e);
+    }
+  }
+  s->batches = batches;
+  s->gdirty = true;
+  return MS_OK;
+}
+
+int32_t ms_mol_batches(const ms_sim* s) { return s ? s->batches : -1; }
 
 size_t ms_device_bytes(const ms_sim* s) { return s ? s->bytes : 0; }
 

@@ -120,6 +120,12 @@ struct SpeciesDev {
   const float2* khalf;      // [nr] e^{-i k^2 dtau / 4mu} / nr, for the psi = T^{1/2} s readout
   const float2* twiddle;    // [n2][n1]: exp(-2 pi i n1 k2 / nr)
   const float2* maskw;      // [nr]: (m, 1 - m^2)
+  // the same three tables with each pair of radial points (2p, 2p + 1) as
+  // (Re 2p, Re 2p+1), (Im 2p, Im 2p+1) (mask: (m, m), (1 - m^2, 1 - m^2)),
+  // for the tiled kernel that holds two points a thread (MS_KERN_PAIR)
+  const float2* vdelta_pp;
+  const float2* vhalf_pp;
+  const float2* maskw_pp;
   const float* r;           // [nr]
   double theta;             // d * dtau (d(R): its largest |d| times dtau)
   double dipole;            // d (e a0) (d(R): its largest |d|)

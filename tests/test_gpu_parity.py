@@ -295,14 +295,16 @@ def test_flux_spectra_match_oracle(B):
     assert o.dft.flux(1)[0].max() > 0 and o.dft.flux(0)[0].min() < 0   # transmitted +z, reflected -z
 
 
-@pytest.mark.parametrize("nr,jmax,E0", [(64, 1, 0.0), (128, 4, 0.0), (128, 4, 1e9)])
-def test_norm_drift_2000_steps(B, nr, jmax, E0):
+@pytest.mark.parametrize("nr,jmax,E0,plan", [(64, 1, 0.0, None), (128, 4, 0.0, None), (128, 4, 1e9, None),
+                                             (128, 8, 1e9, "tile"), (128, 8, 1e9, "pair")])
+def test_norm_drift_2000_steps(B, nr, jmax, E0, plan):
     """Norm drift of the FP32 wavepackets over 2000 steps, field-free and under
     the benchmark's 1e9 V/m pulse: every one of 64 molecules within the 1e-6
-    target.  Without the rounding feedback the final FP32 rounding of each
-    step walks the norm by ~1.5e-8 per step (max of 64 walks 1.9e-6 at 2000
-    steps); with it the norm carries one step's rounding plus the rounding
-    inside the correction."""
+    target, with the default kernels and with both tiled kernels at J = 8.
+    Without the rounding feedback the final FP32 rounding of each step walks
+    the norm by ~1.5e-8 per step (max of 64 walks 1.9e-6 at 2000 steps); with
+    it the norm carries one step's rounding plus the rounding inside the
+    correction."""
     sp = W.Species(nr=nr, jmax=jmax)
     n = 64
     wl = W.custom("norm", 8, 8, 48, n_per_sim=n, species=[sp], layer=(20, 24), seed=3, nsteps=2000)
@@ -310,13 +312,15 @@ def test_norm_drift_2000_steps(B, nr, jmax, E0):
     if E0 == 0.0:
         amp[:] = 0.0
     sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED)
+    if plan is not None:
+        sim.set_plan(0, B.MS_MOL_STREAMING, B.MS_KERN_PAIR if plan == "pair" else B.MS_KERN_TILE, 0)
     sim.set_prescribed(amp, wave)
     sim.step(2000)
     P = sim.populations()
     absb, _ = sim.dissociation()
     drift = np.abs(P.sum(axis=1) + absb.sum(axis=1) - 1.0)
     rms = np.sqrt((drift ** 2).mean())
-    print(f"norm drift nr={nr} J={jmax} E0={E0}: max {drift.max():.3e} rms {rms:.3e}")
+    print(f"norm drift nr={nr} J={jmax} E0={E0} plan={plan}: max {drift.max():.3e} rms {rms:.3e}")
     assert drift.max() < 1e-6
 
 

@@ -24,9 +24,11 @@ def B():
 
 
 def _plans(B):
-    """(layout, kernel, chunk, grid): the tiled kernel at both tile widths and
-    three grids (as many CTAs as fit, one per SM, one per molecule)."""
-    kc = [(B.MS_KERN_POINT, 0, 0)] + [(B.MS_KERN_TILE, t, g) for t in (32, 16, 8) for g in (0, 1, -1)] + \
+    """(layout, kernel, chunk, grid): both tiled kernels (one and two radial
+    points a thread) at their tile widths and three grids (as many CTAs as
+    fit, one per SM, one per molecule)."""
+    kc = [(B.MS_KERN_POINT, 0, 0)] + \
+        [(k, t, g) for k in (B.MS_KERN_TILE, B.MS_KERN_PAIR) for t in (32, 16, 8) for g in (0, 1, -1)] + \
         [(B.MS_KERN_CHUNK, c, 0) for c in (32, 16, 8, 4)]
     return [(p, k, c, g) for p in (B.MS_MOL_FUSED, B.MS_MOL_STREAMING) for k, c, g in kc]
 
@@ -67,12 +69,15 @@ def test_every_plan_matches_oracle(B, nr, jmax, nmol):
         assert B.MS_KERN_POINT in kinds
     tiles = {c for _, k, c, _ in ran if k == B.MS_KERN_TILE}
     assert tiles == ({8} if jmax >= 9 else {16, 32}), ran   # the tile widths of the basis size
+    pairs = {c for _, k, c, _ in ran if k == B.MS_KERN_PAIR}
+    assert pairs == ({8} if jmax >= 9 else ({16, 8} if jmax >= 5 else {32, 16})), ran
     # the grid only changes which CTA runs a molecule: identical results
-    for t in tiles:
-        runs = [results[p] for p in ran if p[1] == B.MS_KERN_TILE and p[2] == t]
-        assert len(runs) == 3
-        for P, mu in runs[1:]:
-            assert np.array_equal(P, runs[0][0]) and np.array_equal(mu, runs[0][1])
+    for k, ts in ((B.MS_KERN_TILE, tiles), (B.MS_KERN_PAIR, pairs)):
+        for t in ts:
+            runs = [results[p] for p in ran if p[1] == k and p[2] == t]
+            assert len(runs) == 3
+            for P, mu in runs[1:]:
+                assert np.array_equal(P, runs[0][0]) and np.array_equal(mu, runs[0][1])
 
 
 def test_autotuned_three_species_coupled(B):
@@ -108,6 +113,7 @@ def test_plan_validation(B):
     for bad in ((B.MS_MOL_STREAMING, B.MS_KERN_POINT, 0),    # J = 9: no point-resident kernel
                 (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 32),    # J = 9: tiles of 8 points only
                 (B.MS_MOL_STREAMING, B.MS_KERN_TILE, 16),
+                (B.MS_MOL_STREAMING, B.MS_KERN_PAIR, 16),    # J = 9: two points a thread on 8-point tiles
                 (B.MS_MOL_STREAMING, B.MS_KERN_CHUNK, 12),   # not a chunk width
                 (B.MS_MOL_STREAMING, B.MS_KERN_CHUNK, 8, 1),  # a grid for a kernel that has none
                 (7, B.MS_KERN_CHUNK, 8)):
@@ -121,22 +127,24 @@ def test_plan_validation(B):
 
 @pytest.mark.parametrize("nr,jmax,nmol", [(64, 6, 7), (128, 8, 5), (64, 10, 3)])
 def test_tiled_plans_are_deterministic(B, nr, jmax, nmol):
-    """Every tile width and grid of the tiled kernel, run twice from the same
-    start: identical results bit for bit (the kernel's shared-memory regions,
-    its tensor copies and the prefetch of the next molecule must not race)."""
+    """Every tile width and grid of both tiled kernels, run twice from the
+    same start: identical results bit for bit (the kernels' shared-memory
+    regions, their tensor copies and the prefetch of the next molecule must
+    not race)."""
     sp = W.Species(nr=nr, jmax=jmax, A=0.05)
     wl = W.custom("tiled determinism", 8, 8, 48, n_per_sim=nmol, species=[sp], layer=(20, 24),
                   seed=nr + jmax, nsteps=120)
     amp, wave = W.prescribed_drive(nmol, 120, wl.dt, E0=3e10, carrier_ev=6.0, fwhm=0.5e-15, t0=0.4e-15)
-    tiles = (8,) if jmax >= 9 else (32, 16)
-    for t in tiles:
+    kt = [(B.MS_KERN_TILE, t) for t in ((8,) if jmax >= 9 else (32, 16))]
+    kt += [(B.MS_KERN_PAIR, t) for t in ((8,) if jmax >= 9 else ((16, 8) if jmax >= 5 else (32, 16)))]
+    for k, t in kt:
         for g in (0, 1, -1):
             runs = []
             for _ in range(2):
                 sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, mol_path=B.MS_MOL_STREAMING)
-                sim.set_plan(0, B.MS_MOL_STREAMING, B.MS_KERN_TILE, t, g)
+                sim.set_plan(0, B.MS_MOL_STREAMING, k, t, g)
                 sim.set_prescribed(amp, wave)
                 sim.step(wl.nsteps)
                 runs.append((sim.populations(), sim.dipoles()))
                 sim.close()
-            assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1]), (t, g)
+            assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1]), (k, t, g)

@@ -237,12 +237,14 @@ def test_population_sums_equal_fp64_sums_of_the_state(B, tmp_path):
     n = 40
     wl = W.custom("fp64 sums", 8, 8, 48, n_per_sim=n, species=[sp], layer=(20, 24), seed=17, nsteps=300)
     amp, wave = W.prescribed_drive(n, 300, wl.dt, E0=3e10, carrier_ev=6.0, fwhm=0.5e-15, t0=0.5e-15)
-    for path in (B.MS_MOL_FUSED, B.MS_MOL_STREAMING):
+    for path, kern in ((B.MS_MOL_FUSED, None), (B.MS_MOL_STREAMING, None), (B.MS_MOL_STREAMING, B.MS_KERN_PAIR)):
         sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, mol_path=path)
+        if kern is not None:   # the two-points-a-thread kernel sums point pairs
+            sim.set_plan(0, path, kern, 0)
         sim.set_prescribed(amp, wave)
         sim.step(300)
         P = sim.populations()
-        ck = str(tmp_path / f"state{path}.ck")
+        ck = str(tmp_path / f"state{path}_{kern}.ck")
         sim.save(ck)
         sim.close()
         raw = open(ck, "rb").read()
@@ -262,7 +264,7 @@ def test_population_sums_equal_fp64_sums_of_the_state(B, tmp_path):
         # molecule order: the state is stored by species, in molecule-id order within it
         rel = np.abs(P - P64) / np.maximum(P64, 1e-300)
         rel_exact = np.abs(P - exact) / np.maximum(exact, 1e-300)
-        print(f"layout {path}: populations vs FP64 sums of the FP32 products {rel.max():.2e}, "
+        print(f"layout {path} kernel {kern}: populations vs FP64 sums of the FP32 products {rel.max():.2e}, "
               f"vs the exact norms of the stored state {rel_exact.max():.2e}")
         assert P[:, 1].max() > 1e-6
         assert rel.max() < 1e-11
