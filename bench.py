@@ -458,6 +458,18 @@ def main():
                 "1.3e-7)")
             forms["mixed_f16x3"] = mixed
         if a.config != 1:
+            # the parity-reduced state of the same workload: only the rows the
+            # j = 0 start populates (half of them), identical dynamics
+            fp = time_form(wl, path, B.MS_PREC_FP32, preroll, state_form=B.MS_STATE_PARITY)
+            par = form_entry(fp, wl, P)
+            par["gain_vs_full_state"] = ms / fp["ms"]
+            par["note"] = ("parity-reduced state: only (ground, even j) and (excited, odd j) rows, the rows the "
+                           "j = 0 start populates (each coupling changes j by one and swaps the surfaces); the "
+                           "dropped rows of the full state stay exactly zero, so the results are those of the "
+                           "full state up to FP32 rounding order (tests/test_gpu_parity.py, "
+                           "test_parity_reduced_matches_oracle)")
+            forms["parity_reduced"] = par
+        if a.config != 1:
             forms.update(splitring_forms(a, B, np, torch, dist, world, time_form, form_entry))
         else:
             forms.update(splitring_forms(a, B, np, torch, dist, world, time_form, form_entry, main=main_form))

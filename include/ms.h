@@ -90,8 +90,11 @@ enum { MS_MOL_AUTO = 0, MS_MOL_FUSED = 1, MS_MOL_STREAMING = 2 };
  * (excited, odd j), the only rows the dynamics populate from the j = 0
  * ground-state start (each coupling changes j by one and swaps the
  * surfaces), which halves the state and the work.  Results are those of the
- * full state.  Parity-reduced species need J <= 4, and the fused layout
- * only at N_r = 128 (MS_EUNSUPPORTED otherwise). */
+ * full state.  Up to J = 4 the point-resident kernels run them (the fused
+ * layout only at N_r = 128); from J = 5 on the two-points-a-thread tiled
+ * kernel in the streaming layout with the FP32 kinetic pass (MS_EUNSUPPORTED
+ * otherwise).  Their plan follows this rule (ms_set_species_plan accepts no
+ * other). */
 enum { MS_STATE_FULL = 0, MS_STATE_PARITY = 1 };
 /* Step replay.  MS_GRAPHS_AUTO: ms_step captures the launches of whole
  * molecular cycles (at least 8 field steps, a multiple of mol_substeps) once

@@ -17,9 +17,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libms.so")
-SOURCES = ["ms_api.cu", "yee.cu", "mol.cu", "bloch.cu"]
+SOURCES = ["ms_api.cu", "yee.cu", "mol.cu", "mol_tile.cu", "mol_pair.cu", "bloch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "--split-compile=0",
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-Xcudafe", "--diag_suppress=177"]
 
 

@@ -39,6 +39,7 @@
 #include <vector>
 
 #include "ms_internal.cuh"
+#include "mol_common.cuh"
 
 namespace ms {
 
@@ -88,11 +89,6 @@ __device__ __forceinline__ float2 cmul_c_add(float2 x, float4 w, float2 a) {
   const float im_lo = fmaf(x.x, w.w, fmaf(x.y, w.z, a.y));
   return make_float2(fmaf(x.x, w.x, fmaf(-x.y, w.y, re_lo)), fmaf(x.x, w.y, fmaf(x.y, w.x, im_lo)));
 }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
 // multiply by exp(-+ i t pi/8) (forward: minus)
 template <int T, bool INV>
@@ -244,48 +240,6 @@ __device__ void kinetic_pass(float2* st, int rows, const float2* kph, const floa
   __syncthreads();
 }
 
-// ---- TMA bulk copies (cp.async.bulk) completing on an mbarrier --------------
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-// 2-D tensor copy global -> shared (box of the map at element (x, y)).
-__device__ __forceinline__ void tensor2d_g2s(void* dst, const CUtensorMap* map, int x, int y,
-                                             unsigned long long* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          smem_u32(dst)),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
-}
-// Wait for phase `parity` of the barrier, giving up after `limit` polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, long long limit) {
-  for (long long it = 0; it < limit; ++it) {
-    unsigned done;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-constexpr long long kWaitPolls = 1LL << 24;  // far beyond any copy's duration
-
 // 16-byte asynchronous global -> shared copies (per thread), completed by
 // cp.async.wait_group.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
@@ -304,7 +258,6 @@ __device__ __forceinline__ void load_state(float2* st, const float2* g, int rows
   }
 }
 
-__device__ __forceinline__ int j_of(int c) { return (int)sqrtf((float)c + 0.5f); }  // c = j^2+j+m
 
 }  // namespace
 
@@ -384,37 +337,6 @@ constexpr int kChunk = 32;            // widest R-space chunk (one radial point 
 //   u  = s + d2 = T s        (per radial point)
 //   s' = Mask V^{1/2} K(E') V^{1/2} u, computed as s + (d2 + d1)
 // ----------------------------------------------------------------------------
-// compensated FP32 accumulation (TwoSum): hi + lo carries ~48 bits
-__device__ __forceinline__ void acc2(float& hi, float& lo, float x) {
-  const float t = hi + x;
-  const float z = t - hi;
-  lo += (hi - (t - z)) + (x - z);
-  hi = t;
-}
-
-// The state's one full-magnitude rounding per step, s' = fl(s + D'), with the
-// update D' = D + c s scaled by the previous step's rounding feedback c, and
-// the exact residual e = (s + D') - s' of that rounding (TwoSum; the FP32
-// operations must stay unfused and unreordered) folded into acc as
-// Re(conj(s') e).  The rounding changed sum |s|^2 by -2 sum Re(conj(s') e) to
-// first order; the next step's c = sum Re(conj(s') e) / sum |s'|^2 gives that
-// back, so the norm carries one step's rounding instead of a random walk.
-__device__ __forceinline__ float2 round_update(float2 sv, float2 D, float c, float& acc) {
-  const float dx = fmaf(c, sv.x, D.x), dy = fmaf(c, sv.y, D.y);
-  const float nx = __fadd_rn(sv.x, dx), ny = __fadd_rn(sv.y, dy);
-  const float bx = __fsub_rn(nx, sv.x), by = __fsub_rn(ny, sv.y);
-  const float ex = __fadd_rn(__fsub_rn(sv.x, __fsub_rn(nx, bx)), __fsub_rn(dx, bx));
-  const float ey = __fadd_rn(__fsub_rn(sv.y, __fsub_rn(ny, by)), __fsub_rn(dy, by));
-  acc = fmaf(nx, ex, fmaf(ny, ey, acc));
-  return make_float2(nx, ny);
-}
-
-// feedback factor for the next step from the summed residual products and the
-// summed |s'|^2 of a molecule (0 for an empty state)
-__device__ __forceinline__ float rounding_feedback(float res, float norm2) {
-  return norm2 > 0.f && isfinite(res) ? res / norm2 : 0.f;
-}
-
 // FUSED: the whole state is staged in shared memory and the kinetic pass runs
 // in this kernel.  Otherwise (streaming form) d2 = (T - 1) s comes from the
 // scratch written by mol_kinetic_kernel and is streamed chunk by chunk with s.
@@ -727,59 +649,12 @@ __global__ void __launch_bounds__(FFTShape<NR>::THREADS, FUSED ? 2 : (MAXR <= 4 
 // outside the basis are zero and their reads land on finite data: kTriGuard
 // zero rows precede each buffer, and a missing run points at them.
 // ----------------------------------------------------------------------------
-// Per channel, on the two runs (j + 1, .) and (j - 1, .): .x S+ (from m - 1),
-// .y Z (from m), .z S- (from m + 1), .w 0.
-__device__ float4 g_tri_up[kMaxRot], g_tri_dn[kMaxRot];
-
+// The angular tables of every translation unit's copy.
 cudaError_t upload_triplet_tables(const CouplEntry* dip) {
-  // dipole slots: 0 Z (j-1, m), 1 Z (j+1, m), 2 S+ (j-1, m-1), 3 S+ (j+1, m-1), 4 S- (j+1, m+1), 5 S- (j-1, m+1)
-  std::vector<float4> up(kMaxRot, make_float4(0.f, 0.f, 0.f, 0.f)), dn = up;
-  for (int c = 0; c < kMaxRot; ++c) {
-    auto cf = [&](int slot) { const CouplEntry& e = dip[c * kMaxCoupl + slot]; return e.nbr >= 0 ? e.coef : 0.f; };
-    up[c] = make_float4(cf(3), cf(1), cf(4), 0.f);
-    dn[c] = make_float4(cf(2), cf(0), cf(5), 0.f);
-  }
-  cudaError_t e = cudaMemcpyToSymbol(g_tri_up, up.data(), sizeof(float4) * kMaxRot);
+  cudaError_t e = upload_triplet_tables_local(dip);
+  if (e == cudaSuccess) e = upload_triplet_tables_tile(dip);
   if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(g_tri_dn, dn.data(), sizeof(float4) * kMaxRot);
-}
-
-constexpr int kTriGuard = 3;  // zero rows ahead of each term buffer
-
-// Tensor maps of one species for the tiled R-space kernel: 8-byte elements
-// (one complex FP32 value), boxes of TILE radial points by the rows of a
-// molecule, at most 256 rows a box (a box dimension's limit): a molecule's
-// rows arrive as full boxes (s, d2) and one remainder box (s_r, d2_r).
-struct RspaceMaps {
-  CUtensorMap s, d2;      // [n_mol * rows][nr], box TILE x min(rows, 256)
-  CUtensorMap s_r, d2_r;  // same arrays, box TILE x the remainder rows (rows > 256 only)
-  CUtensorMap vd, vh;     // [2 (J + 1)][nr], box TILE x 2 (J + 1)
-  CUtensorMap mk;         // [1][nr], box TILE x 1
-};
-
-// One row of the tiled kernel's row table (built per molecule).
-struct RowT {
-  float4 cu, cd;  // theta x coupling on the runs (j + 1, .) and (j - 1, .)
-  float4 du, dd;  // dipole coefficients on the runs
-  float2 ph;      // e^{i m phi_E}
-  int ou, od;     // byte offsets of the two runs in a term buffer (from its base)
-  int vo, pad;    // byte offset of the row's (surface, j) potential row in a table tile
-};
-
-// Wait for phase `parity`, each try suspending up to hint_ns until the phase
-// completes; gives up after `tries` tries (by default about 2 s in all).
-__device__ __forceinline__ bool mbar_wait_sleep(unsigned long long* bar, unsigned parity, int tries = 2000,
-                                                unsigned hint_ns = 1000000u) {
-  for (int it = 0; it < tries; ++it) {
-    unsigned done;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3; selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
+  return upload_triplet_tables_pair(dip);
 }
 
 // Diagnostic of the bounded wait: one CTA waits on a barrier that nothing
@@ -796,833 +671,12 @@ __global__ void wait_timeout_probe_kernel(int tries, int* flag) {
   if (!__syncthreads_and(ok) && threadIdx.x == 0) atomicOr(flag, kErrTimeout);
 }
 
+// Latches a host-detected launch failure into the error word.
+__global__ void flag_error_kernel(int* err, int code) { atomicOr(err, code); }
+
 cudaError_t launch_wait_timeout_probe(int tries, int* flag, cudaStream_t s) {
   wait_timeout_probe_kernel<<<1, 32, 0, s>>>(tries, flag);
   return cudaGetLastError();
-}
-
-// Layout of the tiled R-space kernel for basis size J and tile width TILE
-// (32, 16 or 8 radial points).  A warp covers RPL = 32 / TILE rows of one tile
-// (lane = part * TILE + point, part = lane / TILE) and NW warps of RPW row
-// slots each cover the 2 (J + 1)^2 rows: warp w owns rows RPL (w + NW i) +
-// part.  Up to J = 8 (tiles of 32 or 16) RPW = J + 1 and the rows split
-// exactly, so every row index, buffer offset and stride is known at compile
-// time.  From J = 9 on (tiles of 8, 578 rows at J = 16) RPW = 6 and the last
-// slots run past the rows: those padded rows stay zero, their row-table
-// entries point at the zero guard rows, and they are neither summed nor
-// written.  A row of a tile is SEG = 8 TILE bytes; the RPL rows of a slot
-// are contiguous, so a warp's 32 lanes always read 256 contiguous bytes.
-// Shared memory, from a 128-byte aligned base:
-//   [2 RP] s and d2 of the tile, [2][NV] e^{-iV dtau} - 1, [2][NV]
-//   e^{-iV dtau/2} (double buffered), [1] mask, two term buffers of
-//   kTriGuard + RP rows, the row table of the molecule (RP = padded rows).
-// With 16-point tiles the J = 8 kernel needs 109 KB, so two CTAs share an SM
-// and one's barriers and copies overlap the other's arithmetic; the J = 16
-// kernel needs 211 KB at 800 threads.
-template <int J, int TILE>
-struct RsDims {
-  static constexpr int NROT = (J + 1) * (J + 1), ROWS = 2 * NROT, NV = 2 * (J + 1);
-  static constexpr int RPL = 32 / TILE;
-  static constexpr int RPW = TILE == 8 ? 6 : J + 1;
-  static constexpr int NW = ((ROWS + RPL - 1) / RPL + RPW - 1) / RPW, NT = 32 * NW;
-  static constexpr int RP = NW * RPW * RPL;  // rows with padding
-  static constexpr bool EXACT = RP == ROWS;
-  static constexpr int SEG = TILE * (int)sizeof(float2);
-  static constexpr int BOXR = ROWS < 256 ? ROWS : 256, NBOX = (ROWS + BOXR - 1) / BOXR;
-  static constexpr int LASTR = ROWS - (NBOX - 1) * BOXR;  // rows of the last box
-  static constexpr int TBB = (kTriGuard + RP) * SEG;      // bytes of a term buffer
-  static constexpr int O_STG = 0, O_VD = O_STG + 2 * RP * SEG, O_VH = O_VD + 2 * NV * SEG;
-  static constexpr int O_MK = O_VH + 2 * NV * SEG, O_TB = O_MK + (SEG < 128 ? 128 : SEG), O_RT = O_TB + 2 * TBB;
-  static constexpr int BYTES = 128 + O_RT + RP * (int)sizeof(RowT);
-  static constexpr int MINB = TILE == 16 ? 2 : (J <= 4 ? 3 : 1);
-  static_assert(TILE == 8 || TILE == 16 || TILE == 32, "tile of 8, 16 or 32 radial points");
-  static_assert(TILE == 8 || 2 * (J + 1) % RPL == 0, "rows split evenly over the warps");
-  static_assert(NT <= 1024 && BYTES <= 227 * 1024, "one CTA per molecule fits");
-  static_assert((RP * SEG) % 128 == 0 && (NV * SEG) % 128 == 0 && (BOXR * SEG) % 128 == 0,
-                "tensor-copy destinations 128-byte aligned");
-};
-
-template <int OFF>
-__device__ __forceinline__ float2 lds2(const unsigned char* base, int off) {
-  return *reinterpret_cast<const float2*>(base + off + OFF);
-}
-template <int OFF>
-__device__ __forceinline__ void sts2(unsigned char* base, int off, float2 v) {
-  *reinterpret_cast<float2*>(base + off + OFF) = v;
-}
-
-// Persistent: CTA b runs molecules b, b + gridDim.x, ...; the first tile of
-// its next molecule is requested as soon as the last tile of the current one
-// has left the staging buffer.  The molecule's frame field and term count
-// come from its record (mol_field_kernel).
-template <int J, int TILE>
-__global__ void __launch_bounds__(RsDims<J, TILE>::NT, RsDims<J, TILE>::MINB)
-    mol_rspace_kernel(SpeciesDev sp, MolDev md, int* err, const __grid_constant__ RspaceMaps maps) {
-  using D = RsDims<J, TILE>;
-  constexpr int NROT = D::NROT, ROWS = D::ROWS, NV = D::NV, NW = D::NW, RPW = D::RPW, NT = D::NT;
-  constexpr int RPL = D::RPL, SEG = D::SEG, TBB = D::TBB, G0 = kTriGuard * SEG;
-  constexpr int SLOT = RPL * SEG;                 // bytes of one warp's rows in a tile buffer
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long s_bar[1];
-  __shared__ float s_rot[9];
-  __shared__ double s_mu[3], s_abs[2];
-  __shared__ float2 s_ph[2 * kMaxJ + 1];
-  __shared__ float s_red[NW][10];
-  __shared__ float s_fin[8], s_fin_lo[2];
-
-  const int NR = sp.nr;
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int half = lane / TILE, pt = lane % TILE;
-  const int pad = (int)((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  unsigned char* const sm = smem_raw;
-  // this thread's byte offsets: own rows RPL (w + NW i) + half at point pt, and their row-table entries
-  const int own = pad + w * SLOT + lane * 8;
-  const int rtw = pad + D::O_RT + (RPL * w + half) * (int)sizeof(RowT);
-  auto issue = [&](int mol, int ck) {
-    const int r0 = ck * TILE, b = ck & 1;
-    unsigned char* base = sm + pad;
-#pragma unroll
-    for (int k = 0; k < D::NBOX; ++k) {  // the molecule's rows, in boxes of at most 256
-      const bool last = k == D::NBOX - 1 && D::NBOX > 1;
-      tensor2d_g2s(base + D::O_STG + k * D::BOXR * SEG, last ? &maps.s_r : &maps.s, r0, mol * ROWS + k * D::BOXR,
-                   &s_bar[0]);
-      tensor2d_g2s(base + D::O_STG + (D::RP + k * D::BOXR) * SEG, last ? &maps.d2_r : &maps.d2, r0,
-                   mol * ROWS + k * D::BOXR, &s_bar[0]);
-    }
-    tensor2d_g2s(base + D::O_VD + b * NV * SEG, &maps.vd, r0, 0, &s_bar[0]);
-    tensor2d_g2s(base + D::O_VH + b * NV * SEG, &maps.vh, r0, 0, &s_bar[0]);
-    tensor2d_g2s(base + D::O_MK, &maps.mk, r0, 0, &s_bar[0]);
-  };
-  constexpr unsigned kChunkBytes = (2 * ROWS + 2 * NV + 1) * SEG;  // what the copies of one tile deliver
-  const int nchunks = NR / TILE;  // even: NR is 64, 128 or 256
-
-  int lm = blockIdx.x;
-  if (t == 0) {
-    mbar_init(&s_bar[0], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    mbar_expect_tx(&s_bar[0], kChunkBytes);
-    issue(lm, 0);
-  }
-  for (int q = t; q < kTriGuard * TILE; q += NT) {
-    reinterpret_cast<float2*>(sm + pad + D::O_TB)[q] = make_float2(0.f, 0.f);
-    reinterpret_cast<float2*>(sm + pad + D::O_TB + TBB)[q] = make_float2(0.f, 0.f);
-  }
-  if constexpr (!D::EXACT) {  // padded staging rows: zero, and never written by the copies
-    for (int q = t; q < (D::RP - ROWS) * TILE; q += NT) {
-      reinterpret_cast<float2*>(sm + pad + D::O_STG + ROWS * SEG)[q] = make_float2(0.f, 0.f);
-      reinterpret_cast<float2*>(sm + pad + D::O_STG + (D::RP + ROWS) * SEG)[q] = make_float2(0.f, 0.f);
-    }
-  }
-  // ground rows: q = RPL (w + NW i) + part < NROT; rows past ROWS are padding
-  auto ground = [&](int i) { return RPL * (w + NW * i) + half < NROT; };
-  auto valid = [&](int i) { return D::EXACT || RPL * (w + NW * i) + half < ROWS; };
-
-  for (; lm < sp.nmol; lm += gridDim.x) {
-    const int m = sp.mol[lm];
-    __syncthreads();  // the previous molecule's outputs are written: its records may be replaced
-    const float4 f = __ldg(&sp.fld[lm]);  // (theta E'_z, theta E'_x/2, theta E'_y/2, terms)
-    const int nterms = __float_as_int(f.w);
-    if (t <= J) {  // e^{i t phi_E} by binary powers of e^{i phi_E} = (E'_x + i E'_y)/E_perp
-      const float ep = sqrtf(f.y * f.y + f.z * f.z);
-      float2 e1 = ep > 0.f ? make_float2(f.y / ep, f.z / ep) : make_float2(1.f, 0.f);
-      float2 pw = make_float2(1.f, 0.f);
-      for (int k = t; k > 0; k >>= 1) {
-        if (k & 1) pw = cmul(pw, e1);
-        e1 = cmul(e1, e1);
-      }
-      s_ph[J + t] = pw;
-      s_ph[J - t] = make_float2(pw.x, -pw.y);
-    }
-    for (int q = t; q < 14; q += NT) {  // rotation, previous dipole, absorbed norm so far
-      if (q < 9) s_rot[q] = md.rot[9 * (long long)m + q];
-      else if (q < 12) s_mu[q - 9] = md.mu[3 * (long long)m + (q - 9)];
-      else s_abs[q - 12] = md.absorbed[2 * (long long)m + (q - 12)];
-    }
-    const float cfix = md.ncorr[m];  // rounding feedback of the previous step
-    __syncthreads();
-    for (int q = t; q < D::RP; q += NT) {  // the row table of this molecule (padding: zero, guard rows)
-      if (!D::EXACT && q >= ROWS) {
-        RowT r;
-        r.cu = r.cd = r.du = r.dd = make_float4(0.f, 0.f, 0.f, 0.f);
-        r.ph = make_float2(1.f, 0.f);
-        r.ou = r.od = D::O_TB;
-        r.vo = 0;
-        r.pad = 0;
-        *reinterpret_cast<RowT*>(sm + pad + D::O_RT + q * (int)sizeof(RowT)) = r;
-        continue;
-      }
-      // theta E_perp / 2 on the X runs and theta E'_z on the Z runs (frame turned so E'_y = 0)
-      const float ep = sqrtf(f.y * f.y + f.z * f.z), ez = f.x;
-      const int sf = q >= NROT, c = q - sf * NROT, j = j_of(c), mm = c - j * j - j;
-      const int other = kTriGuard + (1 - sf) * NROT;
-      RowT r;
-      r.ph = s_ph[mm + J];
-      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-      r.du = j < J ? g_tri_up[c] : z4;
-      r.dd = j > 0 ? g_tri_dn[c] : z4;
-      r.cu = make_float4(ep * r.du.x, ez * r.du.y, ep * r.du.z, 0.f);
-      r.cd = make_float4(ep * r.dd.x, ez * r.dd.y, ep * r.dd.z, 0.f);
-      r.ou = D::O_TB + (j < J ? (other + c + 2 * j + 1) * SEG : 0);
-      r.od = D::O_TB + (j > 0 ? (other + c - 2 * j - 1) * SEG : 0);
-      r.vo = (sf * (J + 1) + j) * SEG;
-      r.pad = 0;
-      *reinterpret_cast<RowT*>(sm + pad + D::O_RT + q * (int)sizeof(RowT)) = r;
-    }
-    float2 sv[RPW], dv[RPW], sacc[RPW];
-    float p_hi[2] = {0.f, 0.f}, p_lo[2] = {0.f, 0.f};  // populations, compensated
-    float a_gf = 0.f, a_ef = 0.f, dP = 0.f, dQ = 0.f, dZ = 0.f, rnd = 0.f;
-    float2* gs = sp.psi + (long long)lm * ROWS * NR;
-
-    // one coupling-series term reading term buffer P (compile-time), writing
-    // the other one unless it is the last
-    auto term = [&](auto Pc, int n) {
-      constexpr int P = decltype(Pc)::value;
-      const float cn = 1.f / (float)n;
-      const bool store = n < nterms;
-#pragma unroll
-      for (int i = 0; i < RPW; ++i) {
-        const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowT);
-        const float4 cu = *reinterpret_cast<const float4*>(rt + offsetof(RowT, cu));
-        const float4 cd = *reinterpret_cast<const float4*>(rt + offsetof(RowT, cd));
-        const int2 oo = *reinterpret_cast<const int2*>(rt + offsetof(RowT, ou));
-        const int ou = pad + pt * 8 + oo.x, od = pad + pt * 8 + oo.y;
-        const float2 u0 = lds2<P * TBB>(sm, ou), u1 = lds2<P * TBB + SEG>(sm, ou),
-                     u2 = lds2<P * TBB + 2 * SEG>(sm, ou);
-        const float2 d0 = lds2<P * TBB>(sm, od), d1 = lds2<P * TBB + SEG>(sm, od),
-                     d2 = lds2<P * TBB + 2 * SEG>(sm, od);
-        float ax = cu.x * u0.x, ay = cu.x * u0.y;
-        ax = fmaf(cu.y, u1.x, ax); ay = fmaf(cu.y, u1.y, ay);
-        ax = fmaf(cu.z, u2.x, ax); ay = fmaf(cu.z, u2.y, ay);
-        ax = fmaf(cd.x, d0.x, ax); ay = fmaf(cd.x, d0.y, ay);
-        ax = fmaf(cd.y, d1.x, ax); ay = fmaf(cd.y, d1.y, ay);
-        ax = fmaf(cd.z, d2.x, ax); ay = fmaf(cd.z, d2.y, ay);
-        const float2 o = make_float2(-cn * ay, cn * ax);  // i (theta/n) M in
-        sacc[i].x += o.x;
-        sacc[i].y += o.y;
-        if (store) sts2<(1 - P) * TBB + G0>(sm, own + D::O_TB + NW * i * SLOT, o);
-      }
-      if (store) __syncthreads();
-    };
-
-    // one tile with the buffer parity B known at compile time; false on a timeout
-    auto chunk = [&](auto Bc, int ck) -> bool {
-      constexpr int B = decltype(Bc)::value;
-      constexpr int OVD = D::O_VD + B * NV * SEG, OVH = D::O_VH + B * NV * SEG;
-      const bool ok = mbar_wait_sleep(&s_bar[0], (unsigned)B);
-      if (!__syncthreads_and(ok)) {
-        if (t == 0) atomicOr(err, kErrTimeout);
-        if (!ok) mbar_wait_sleep(&s_bar[0], (unsigned)B);
-        return false;
-      }
-      const float mk = reinterpret_cast<const float2*>(sm + pad + D::O_MK)[pt].x;
-      // ---- s, d2; eta = e^{i m phi} V^{1/2} u into term buffer 0
-#pragma unroll
-      for (int i = 0; i < RPW; ++i) {
-        sv[i] = lds2<D::O_STG>(sm, own + NW * i * SLOT);
-        dv[i] = lds2<D::O_STG + D::RP * SEG>(sm, own + NW * i * SLOT);
-        sacc[i] = make_float2(0.f, 0.f);
-        if (nterms > 0) {
-          const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowT);
-          const int vo = pad + pt * 8 + *reinterpret_cast<const int*>(rt + offsetof(RowT, vo));
-          const float2 vh = lds2<OVH>(sm, vo);
-          const float2 ph = *reinterpret_cast<const float2*>(rt + offsetof(RowT, ph));
-          sts2<D::O_TB + G0>(sm, own + NW * i * SLOT, cmul(ph, cmul(vh, sv[i] + dv[i])));
-        }
-      }
-      __syncthreads();
-      if (t == 0) {  // the staging buffer is free: the next tile, or the next molecule's first
-        if (ck + 1 < nchunks) {
-          mbar_expect_tx(&s_bar[0], kChunkBytes);
-          issue(lm, ck + 1);
-        } else if (lm + (int)gridDim.x < sp.nmol) {
-          mbar_expect_tx(&s_bar[0], kChunkBytes);
-          issue(lm + (int)gridDim.x, 0);
-        }
-      }
-      for (int n = 1; n <= nterms; n += 2) {
-        term(std::integral_constant<int, 0>(), n);
-        if (n + 1 <= nterms) term(std::integral_constant<int, 1>(), n + 1);
-      }
-      // ---- d1 = (V - 1) u + V^{1/2} e^{-i m phi} S ; mask ; s' = s + (d2 + d1) + cfix s
-      const int sbo = (nterms & 1) * TBB;  // s' buffer: not read by the last term
-      float2* gsw = gs + (long long)(RPL * w + half) * NR + ck * TILE + pt;
-#pragma unroll
-      for (int i = 0; i < RPW; ++i) {
-        const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowT);
-        const int vo = pad + pt * 8 + *reinterpret_cast<const int*>(rt + offsetof(RowT, vo));
-        const float2 u = sv[i] + dv[i];
-        const float2 vd = lds2<OVD>(sm, vo);
-        float2 d1 = cmul(vd, u);
-        if (nterms > 0) {
-          const float2 vh = lds2<OVH>(sm, vo);
-          const float2 ph = *reinterpret_cast<const float2*>(rt + offsetof(RowT, ph));
-          d1 = d1 + cmul(vh, cmul(make_float2(ph.x, -ph.y), sacc[i]));
-        }
-        const bool gr = ground(i);
-        if (mk < 1.f) {
-          const float px = u.x + d1.x, py = u.y + d1.y;
-          d1.x = fmaf(mk - 1.f, u.x, mk * d1.x);
-          d1.y = fmaf(mk - 1.f, u.y, mk * d1.y);
-          const float dd = (1.f - mk * mk) * fmaf(px, px, py * py);
-          if (gr) a_gf += dd; else a_ef += dd;
-        }
-        const float2 sn = round_update(sv[i], dv[i] + d1, cfix, rnd);
-        if (valid(i)) gsw[(long long)(RPL * NW * i) * NR] = sn;  // padded rows: zero, not stored
-        sts2<D::O_TB + G0>(sm, own + sbo + NW * i * SLOT, sn);
-        sv[i] = sn;
-        const float b2 = fmaf(sn.x, sn.x, sn.y * sn.y);
-        if (gr) acc2(p_hi[0], p_lo[0], b2);  // compensated from the first term on
-        else acc2(p_hi[1], p_lo[1], b2);
-      }
-      __syncthreads();
-      // ---- dipole in the molecule frame: sum_c conj(g_c) (A e)_c for A = Z, S+, S-
-      float2 accP = make_float2(0.f, 0.f), accM = accP, accZ = accP;
-#pragma unroll
-      for (int i = 0; i < RPW; ++i) {
-        if (ground(i)) {
-          const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowT);
-          const float2 gc = sv[i];
-          const float4 du = *reinterpret_cast<const float4*>(rt + offsetof(RowT, du));
-          const float4 dd = *reinterpret_cast<const float4*>(rt + offsetof(RowT, dd));
-          const int2 oo = *reinterpret_cast<const int2*>(rt + offsetof(RowT, ou));
-          const int a = pad + pt * 8 + oo.x + sbo, c = pad + pt * 8 + oo.y + sbo;
-          const float2 u0 = lds2<0>(sm, a), u1 = lds2<SEG>(sm, a), u2 = lds2<2 * SEG>(sm, a);
-          const float2 e0 = lds2<0>(sm, c), e1 = lds2<SEG>(sm, c), e2 = lds2<2 * SEG>(sm, c);
-          const float2 wP = make_float2(fmaf(du.x, u0.x, dd.x * e0.x), fmaf(du.x, u0.y, dd.x * e0.y));
-          const float2 wZ = make_float2(fmaf(du.y, u1.x, dd.y * e1.x), fmaf(du.y, u1.y, dd.y * e1.y));
-          const float2 wM = make_float2(fmaf(du.z, u2.x, dd.z * e2.x), fmaf(du.z, u2.y, dd.z * e2.y));
-          accZ.x += fmaf(gc.x, wZ.x, gc.y * wZ.y);
-          accZ.y += fmaf(gc.x, wZ.y, -gc.y * wZ.x);
-          accP.x += fmaf(gc.x, wP.x, gc.y * wP.y);
-          accP.y += fmaf(gc.x, wP.y, -gc.y * wP.x);
-          accM.x += fmaf(gc.x, wM.x, gc.y * wM.y);
-          accM.y += fmaf(gc.x, wM.y, -gc.y * wM.x);
-        }
-      }
-      dP += accP.x + accM.x;
-      dQ += accP.y - accM.y;
-      dZ += 2.f * accZ.x;
-      return true;
-    };
-
-    for (int ck = 0; ck < nchunks; ck += 2) {
-      if (!chunk(std::integral_constant<int, 0>(), ck)) return;
-      if (!chunk(std::integral_constant<int, 1>(), ck + 1)) return;
-    }
-    // ---- block reduction: populations compensated, the rest plain FP32
-    {
-      float v[8] = {p_hi[0], p_hi[1], a_gf, a_ef, dP, dQ, dZ, rnd};
-      float lo[2] = {p_lo[0], p_lo[1]};
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const float h2 = __shfl_xor_sync(0xffffffffu, v[k], o);
-          const float l2 = __shfl_xor_sync(0xffffffffu, lo[k], o);
-          acc2(v[k], lo[k], h2);
-          lo[k] += l2;
-        }
-#pragma unroll
-        for (int k = 2; k < 8; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 7; ++k) s_red[w][k] = v[k];
-        s_red[w][7] = lo[0];
-        s_red[w][8] = lo[1];
-        s_red[w][9] = v[7];
-      }
-      __syncthreads();
-      if (t < 8) {
-        float hi = 0.f, l = 0.f;
-        for (int ww = 0; ww < NW; ++ww) {
-          acc2(hi, l, s_red[ww][t < 7 ? t : 9]);
-          if (t < 2) l += s_red[ww][7 + t];
-        }
-        s_fin[t] = hi + l;
-        if (t < 2) s_fin_lo[t] = l - (s_fin[t] - hi);
-      }
-      __syncthreads();
-      if (t < 3) {  // lab dipole: mu = O mu', mu' = d dR (Re(S+ + S-), Im(S+ - S-), 2 Re Z)
-        const float sc = (float)sp.dipole * sp.dR;
-        const float lab =
-            sc * (s_rot[3 * t] * s_fin[4] + s_rot[3 * t + 1] * s_fin[5] + s_rot[3 * t + 2] * s_fin[6]);
-        const double nl = (double)lab;
-        md.dmu[3 * (long long)m + t] = nl - s_mu[t];
-        md.mu[3 * (long long)m + t] = nl;
-      } else if (t < 5) {
-        const double P = ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
-        md.pop[2 * (long long)m + (t - 3)] = P;
-        if (!isfinite(P)) atomicOr(err, kErrNonFinite);
-      } else if (t < 7) {
-        md.absorbed[2 * (long long)m + (t - 5)] = s_abs[t - 5] + (double)s_fin[t - 3] * (double)sp.dR;
-      } else if (t == 7) {
-        md.ncorr[m] = rounding_feedback(s_fin[7], s_fin[0] + s_fin[1]);
-      }
-    }
-  }
-}
-
-
-// ----------------------------------------------------------------------------
-// R-space pass of the streaming form, tiled, two radial points per thread
-// (MS_KERN_PAIR).  Tiles, tensor copies, persistence, bounded waits and the
-// step computed are those of mol_rspace_kernel; here each thread holds a pair
-// of neighbouring radial points of its rows, so the arithmetic runs as packed
-// FP32x2 operations (one instruction for both points) and every shared-memory
-// access moves 16 bytes.  Values whose complex products matter (eta, the
-// series terms, the potential and mask tables) are kept per point pair as
-// (Re p, Re p+1, Im p, Im p+1): a complex product is then four packed
-// operations with no exchange of parts.  The state arrives and leaves as
-// stored, (Re, Im) per point; the operations that keep real and imaginary
-// parts apart (the update, its rounding residual, the sums, the dipole's
-// real-coefficient couplings) run on it in that order.
-//
-// The coupling series is carried as R_n = M^n eta, with M = theta (E_perp X +
-// E'_z Z) real in the turned frame, so no term needs the factor i: the sum
-// S = sum_{n >= 1} (i^n / n!) R_n takes a real weight on even n and a weight
-// times a swap of parts on odd n.  Rows are padded to whole warp slots (RPL
-// rows of TILE / 2 threads); padded rows stay zero and are neither summed
-// nor written.
-// ----------------------------------------------------------------------------
-constexpr int pair_rows(int slots, int rpw, int rpl) { return (slots + rpw - 1) / rpw * rpw * rpl; }
-// rows per thread: 6 down to 3, the fewest padded rows (ties: more rows a thread)
-constexpr int pair_rpw(int slots, int rpl) {
-  int best = 6;
-  for (int r = 5; r >= 3; --r)
-    if (pair_rows(slots, r, rpl) < pair_rows(slots, best, rpl)) best = r;
-  return best;
-}
-
-// One row of the pair kernel's row table (built per molecule); the
-// coefficients appear twice, once per point of a pair.
-struct RowP {
-  float4 c0, c1, c2;  // theta x coupling: (u.x u.x u.y u.y) (u.z u.z d.x d.x) (d.y d.y d.z d.z) on the runs
-  float4 ph;          // e^{i m phi_E}: (Re, Re, Im, Im)
-  int ou, od, vo, pad;
-};
-// Dipole coefficients of a ground row, laid out as RowP's c0..c2 (built once per CTA).
-struct DipP {
-  float4 d0, d1, d2;
-};
-
-template <int J, int TILE>
-struct Rs2Dims {
-  static constexpr int NROT = (J + 1) * (J + 1), ROWS = 2 * NROT, NV = 2 * (J + 1);
-  static constexpr int TPR = TILE / 2, RPL = 32 / TPR;  // threads per row, rows per warp slot
-  static constexpr int SLOTS = (ROWS + RPL - 1) / RPL;
-  static constexpr int RPW = pair_rpw(SLOTS, RPL);
-  static constexpr int NW = (SLOTS + RPW - 1) / RPW, NT = 32 * NW;
-  static constexpr int RP = NW * RPW * RPL;  // rows with padding
-  static constexpr bool EXACT = RP == ROWS;
-  static constexpr int SEG = TILE * (int)sizeof(float2), SLOT = RPL * SEG;
-  static constexpr int BOXR = ROWS < 256 ? ROWS : 256, NBOX = (ROWS + BOXR - 1) / BOXR;
-  static constexpr int TBB = (kTriGuard + RP) * SEG;
-  static constexpr int O_STG = 0, O_VD = O_STG + 2 * RP * SEG, O_VH = O_VD + 2 * NV * SEG;
-  static constexpr int O_MK = O_VH + 2 * NV * SEG, O_TB = O_MK + (SEG < 128 ? 128 : SEG), O_RT = O_TB + 2 * TBB;
-  static constexpr int O_DT = O_RT + RP * (int)sizeof(RowP);
-  static constexpr int BYTES = 128 + O_DT + NROT * (int)sizeof(DipP);
-  static constexpr int MINB = J >= 9 ? 1 : (TILE == 8 ? 3 : 2);
-  static_assert(TILE == 8 || TILE == 16 || TILE == 32, "tile of 8, 16 or 32 radial points");
-  static_assert(NT <= 1024 && BYTES <= 227 * 1024, "one CTA per molecule fits");
-  static_assert(SLOT == 512, "a warp slot is 512 contiguous bytes");
-  static_assert((RP * SEG) % 128 == 0 && (NV * SEG) % 128 == 0 && (BOXR * SEG) % 128 == 0 && O_RT % 16 == 0,
-                "tensor-copy destinations 128-byte aligned, tables 16-byte aligned");
-};
-
-__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
-__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
-__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
-__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, neg2(b)); }
-// (ax + i ay)(bx + i by) on point pairs
-__device__ __forceinline__ void cmul2(float2 ax, float2 ay, float2 bx, float2 by, float2& rx, float2& ry) {
-  rx = fma2(ax, bx, neg2(mul2(ay, by)));
-  ry = fma2(ax, by, mul2(ay, bx));
-}
-template <int OFF>
-__device__ __forceinline__ float4 lds4(const unsigned char* base, int off) {
-  return *reinterpret_cast<const float4*>(base + off + OFF);
-}
-template <int OFF>
-__device__ __forceinline__ void sts4(unsigned char* base, int off, float4 v) {
-  *reinterpret_cast<float4*>(base + off + OFF) = v;
-}
-// round_update on one point held as a (Re, Im) pair, packed: s' = fl(s + D'),
-// D' = D + c s, with the exact residual of that rounding folded into acc
-// (per part; the two parts are added at the end)
-__device__ __forceinline__ float2 round_update2(float2 sv, float2 D, float2 c, float2& acc) {
-  const float2 d = fma2(c, sv, D);
-  const float2 n = add2(sv, d);
-  const float2 b = sub2(n, sv);
-  const float2 e = add2(sub2(sv, sub2(n, b)), sub2(d, b));
-  acc = fma2(n, e, acc);
-  return n;
-}
-// compensated sums of point pairs (TwoSum per part)
-__device__ __forceinline__ void acc2p(float2& hi, float2& lo, float2 x) {
-  const float2 t = add2(hi, x);
-  const float2 z = sub2(t, hi);
-  lo = add2(lo, add2(sub2(hi, sub2(t, z)), sub2(x, z)));
-  hi = t;
-}
-
-template <int J, int TILE>
-__global__ void __launch_bounds__(Rs2Dims<J, TILE>::NT, Rs2Dims<J, TILE>::MINB)
-    mol_rspace_pair_kernel(SpeciesDev sp, MolDev md, int* err, const __grid_constant__ RspaceMaps maps) {
-  using D = Rs2Dims<J, TILE>;
-  constexpr int NROT = D::NROT, ROWS = D::ROWS, NV = D::NV, NW = D::NW, RPW = D::RPW, NT = D::NT;
-  constexpr int RPL = D::RPL, SEG = D::SEG, SLOT = D::SLOT, TBB = D::TBB, G0 = kTriGuard * SEG;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ __align__(8) unsigned long long s_bar[1];
-  __shared__ float s_rot[9];
-  __shared__ double s_mu[3], s_abs[2];
-  __shared__ float2 s_ph[2 * kMaxJ + 1];
-  __shared__ float s_red[NW][10];
-  __shared__ float s_fin[8], s_fin_lo[2];
-
-  const int NR = sp.nr;
-  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int part = lane / D::TPR, pp = lane % D::TPR;  // row within the warp slot, point pair
-  const int pad = (int)((128u - (smem_u32(smem_raw) & 127u)) & 127u);
-  unsigned char* const sm = smem_raw;
-  // this thread's byte offsets: own rows RPL (w + NW i) + part at points 2 pp, 2 pp + 1
-  const int own = pad + w * SLOT + lane * 16;
-  const int rtw = pad + D::O_RT + (RPL * w + part) * (int)sizeof(RowP);
-  const int dtw = pad + D::O_DT + (RPL * w + part) * (int)sizeof(DipP);
-  auto issue = [&](int mol, int ck) {
-    const int r0 = ck * TILE, b = ck & 1;
-    unsigned char* base = sm + pad;
-#pragma unroll
-    for (int k = 0; k < D::NBOX; ++k) {
-      const bool last = k == D::NBOX - 1 && D::NBOX > 1;
-      tensor2d_g2s(base + D::O_STG + k * D::BOXR * SEG, last ? &maps.s_r : &maps.s, r0, mol * ROWS + k * D::BOXR,
-                   &s_bar[0]);
-      tensor2d_g2s(base + D::O_STG + (D::RP + k * D::BOXR) * SEG, last ? &maps.d2_r : &maps.d2, r0,
-                   mol * ROWS + k * D::BOXR, &s_bar[0]);
-    }
-    tensor2d_g2s(base + D::O_VD + b * NV * SEG, &maps.vd, r0, 0, &s_bar[0]);
-    tensor2d_g2s(base + D::O_VH + b * NV * SEG, &maps.vh, r0, 0, &s_bar[0]);
-    tensor2d_g2s(base + D::O_MK, &maps.mk, r0, 0, &s_bar[0]);
-  };
-  constexpr unsigned kChunkBytes = (2 * ROWS + 2 * NV + 1) * SEG;
-  const int nchunks = NR / TILE;  // even: NR is 64, 128 or 256
-
-  int lm = blockIdx.x;
-  if (t == 0) {
-    mbar_init(&s_bar[0], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    mbar_expect_tx(&s_bar[0], kChunkBytes);
-    issue(lm, 0);
-  }
-  for (int q = t; q < kTriGuard * TILE; q += NT) {
-    reinterpret_cast<float2*>(sm + pad + D::O_TB)[q] = make_float2(0.f, 0.f);
-    reinterpret_cast<float2*>(sm + pad + D::O_TB + TBB)[q] = make_float2(0.f, 0.f);
-  }
-  if constexpr (!D::EXACT) {  // padded staging rows: zero, and never written by the copies
-    for (int q = t; q < (D::RP - ROWS) * TILE; q += NT) {
-      reinterpret_cast<float2*>(sm + pad + D::O_STG + ROWS * SEG)[q] = make_float2(0.f, 0.f);
-      reinterpret_cast<float2*>(sm + pad + D::O_STG + (D::RP + ROWS) * SEG)[q] = make_float2(0.f, 0.f);
-    }
-  }
-  for (int q = t; q < NROT; q += NT) {  // dipole coefficients of the ground rows (the same for every molecule)
-    const int j = j_of(q);
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 du = j < J ? g_tri_up[q] : z4, dd = j > 0 ? g_tri_dn[q] : z4;
-    DipP d;
-    d.d0 = make_float4(du.x, du.x, du.y, du.y);
-    d.d1 = make_float4(du.z, du.z, dd.x, dd.x);
-    d.d2 = make_float4(dd.y, dd.y, dd.z, dd.z);
-    *reinterpret_cast<DipP*>(sm + pad + D::O_DT + q * (int)sizeof(DipP)) = d;
-  }
-  auto ground = [&](int i) { return RPL * (w + NW * i) + part < NROT; };
-  auto valid = [&](int i) { return D::EXACT || RPL * (w + NW * i) + part < ROWS; };
-
-  for (; lm < sp.nmol; lm += gridDim.x) {
-    const int m = sp.mol[lm];
-    __syncthreads();  // the previous molecule's outputs are written: its records may be replaced
-    const float4 f = __ldg(&sp.fld[lm]);  // (theta E'_z, theta E'_x/2, theta E'_y/2, terms)
-    const int nterms = __float_as_int(f.w);
-    if (t <= J) {  // e^{i t phi_E} by binary powers of e^{i phi_E} = (E'_x + i E'_y)/E_perp
-      const float ep = sqrtf(f.y * f.y + f.z * f.z);
-      float2 e1 = ep > 0.f ? make_float2(f.y / ep, f.z / ep) : make_float2(1.f, 0.f);
-      float2 pw = make_float2(1.f, 0.f);
-      for (int k = t; k > 0; k >>= 1) {
-        if (k & 1) pw = cmul(pw, e1);
-        e1 = cmul(e1, e1);
-      }
-      s_ph[J + t] = pw;
-      s_ph[J - t] = make_float2(pw.x, -pw.y);
-    }
-    for (int q = t; q < 14; q += NT) {  // rotation, previous dipole, absorbed norm so far
-      if (q < 9) s_rot[q] = md.rot[9 * (long long)m + q];
-      else if (q < 12) s_mu[q - 9] = md.mu[3 * (long long)m + (q - 9)];
-      else s_abs[q - 12] = md.absorbed[2 * (long long)m + (q - 12)];
-    }
-    const float cfix = md.ncorr[m];  // rounding feedback of the previous step
-    const float2 cf2 = make_float2(cfix, cfix);
-    __syncthreads();
-    for (int q = t; q < D::RP; q += NT) {  // the row table of this molecule (padding: zero, guard rows)
-      RowP r;
-      if (!D::EXACT && q >= ROWS) {
-        r.c0 = r.c1 = r.c2 = make_float4(0.f, 0.f, 0.f, 0.f);
-        r.ph = make_float4(1.f, 1.f, 0.f, 0.f);
-        r.ou = r.od = D::O_TB;
-        r.vo = 0;
-      } else {
-        // theta E_perp / 2 on the X runs and theta E'_z on the Z runs (frame turned so E'_y = 0)
-        const float ep = sqrtf(f.y * f.y + f.z * f.z), ez = f.x;
-        const int sf = q >= NROT, c = q - sf * NROT, j = j_of(c), mm = c - j * j - j;
-        const int other = kTriGuard + (1 - sf) * NROT;
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 du = j < J ? g_tri_up[c] : z4, dd = j > 0 ? g_tri_dn[c] : z4;
-        const float ux = ep * du.x, uy = ez * du.y, uz = ep * du.z;
-        const float dx = ep * dd.x, dy = ez * dd.y, dz = ep * dd.z;
-        r.c0 = make_float4(ux, ux, uy, uy);
-        r.c1 = make_float4(uz, uz, dx, dx);
-        r.c2 = make_float4(dy, dy, dz, dz);
-        const float2 ph = s_ph[mm + J];
-        r.ph = make_float4(ph.x, ph.x, ph.y, ph.y);
-        r.ou = D::O_TB + (j < J ? (other + c + 2 * j + 1) * SEG : 0);
-        r.od = D::O_TB + (j > 0 ? (other + c - 2 * j - 1) * SEG : 0);
-        r.vo = (sf * (J + 1) + j) * SEG;
-      }
-      r.pad = 0;
-      *reinterpret_cast<RowP*>(sm + pad + D::O_RT + q * (int)sizeof(RowP)) = r;
-    }
-    float4 sv[RPW], dv[RPW];  // s and d2 of the own rows, as stored: (Re, Im) of point 2 pp, then 2 pp + 1
-    float2 sx[RPW], sy[RPW];  // the series sum S, pair layout
-    float2 pg_hi = make_float2(0.f, 0.f), pg_lo = pg_hi, pe_hi = pg_hi, pe_lo = pg_hi;  // populations
-    float2 a_g = pg_hi, a_e = pg_hi, aS = pg_hi, aZ = pg_hi, aD = pg_hi, rnd = pg_hi;
-    float2* gs = sp.psi + (long long)lm * ROWS * NR;
-
-    // R_n = M R_{n-1} from term buffer P, added to S with weight (ka, kb):
-    // odd n (P = 0): S += i k R, ka = -k, kb = k; even n (P = 1): S += k R, kb = k
-    auto term = [&](auto Pc, int n, float2 ka, float2 kb) {
-      constexpr int P = decltype(Pc)::value;
-      const bool store = n < nterms;
-#pragma unroll
-      for (int i = 0; i < RPW; ++i) {
-        const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowP);
-        const float4 c0 = *reinterpret_cast<const float4*>(rt + offsetof(RowP, c0));
-        const float4 c1 = *reinterpret_cast<const float4*>(rt + offsetof(RowP, c1));
-        const float4 c2 = *reinterpret_cast<const float4*>(rt + offsetof(RowP, c2));
-        const int2 oo = *reinterpret_cast<const int2*>(rt + offsetof(RowP, ou));
-        const int ou = pad + pp * 16 + oo.x, od = pad + pp * 16 + oo.y;
-        const float4 u0 = lds4<P * TBB>(sm, ou), u1 = lds4<P * TBB + SEG>(sm, ou),
-                     u2 = lds4<P * TBB + 2 * SEG>(sm, ou);
-        const float4 e0 = lds4<P * TBB>(sm, od), e1 = lds4<P * TBB + SEG>(sm, od),
-                     e2 = lds4<P * TBB + 2 * SEG>(sm, od);
-        float2 rx = mul2(lo2(c0), lo2(u0)), ry = mul2(lo2(c0), hi2(u0));
-        rx = fma2(hi2(c0), lo2(u1), rx); ry = fma2(hi2(c0), hi2(u1), ry);
-        rx = fma2(lo2(c1), lo2(u2), rx); ry = fma2(lo2(c1), hi2(u2), ry);
-        rx = fma2(hi2(c1), lo2(e0), rx); ry = fma2(hi2(c1), hi2(e0), ry);
-        rx = fma2(lo2(c2), lo2(e1), rx); ry = fma2(lo2(c2), hi2(e1), ry);
-        rx = fma2(hi2(c2), lo2(e2), rx); ry = fma2(hi2(c2), hi2(e2), ry);
-        if constexpr (P == 0) {
-          sx[i] = fma2(ka, ry, sx[i]);
-          sy[i] = fma2(kb, rx, sy[i]);
-        } else {
-          sx[i] = fma2(kb, rx, sx[i]);
-          sy[i] = fma2(kb, ry, sy[i]);
-        }
-        if (store) sts4<(1 - P) * TBB + G0>(sm, own + D::O_TB + NW * i * SLOT, make_float4(rx.x, rx.y, ry.x, ry.y));
-      }
-      if (store) __syncthreads();
-    };
-
-    // one tile with the buffer parity B known at compile time; false on a timeout
-    auto chunk = [&](auto Bc, int ck) -> bool {
-      constexpr int B = decltype(Bc)::value;
-      constexpr int OVD = D::O_VD + B * NV * SEG, OVH = D::O_VH + B * NV * SEG;
-      const bool ok = mbar_wait_sleep(&s_bar[0], (unsigned)B);
-      if (!__syncthreads_and(ok)) {
-        if (t == 0) atomicOr(err, kErrTimeout);
-        if (!ok) mbar_wait_sleep(&s_bar[0], (unsigned)B);
-        return false;
-      }
-      const float4 mk = *reinterpret_cast<const float4*>(sm + pad + D::O_MK + pp * 16);  // (m, m, 1-m^2, 1-m^2)
-      // ---- s, d2; eta = e^{i m phi} V^{1/2} u into term buffer 0 (pair layout)
-#pragma unroll
-      for (int i = 0; i < RPW; ++i) {
-        sv[i] = lds4<D::O_STG>(sm, own + NW * i * SLOT);
-        dv[i] = lds4<D::O_STG + D::RP * SEG>(sm, own + NW * i * SLOT);
-        sx[i] = sy[i] = make_float2(0.f, 0.f);
-        if (nterms > 0) {
-          const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowP);
-          const int vo = pad + pp * 16 + *reinterpret_cast<const int*>(rt + offsetof(RowP, vo));
-          const float4 vh = lds4<OVH>(sm, vo);
-          const float4 ph = *reinterpret_cast<const float4*>(rt + offsetof(RowP, ph));
-          const float2 ux = make_float2(sv[i].x + dv[i].x, sv[i].z + dv[i].z);
-          const float2 uy = make_float2(sv[i].y + dv[i].y, sv[i].w + dv[i].w);
-          float2 ax, ay, ex, ey;
-          cmul2(lo2(vh), hi2(vh), ux, uy, ax, ay);
-          cmul2(lo2(ph), hi2(ph), ax, ay, ex, ey);
-          sts4<D::O_TB + G0>(sm, own + NW * i * SLOT, make_float4(ex.x, ex.y, ey.x, ey.y));
-        }
-      }
-      __syncthreads();
-      if (t == 0) {  // the staging buffer is free: the next tile, or the next molecule's first
-        if (ck + 1 < nchunks) {
-          mbar_expect_tx(&s_bar[0], kChunkBytes);
-          issue(lm, ck + 1);
-        } else if (lm + (int)gridDim.x < sp.nmol) {
-          mbar_expect_tx(&s_bar[0], kChunkBytes);
-          issue(lm + (int)gridDim.x, 0);
-        }
-      }
-      float fac = 1.f;  // 1 / n!
-      for (int n = 1; n <= nterms; n += 2) {
-        fac /= (float)n;
-        const float k1 = (n & 2) ? -fac : fac;  // i^n / n! = i k1
-        term(std::integral_constant<int, 0>(), n, make_float2(-k1, -k1), make_float2(k1, k1));
-        if (n + 1 <= nterms) {
-          fac /= (float)(n + 1);
-          const float k2 = ((n + 1) & 2) ? -fac : fac;  // i^(n+1) / (n+1)! = k2
-          term(std::integral_constant<int, 1>(), n + 1, make_float2(0.f, 0.f), make_float2(k2, k2));
-        }
-      }
-      // ---- d1 = (V - 1) u + V^{1/2} e^{-i m phi} S ; mask ; s' = s + (d2 + d1) + cfix s
-      const int sbo = (nterms & 1) * TBB;  // s' buffer: not read by the last term
-      float2* gsw = gs + (long long)(RPL * w + part) * NR + ck * TILE + 2 * pp;
-      const bool masked = mk.x < 1.f || mk.y < 1.f;
-#pragma unroll
-      for (int i = 0; i < RPW; ++i) {
-        const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowP);
-        const int vo = pad + pp * 16 + *reinterpret_cast<const int*>(rt + offsetof(RowP, vo));
-        const float2 ux = make_float2(sv[i].x + dv[i].x, sv[i].z + dv[i].z);
-        const float2 uy = make_float2(sv[i].y + dv[i].y, sv[i].w + dv[i].w);
-        const float4 vd = lds4<OVD>(sm, vo);
-        float2 d1x, d1y;
-        cmul2(lo2(vd), hi2(vd), ux, uy, d1x, d1y);
-        if (nterms > 0) {
-          const float4 vh = lds4<OVH>(sm, vo);
-          const float4 ph = *reinterpret_cast<const float4*>(rt + offsetof(RowP, ph));
-          // conj(ph) S, then V^{1/2} times it
-          const float2 tx = fma2(lo2(ph), sx[i], mul2(hi2(ph), sy[i]));
-          const float2 ty = fma2(lo2(ph), sy[i], neg2(mul2(hi2(ph), sx[i])));
-          d1x = fma2(lo2(vh), tx, fma2(neg2(hi2(vh)), ty, d1x));
-          d1y = fma2(lo2(vh), ty, fma2(hi2(vh), tx, d1y));
-        }
-        const bool gr = ground(i);
-        if (masked) {
-          const float2 mv = lo2(mk), mm1 = make_float2(mk.x - 1.f, mk.y - 1.f);
-          const float2 px = add2(ux, d1x), py = add2(uy, d1y);
-          d1x = fma2(mm1, ux, mul2(mv, d1x));
-          d1y = fma2(mm1, uy, mul2(mv, d1y));
-          const float2 dd = mul2(hi2(mk), fma2(px, px, mul2(py, py)));
-          if (gr) a_g = add2(a_g, dd);
-          else a_e = add2(a_e, dd);
-        }
-        // back to (Re, Im) per point: D = d2 + d1
-        const float2 D0 = make_float2(dv[i].x + d1x.x, dv[i].y + d1y.x);
-        const float2 D1 = make_float2(dv[i].z + d1x.y, dv[i].w + d1y.y);
-        const float2 n0 = round_update2(lo2(sv[i]), D0, cf2, rnd);
-        const float2 n1 = round_update2(hi2(sv[i]), D1, cf2, rnd);
-        const float4 sn = make_float4(n0.x, n0.y, n1.x, n1.y);
-        if (valid(i)) *reinterpret_cast<float4*>(gsw + (long long)(RPL * NW * i) * NR) = sn;
-        sts4<D::O_TB + G0>(sm, own + sbo + NW * i * SLOT, sn);
-        sv[i] = sn;
-        const float2 b2 = make_float2(fmaf(n0.x, n0.x, n0.y * n0.y), fmaf(n1.x, n1.x, n1.y * n1.y));
-        if (gr) acc2p(pg_hi, pg_lo, b2);  // compensated from the first term on
-        else acc2p(pe_hi, pe_lo, b2);
-      }
-      __syncthreads();
-      // ---- dipole in the molecule frame on s' (as stored): sum_c conj(g_c) (A e)_c for A = Z, S+, S-
-#pragma unroll
-      for (int i = 0; i < RPW; ++i) {
-        if (ground(i)) {
-          const unsigned char* rt = sm + rtw + NW * RPL * i * (int)sizeof(RowP);
-          const unsigned char* dt = sm + dtw + NW * RPL * i * (int)sizeof(DipP);
-          const float4 q0 = *reinterpret_cast<const float4*>(dt + offsetof(DipP, d0));
-          const float4 q1 = *reinterpret_cast<const float4*>(dt + offsetof(DipP, d1));
-          const float4 q2 = *reinterpret_cast<const float4*>(dt + offsetof(DipP, d2));
-          const int2 oo = *reinterpret_cast<const int2*>(rt + offsetof(RowP, ou));
-          const int a = pad + pp * 16 + oo.x + sbo, c = pad + pp * 16 + oo.y + sbo;
-          const float4 u0 = lds4<0>(sm, a), u1 = lds4<SEG>(sm, a), u2 = lds4<2 * SEG>(sm, a);
-          const float4 e0 = lds4<0>(sm, c), e1 = lds4<SEG>(sm, c), e2 = lds4<2 * SEG>(sm, c);
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {  // the two points, (Re, Im) each
-            const float2 g = h ? hi2(sv[i]) : lo2(sv[i]);
-            const float2 U0 = h ? hi2(u0) : lo2(u0), U1 = h ? hi2(u1) : lo2(u1), U2 = h ? hi2(u2) : lo2(u2);
-            const float2 E0 = h ? hi2(e0) : lo2(e0), E1 = h ? hi2(e1) : lo2(e1), E2 = h ? hi2(e2) : lo2(e2);
-            const float2 wP = fma2(lo2(q0), U0, mul2(hi2(q1), E0));  // S+ from both runs
-            const float2 wZ = fma2(hi2(q0), U1, mul2(lo2(q2), E1));  // Z
-            const float2 wM = fma2(lo2(q1), U2, mul2(hi2(q2), E2));  // S-
-            aS = fma2(g, add2(wP, wM), aS);            // (sum gx (P+M)x, sum gy (P+M)y)
-            aZ = fma2(g, wZ, aZ);
-            aD = fma2(make_float2(g.y, g.x), sub2(wP, wM), aD);  // (sum gy (P-M)x, sum gx (P-M)y)
-          }
-        }
-      }
-      return true;
-    };
-
-    for (int ck = 0; ck < nchunks; ck += 2) {
-      if (!chunk(std::integral_constant<int, 0>(), ck)) return;
-      if (!chunk(std::integral_constant<int, 1>(), ck + 1)) return;
-    }
-    // ---- block reduction: populations compensated, the rest plain FP32
-    {
-      float v[8], lo[2];
-      v[0] = pg_hi.x; lo[0] = pg_lo.x + pg_lo.y; acc2(v[0], lo[0], pg_hi.y);
-      v[1] = pe_hi.x; lo[1] = pe_lo.x + pe_lo.y; acc2(v[1], lo[1], pe_hi.y);
-      v[2] = a_g.x + a_g.y;
-      v[3] = a_e.x + a_e.y;
-      v[4] = aS.x + aS.y;         // Re(P + M)
-      v[5] = aD.y - aD.x;         // Im(P - M)
-      v[6] = 2.f * (aZ.x + aZ.y); // 2 Re Z
-      v[7] = rnd.x + rnd.y;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const float h2 = __shfl_xor_sync(0xffffffffu, v[k], o);
-          const float l2 = __shfl_xor_sync(0xffffffffu, lo[k], o);
-          acc2(v[k], lo[k], h2);
-          lo[k] += l2;
-        }
-#pragma unroll
-        for (int k = 2; k < 8; ++k) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int k = 0; k < 7; ++k) s_red[w][k] = v[k];
-        s_red[w][7] = lo[0];
-        s_red[w][8] = lo[1];
-        s_red[w][9] = v[7];
-      }
-      __syncthreads();
-      if (t < 8) {
-        float hi = 0.f, l = 0.f;
-        for (int ww = 0; ww < NW; ++ww) {
-          acc2(hi, l, s_red[ww][t < 7 ? t : 9]);
-          if (t < 2) l += s_red[ww][7 + t];
-        }
-        s_fin[t] = hi + l;
-        if (t < 2) s_fin_lo[t] = l - (s_fin[t] - hi);
-      }
-      __syncthreads();
-      if (t < 3) {  // lab dipole: mu = O mu', mu' = d dR (Re(S+ + S-), Im(S+ - S-), 2 Re Z)
-        const float sc = (float)sp.dipole * sp.dR;
-        const float lab =
-            sc * (s_rot[3 * t] * s_fin[4] + s_rot[3 * t + 1] * s_fin[5] + s_rot[3 * t + 2] * s_fin[6]);
-        const double nl = (double)lab;
-        md.dmu[3 * (long long)m + t] = nl - s_mu[t];
-        md.mu[3 * (long long)m + t] = nl;
-      } else if (t < 5) {
-        const double P = ((double)s_fin[t - 3] + (double)s_fin_lo[t - 3]) * (double)sp.dR;
-        md.pop[2 * (long long)m + (t - 3)] = P;
-        if (!isfinite(P)) atomicOr(err, kErrNonFinite);
-      } else if (t < 7) {
-        md.absorbed[2 * (long long)m + (t - 5)] = s_abs[t - 5] + (double)s_fin[t - 3] * (double)sp.dR;
-      } else if (t == 7) {
-        md.ncorr[m] = rounding_feedback(s_fin[7], s_fin[0] + s_fin[1]);
-      }
-    }
-  }
 }
 
 // ----------------------------------------------------------------------------
@@ -2200,9 +1254,11 @@ static bool rspace_ok(int nr, int jmax);
 // resident one does not and it applies, unless the plan names another kernel.
 static bool pair_ok(int nr, int jmax) { return (nr == 64 || nr == 128 || nr == 256) && jmax <= 16; }
 // The two-points-a-thread tiled kernel runs a streaming species' R-space pass
-// where the plan names it, and by the static rule from J = 5 on.
+// where the plan names it, and by the static rule from J = 5 on (for the
+// parity-reduced state it is the only kernel from J = 5 on).
 static bool use_pair(const SpeciesDev& sp) {
-  if (sp.path != MS_MOL_STREAMING || sp.par || sp.dipw || !pair_ok(sp.nr, sp.jmax)) return false;
+  if (sp.path != MS_MOL_STREAMING || sp.dipw || !pair_ok(sp.nr, sp.jmax)) return false;
+  if (sp.par) return sp.jmax >= 5;
   return sp.kern == MS_KERN_PAIR || (sp.kern == MS_KERN_DEFAULT && sp.jmax >= 5);
 }
 static bool use_tile(const SpeciesDev& sp) {
@@ -2210,9 +1266,10 @@ static bool use_tile(const SpeciesDev& sp) {
   return sp.kern == MS_KERN_DEFAULT || sp.kern == MS_KERN_TILE;
 }
 // its tile width: 8 points from J = 9 on; else the plan's, or 16 points from
-// J = 5 on and 32 below
+// J = 5 on and 32 below (parity-reduced: 16 points to J = 8)
 static int pair_tile(const SpeciesDev& sp) {
   if (sp.jmax >= 9) return 8;
+  if (sp.par) return 16;
   if (sp.ch == 8 || sp.ch == 16 || sp.ch == 32) return sp.ch;
   return sp.jmax >= 5 ? 16 : 32;
 }
@@ -2453,99 +1510,6 @@ int mol_plan_candidates(const SpeciesDev& sp, int (*out)[4], int max) {
   return n < max ? n : max;
 }
 
-// persistent launch of a tiled kernel: CTA b walks molecules b, b + grid,
-// ...; the grid is the plan's resident CTAs per SM (0: as many as fit) times
-// the SMs, or one CTA per molecule (cps < 0)
-using RspaceKernel = void (*)(SpeciesDev, MolDev, int*, const RspaceMaps);
-static void launch_persistent(RspaceKernel k, int nt, int bytes, const SpeciesDev& sp, const MolDev& md, int* err,
-                              const RspaceMaps& maps, cudaStream_t s) {
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  int dev = 0, nsm = 0, per = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, nt, bytes);
-  per = std::max(per, 1);
-  if (sp.cps > 0) per = std::min(per, sp.cps);
-  const long long fit = sp.cps < 0 ? (long long)sp.nmol : (long long)std::max(nsm, 1) * per;
-  const int grid = (int)std::min<long long>(sp.nmol, fit);
-  k<<<grid, nt, bytes, s>>>(sp, md, err, maps);
-}
-
-template <int J, int TILE>
-static void launch_rspace_jt(const SpeciesDev& sp, const MolDev& md, int* err, const RspaceMaps& maps,
-                             cudaStream_t s) {
-  using D = RsDims<J, TILE>;
-  launch_persistent(mol_rspace_kernel<J, TILE>, D::NT, D::BYTES, sp, md, err, maps, s);
-}
-
-template <int J, int TILE>
-static void launch_pair_jt(const SpeciesDev& sp, const MolDev& md, int* err, const RspaceMaps& maps,
-                           cudaStream_t s) {
-  using D = Rs2Dims<J, TILE>;
-  launch_persistent(mol_rspace_pair_kernel<J, TILE>, D::NT, D::BYTES, sp, md, err, maps, s);
-}
-
-static void launch_rspace_pair(const SpeciesDev& sp, const MolDev& md, int* err, const RspaceMaps& maps, int tile,
-                               cudaStream_t s) {
-#define MS_PAIR_LO(J)                                                  \
-  case J:                                                              \
-    if (tile == 16) launch_pair_jt<J, 16>(sp, md, err, maps, s);       \
-    else launch_pair_jt<J, 32>(sp, md, err, maps, s);                  \
-    break;
-#define MS_PAIR_HI(J)                                                  \
-  case J:                                                              \
-    if (tile == 8) launch_pair_jt<J, 8>(sp, md, err, maps, s);         \
-    else launch_pair_jt<J, 16>(sp, md, err, maps, s);                  \
-    break;
-#define MS_PAIR_8(J)                                                   \
-  case J:                                                              \
-    launch_pair_jt<J, 8>(sp, md, err, maps, s);                        \
-    break;
-  switch (sp.jmax) {
-    MS_PAIR_LO(0) MS_PAIR_LO(1) MS_PAIR_LO(2) MS_PAIR_LO(3) MS_PAIR_LO(4)
-    MS_PAIR_HI(5) MS_PAIR_HI(6) MS_PAIR_HI(7) MS_PAIR_HI(8)
-    MS_PAIR_8(9) MS_PAIR_8(10) MS_PAIR_8(11) MS_PAIR_8(12) MS_PAIR_8(13) MS_PAIR_8(14) MS_PAIR_8(15) MS_PAIR_8(16)
-  }
-#undef MS_PAIR_LO
-#undef MS_PAIR_HI
-#undef MS_PAIR_8
-}
-
-template <int J>
-static void launch_rspace_j(const SpeciesDev& sp, const MolDev& md, int* err, const RspaceMaps& maps,
-                            int tile, cudaStream_t s) {
-  if constexpr (J >= 9) {
-    launch_rspace_jt<J, 8>(sp, md, err, maps, s);
-  } else {
-    if (tile == 16) launch_rspace_jt<J, 16>(sp, md, err, maps, s);
-    else launch_rspace_jt<J, 32>(sp, md, err, maps, s);
-  }
-}
-
-static void launch_rspace(const SpeciesDev& sp, const MolDev& md, int* err, const RspaceMaps& maps, int tile,
-                          cudaStream_t s) {
-  switch (sp.jmax) {
-    case 0: launch_rspace_j<0>(sp, md, err, maps, tile, s); break;
-    case 1: launch_rspace_j<1>(sp, md, err, maps, tile, s); break;
-    case 2: launch_rspace_j<2>(sp, md, err, maps, tile, s); break;
-    case 3: launch_rspace_j<3>(sp, md, err, maps, tile, s); break;
-    case 4: launch_rspace_j<4>(sp, md, err, maps, tile, s); break;
-    case 5: launch_rspace_j<5>(sp, md, err, maps, tile, s); break;
-    case 6: launch_rspace_j<6>(sp, md, err, maps, tile, s); break;
-    case 7: launch_rspace_j<7>(sp, md, err, maps, tile, s); break;
-    case 8: launch_rspace_j<8>(sp, md, err, maps, tile, s); break;
-    case 9: launch_rspace_j<9>(sp, md, err, maps, tile, s); break;
-    case 10: launch_rspace_j<10>(sp, md, err, maps, tile, s); break;
-    case 11: launch_rspace_j<11>(sp, md, err, maps, tile, s); break;
-    case 12: launch_rspace_j<12>(sp, md, err, maps, tile, s); break;
-    case 13: launch_rspace_j<13>(sp, md, err, maps, tile, s); break;
-    case 14: launch_rspace_j<14>(sp, md, err, maps, tile, s); break;
-    case 15: launch_rspace_j<15>(sp, md, err, maps, tile, s); break;
-    case 16: launch_rspace_j<16>(sp, md, err, maps, tile, s); break;
-  }
-}
-
 // cuTensorMapEncodeTiled, looked up once through the runtime
 static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -2582,7 +1546,7 @@ static bool encode_rows(CUtensorMap* m, const void* base, unsigned long long nr,
 static bool rspace_maps(const SpeciesDev& sp, int tile, bool pair, RspaceMaps* out) {
   struct Entry {
     const void *psi, *d2, *vd, *vh, *mk;
-    int nmol, nr, nrot, tile;
+    int nmol, nr, rows, tile;
     RspaceMaps maps;
   };
   static std::mutex mu;
@@ -2593,12 +1557,12 @@ static bool rspace_maps(const SpeciesDev& sp, int tile, bool pair, RspaceMaps* o
                *mk = pair ? sp.maskw_pp : sp.maskw;
   for (const Entry& e : cache)
     if (e.psi == sp.psi && e.d2 == sp.d2 && e.vd == vd && e.vh == vh && e.mk == mk && e.nmol == sp.nmol &&
-        e.nr == sp.nr && e.nrot == sp.nrot && e.tile == tile) {
+        e.nr == sp.nr && e.rows == sp.rows && e.tile == tile) {
       *out = e.maps;
       return true;
     }
-  Entry e{sp.psi, sp.d2, vd, vh, mk, sp.nmol, sp.nr, sp.nrot, tile, {}};
-  const unsigned rows = 2 * sp.nrot, nv = 2 * (sp.jmax + 1);
+  Entry e{sp.psi, sp.d2, vd, vh, mk, sp.nmol, sp.nr, sp.rows, tile, {}};
+  const unsigned rows = sp.rows, nv = 2 * (sp.jmax + 1);  // stored rows a molecule (parity-reduced: half)
   const unsigned boxr = rows < 256 ? rows : 256, lastr = rows - (rows + boxr - 1) / boxr * boxr + boxr;
   const unsigned long long nr = sp.nr, nrows = (unsigned long long)sp.nmol * rows;
   if (!encode_rows(&e.maps.s, sp.psi, nr, nrows, boxr, tile) || !encode_rows(&e.maps.d2, sp.d2, nr, nrows, boxr, tile) ||
@@ -2612,6 +1576,8 @@ static bool rspace_maps(const SpeciesDev& sp, int tile, bool pair, RspaceMaps* o
   *out = e.maps;
   return true;
 }
+
+bool mol_tensor_maps_available() { return tensor_map_encoder() != nullptr; }
 
 // rows per kinetic block: 32 KB of state
 static int kinetic_rows(int nr) { return 4096 / nr; }
@@ -2955,9 +1921,15 @@ static int launch_stage2_t(const SpeciesDev& sp, const MolDev& md, const Grid& g
     return 1;
   }
   RspaceMaps maps;
-  if (use_pair(sp) && rspace_maps(sp, pair_tile(sp), true, &maps)) {
-    launch_rspace_pair(sp, md, err, maps, pair_tile(sp), s);
-    return 1;
+  if (use_pair(sp)) {
+    if (rspace_maps(sp, pair_tile(sp), true, &maps)) {
+      launch_rspace_pair(sp, md, err, maps, pair_tile(sp), s);
+      return 1;
+    }
+    if (sp.par) {  // no other kernel takes the parity-reduced state beyond J = 4: report it
+      flag_error_kernel<<<1, 1, 0, s>>>(err, kErrLaunch);
+      return 1;
+    }
   }
   if (use_tile(sp) && rspace_maps(sp, rspace_tile(sp), false, &maps)) {
     launch_rspace(sp, md, err, maps, rspace_tile(sp), s);

@@ -935,8 +935,11 @@ ms_status validate(const ms_grid_desc* G, const ms_materials_desc* M, const ms_m
         return MS_EUNSUPPORTED;
       // the mixed kinetic pass: streaming form, radial grids of 64 or 128 points
       if (mixed && (path == MS_MOL_FUSED || !ms::mol_mixed_supported(sp.nr))) return MS_EUNSUPPORTED;
-      // parity-reduced rows: the point-resident kernels (J <= 4; fused only at N_r = 128)
-      if (par && (sp.jmax > 4 || (path == MS_MOL_FUSED && sp.nr != 128))) return MS_EUNSUPPORTED;
+      // parity-reduced rows: the point-resident kernels (J <= 4; fused only at N_r = 128), and from
+      // J = 5 on the two-points-a-thread tiled kernel (streaming layout, FP32 kinetic pass)
+      if (par && sp.jmax <= 4 && path == MS_MOL_FUSED && sp.nr != 128) return MS_EUNSUPPORTED;
+      if (par && sp.jmax >= 5 && (path == MS_MOL_FUSED || mixed || !ms::mol_tensor_maps_available()))
+        return MS_EUNSUPPORTED;
     }
     for (long long q = 0; q < D->n_molecules; ++q) {
       const int si = D->species_id[q];
@@ -1057,6 +1060,7 @@ static ms_status latched(ms_sim* s) {
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
   if (e & ms::kErrPrescribedRange) return MS_EINVAL;
   if (e & ms::kErrTimeout) return MS_ETIMEOUT;
+  if (e & ms::kErrLaunch) return MS_ECUDA;
   return e ? MS_ENUMERIC : MS_OK;
 }
 

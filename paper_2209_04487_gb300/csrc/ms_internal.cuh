@@ -20,6 +20,7 @@ enum : int {
   kErrCouplingSeries = 2, // |theta E'| too large for the coupling series
   kErrPrescribedRange = 4,
   kErrTimeout = 8,        // a bounded wait on an asynchronous copy gave up
+  kErrLaunch = 16,        // a kernel could not be prepared (its tensor maps), so it did not run
 };
 
 // Incident wave parameters of one sim.
@@ -216,6 +217,8 @@ int launch_bloch_step(const SpeciesDev& sp, const MolDev& md, const Grid& g, int
                       cudaStream_t s);
 void launch_bloch_observe(const SpeciesDev& sp, const MolDev& md, cudaStream_t s);
 bool mol_step_supported(int nr, int nrot, int path);
+// the driver's tensor-map encoder, which the tiled kernels need, is available
+bool mol_tensor_maps_available();
 // the (layout, kernel, chunk width, CTAs per SM) plans a species can run; returns how many
 int mol_plan_candidates(const SpeciesDev& sp, int (*out)[4], int max);
 cudaError_t upload_coupling_tables(const CouplEntry* rot, const CouplEntry* dip);

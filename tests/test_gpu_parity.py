@@ -132,6 +132,8 @@ def test_prescribed_molecules_match_oracle(B, nr, jmax, nmol, path):
 @pytest.mark.parametrize("nr,jmax,nmol,path", [
     (128, 4, 19, "fused"), (128, 4, 19, "streaming"), (64, 1, 37, "streaming"), (128, 2, 7, "fused"),
     (64, 3, 11, "streaming"), (256, 2, 5, "streaming"),
+    # from J = 5 on: the two-points-a-thread tiled kernel on the reduced rows
+    (64, 6, 11, "streaming"), (128, 8, 9, "streaming"), (64, 10, 3, "streaming"),
 ])
 def test_parity_reduced_matches_oracle(B, nr, jmax, nmol, path):
     sp = W.Species(nr=nr, jmax=jmax, A=0.05)
@@ -159,6 +161,23 @@ def test_parity_reduced_matches_oracle(B, nr, jmax, nmol, path):
     tot = P.sum(axis=1) + absb.sum(axis=1)
     print(f"parity-reduced nr={nr} J={jmax} {path}: norm bookkeeping max {np.abs(tot - 1).max():.3e}")
     assert np.abs(tot - 1).max() < 1e-6
+
+
+def test_parity_reduced_unsupported_forms(B):
+    """From J = 5 on the reduced rows run only in the streaming layout with
+    the FP32 kinetic pass, and their plan is not settable."""
+    for kw in ({"mol_path": B.MS_MOL_FUSED}, {"precision": B.MS_PREC_MIXED_F16X3}):
+        wl = W.custom("parity forms", 8, 8, 48, n_per_sim=4, species=[W.Species(nr=64, jmax=6)],
+                      layer=(20, 24), nsteps=4)
+        with pytest.raises(B.MSError) as e:
+            B.Simulation(wl, state_form=B.MS_STATE_PARITY, **kw)
+        assert e.value.code == B.MS_EUNSUPPORTED
+    sim = B.Simulation(wl, state_form=B.MS_STATE_PARITY)
+    assert sim.species_path(0) == B.MS_MOL_STREAMING
+    with pytest.raises(B.MSError):
+        sim.set_plan(0, B.MS_MOL_STREAMING, B.MS_KERN_TILE, 16)
+    sim.step(4)
+    sim.close()
 
 
 def test_parity_reduced_coupled_matches_oracle(B):
