@@ -59,6 +59,8 @@ def _args(argv=None):
                         "configuration's own pulse (peak at 40 fs) on a reduced copy of --sweep-molecules per cell, "
                         "and add the dissociation yield and Eq. 8's <R>_e per carrier to the line")
     p.add_argument("--sweep-molecules", type=int, default=2000)
+    p.add_argument("--state", default="full", choices=["full", "parity"],
+                   help="state form of the headline run: every row, or only the rows the j = 0 start populates")
     p.add_argument("--batches", type=int, default=0,
                    help="pipelined molecular step: runs per species (ms_set_mol_batches; 0 = stages in sequence)")
     p.add_argument("--plan", default=None, metavar="KERNEL:CHUNK[:CTAS][,...]",
@@ -425,7 +427,8 @@ def main():
         return {"ms": ms_, "phases": ph, "nsteps": nst, "launches": nlaunch, "clocks": cl, "P": Pf,
                 "norm_err": nerr, "path": form_path, "plans": plans}
 
-    main_form = time_form(wl, path, B.MS_PREC_FP32, preroll, clocks=True, pinned=True)
+    main_state = B.MS_STATE_PARITY if a.state == "parity" else 0
+    main_form = time_form(wl, path, B.MS_PREC_FP32, preroll, clocks=True, pinned=True, state_form=main_state)
     ms, phases, nsteps, launches = main_form["ms"], main_form["phases"], main_form["nsteps"], main_form["launches"]
     cl, P, norm_err = main_form["clocks"], main_form["P"], main_form["norm_err"]
     fused = main_form["path"] == B.MS_MOL_FUSED
@@ -457,7 +460,7 @@ def main():
                 "300 strongly driven steps; norm drift max 7.3e-7 over 64 molecules in 2000 steps (plain FP32: "
                 "1.3e-7)")
             forms["mixed_f16x3"] = mixed
-        if a.config != 1:
+        if a.config != 1 and a.state == "full":
             # the parity-reduced state of the same workload: only the rows the
             # j = 0 start populates (half of them), identical dynamics
             fp = time_form(wl, path, B.MS_PREC_FP32, preroll, state_form=B.MS_STATE_PARITY)
@@ -480,7 +483,8 @@ def main():
     per_step = lambda k: phases[k] / max(nsteps, 1)    # ms per step of one timed phase
     peak, peak_src = _peaks()
     nm = [int((wl.species_id == i).sum()) for i in range(len(wl.species))]
-    states = [16 * s.nr * s.nrot for s in wl.species]   # FP32 state of one molecule (bytes)
+    rows_of = (lambda sp: sp.nrot) if a.state == "parity" else (lambda sp: 2 * sp.nrot)
+    states = [8 * s.nr * rows_of(s) for s in wl.species]   # FP32 state of one molecule (bytes)
     st_bytes = sum(b * n for b, n in zip(states, nm))
     one = len(wl.species) == 1
     sp = wl.species[0]
@@ -501,6 +505,8 @@ def main():
         elif one and main_form["plans"][0][1] in (B.MS_KERN_PAIR, B.MS_KERN_DEFAULT) and sp.jmax >= 5:
             tile = 8 if sp.jmax >= 9 else (main_form["plans"][0][2] or 16)    # the pair kernel's rule
             kernel, traffic_key = f"mol_rspace_pair_kernel<{sp.jmax},{tile}>", "mol_rspace_pair_kernel"
+            if a.state == "parity":
+                kernel, traffic_key = f"mol_rspace_pair_kernel<{sp.jmax},{tile},parity>", None
         elif one and sp.jmax <= 8:
             tile = main_form["plans"][0][2] or (16 if sp.jmax >= 5 else 32)   # the tiled kernel's rule
             kernel, traffic_key = f"mol_rspace_kernel<{sp.jmax},{tile}>", "mol_rspace_kernel"
@@ -570,7 +576,10 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": _config(a.config, wl, preroll), "cell_updates_per_s": cells_rate,
+                "config": dict(_config(a.config, wl, preroll), **({"state": "parity-reduced: the rows the j = 0 "
+                                                                               "start populates"}
+                                                                      if a.state == "parity" else {})),
+                "cell_updates_per_s": cells_rate,
                 "phases_ms_per_step": {"h": phases[0] / nsteps, "molecules": phases[1] / nsteps,
                                        "e": phases[2] / nsteps, "molecules_stage1": phases[4] / nsteps,
                                        "molecules_stage2": phases[5] / nsteps},

@@ -83,7 +83,11 @@ struct Rs2Dims {
   static constexpr int O_MK = O_VH + 2 * NV * SEG, O_TB = O_MK + (SEG < 128 ? 128 : SEG), O_RT = O_TB + 2 * TBB;
   static constexpr int O_DT = O_RT + RP * (int)sizeof(RowP);
   static constexpr int BYTES = 128 + O_DT + NGR * (int)sizeof(DipP);
-  static constexpr int MINB = J >= 9 ? 1 : (TILE == 8 ? 3 : 2);
+  // parity-reduced kernels: as many resident CTAs (up to 3) as their shared memory allows (78.1 against
+  // 81.0 ms a step on the nanohole workload at J = 8, two CTAs before)
+  static constexpr int MINB_SMEM = 228 * 1024 / (BYTES + 2048);
+  static constexpr int MINB = PAR ? (MINB_SMEM < 1 ? 1 : (MINB_SMEM > 3 ? 3 : MINB_SMEM))
+                                  : (J >= 9 ? 1 : (TILE == 8 ? 3 : 2));
   static_assert(TILE == 8 || TILE == 16 || TILE == 32, "tile of 8, 16 or 32 radial points");
   static_assert(NT <= 1024 && BYTES <= 227 * 1024, "one CTA per molecule fits");
   static_assert(SLOT == 512, "a warp slot is 512 contiguous bytes");
