@@ -506,7 +506,7 @@ def main():
             tile = 8 if sp.jmax >= 9 else (main_form["plans"][0][2] or 16)    # the pair kernel's rule
             kernel, traffic_key = f"mol_rspace_pair_kernel<{sp.jmax},{tile}>", "mol_rspace_pair_kernel"
             if a.state == "parity":
-                kernel, traffic_key = f"mol_rspace_pair_kernel<{sp.jmax},{tile},parity>", None
+                kernel, traffic_key = f"mol_rspace_pair_kernel<{sp.jmax},{tile},parity>", "mol_rspace_pair_kernel_parity"
         elif one and sp.jmax <= 8:
             tile = main_form["plans"][0][2] or (16 if sp.jmax >= 5 else 32)   # the tiled kernel's rule
             kernel, traffic_key = f"mol_rspace_kernel<{sp.jmax},{tile}>", "mol_rspace_kernel"
