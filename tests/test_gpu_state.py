@@ -269,3 +269,39 @@ def test_population_sums_equal_fp64_sums_of_the_state(B, tmp_path):
         assert P[:, 1].max() > 1e-6
         assert rel.max() < 1e-11
         assert rel_exact.max() < 1e-7
+
+
+def test_parity_reduced_pair_kernel_state_paths(B, tmp_path):
+    """The parity-reduced rows on the two-points-a-thread kernel (J = 6 and
+    J = 9 species, coupled to the grid) through the paths that move or
+    replay the state: eager stepping equals graph replay and the pipelined
+    step bit for bit, and a checkpoint taken halfway resumes to the same
+    result."""
+    species = [W.Species(nr=64, jmax=6, A=0.05), W.Species(nr=64, jmax=9)]
+    wl = W.custom("parity state", 16, 16, 48, src_k=14, pulses=[[2e10, 1.5498, 2e-15, 1e-15]],
+                  layer=(22, 26), n_per_sim=90, species=species, fractions=[0.5, 0.5], seed=21, nsteps=96)
+
+    def run(graphs, batches=0, split=None):
+        sim = B.Simulation(wl, state_form=B.MS_STATE_PARITY,
+                           step_graphs=B.MS_GRAPHS_AUTO if graphs else B.MS_GRAPHS_OFF)
+        assert sim.species_path(0) == sim.species_path(1) == B.MS_MOL_STREAMING
+        sim.set_batches(batches)
+        if split is None:
+            sim.step(wl.nsteps)
+        else:
+            sim.step(split)
+            path = str(tmp_path / "parity.ck")
+            sim.save(path)
+            sim.close()
+            sim = B.Simulation(wl, state_form=B.MS_STATE_PARITY)
+            sim.load(path)
+            sim.step(wl.nsteps - split)
+        out = _snapshot(B, sim, wl.nsim)
+        sim.close()
+        return out
+
+    ref = run(False)
+    assert np.abs(ref["mu"]).max() > 0.0 and ref["P"][:, 1].max() > 0.0
+    _assert_identical(ref, run(True))
+    _assert_identical(ref, run(True, batches=3))
+    _assert_identical(ref, run(False, split=40))
