@@ -1818,18 +1818,18 @@ ms_status ms_set_species_plan(ms_sim* s, int32_t species, int32_t path, int32_t 
 ms_status ms_set_mol_batches(ms_sim* s, int32_t batches) {
   if (!s || batches < 0 || batches > kMaxMolBatches) return MS_EINVAL;
   if (cudaStreamSynchronize(s->stream) != cudaSuccess) return MS_ECUDA;
-  if (batches > 0 && !s->stream2) {
-    if (cudaStreamCreateWithFlags(&s->stream2, cudaStreamNonBlocking) != cudaSuccess) {
+  if (batches > 0) {  // the second stream and the event pool (completed by a later call if one failed)
+    if (!s->stream2 && cudaStreamCreateWithFlags(&s->stream2, cudaStreamNonBlocking) != cudaSuccess) {
       cudaGetLastError();
       s->stream2 = nullptr;
       return MS_ECUDA;
     }
-    const int nev = ms::kMaxSpecies * kMaxMolBatches + 1;  // one per run, one for the join
-    for (int k = 0; k < nev; ++k) {
+    const size_t nev = (size_t)ms::kMaxSpecies * kMaxMolBatches + 1;  // one per run, one for the join
+    while (s->bev.size() < nev) {
       cudaEvent_t e = nullptr;
       if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
-        return MS_ECUDA;
+        return MS_ECUDA;  // batches unchanged: the step stays sequential
       }
       s->bev.push_back(e);
     }
