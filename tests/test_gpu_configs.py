@@ -79,11 +79,11 @@ def _seeded_field(wl, E0=5e9, seed=5):
     return out
 
 
-def _molecules_prescribed(B, wl, precision, sample, nsteps=12):
+def _molecules_prescribed(B, wl, precision, sample, nsteps=12, state_form=0):
     """Part 1: all molecules under a seeded prescribed drive; the sample against the oracle."""
     amp, wave = W.prescribed_drive(wl.n_molecules, nsteps, wl.dt, E0=5e9, carrier_ev=6.0, fwhm=0.02e-15,
                                    t0=0.5 * nsteps * wl.dt, seed=79)
-    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, precision=precision)
+    sim = B.Simulation(wl, drive=B.MS_DRIVE_PRESCRIBED, precision=precision, state_form=state_form)
     sim.set_prescribed(amp, wave)
     sim.step(nsteps)
     P, mu = sim.populations(), sim.dipoles()
@@ -187,3 +187,20 @@ def test_sixteen_nanohole_cells_in_one_launch(B):
     E = _seeded_field(wl)
     _coupled_properties(B, wl, E, 20)
     _fields_vs_oracle(B, wl, E)
+
+
+@pytest.mark.parametrize("config", [2, 3])
+def test_parity_reduced_state_at_full_size(B, config):
+    """The parity-reduced rows (the rows the j = 0 start populates) on the
+    full nanohole (700,000 molecules, J <= 8) and three-species (J 4/8/16)
+    workloads: every molecule under the prescribed drive with a seeded
+    sample against the oracle (which keeps every row), then the coupled run's
+    bookkeeping."""
+    wl = W.config2() if config == 2 else W.config3()
+    _need(_state_bytes(wl) + 12e9)              # half the rows, state and scratch
+    rng = np.random.default_rng(40 + config)
+    sample = np.sort(np.concatenate([rng.choice(np.nonzero(wl.species_id == s)[0], 3, replace=False)
+                                     for s in range(len(wl.species))]))
+    _molecules_prescribed(B, wl, B.MS_PREC_FP32, sample, nsteps=8, state_form=B.MS_STATE_PARITY)
+    E = _seeded_field(wl)
+    _coupled_properties(B, wl, E, 8, state_form=B.MS_STATE_PARITY)
