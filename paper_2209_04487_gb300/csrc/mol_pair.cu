@@ -192,10 +192,12 @@ __global__ void __launch_bounds__(Rs2Dims<J, TILE, PAR>::NT, Rs2Dims<J, TILE, PA
     mbar_expect_tx(&s_bar[0], kChunkBytes);
     issue(lm, 0);
   }
-  for (int q = t; q < kTriGuard * TILE; q += NT) {
-    reinterpret_cast<float2*>(sm + pad + D::O_TB)[q] = make_float2(0.f, 0.f);
-    reinterpret_cast<float2*>(sm + pad + D::O_TB + TBB)[q] = make_float2(0.f, 0.f);
-  }
+  // both term buffers zeroed once: the guard rows stay zero, and every row a
+  // zero coefficient may read (the dipole reads only excited rows' s', so a
+  // down-run at its lowest shell can land on ground rows never stored) holds
+  // finite data from then on
+  for (int q = t; q < 2 * TBB / 16; q += NT)
+    reinterpret_cast<float4*>(sm + pad + D::O_TB)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
   if constexpr (!D::EXACT) {  // padded staging rows: zero, and never written by the copies
     for (int q = t; q < (D::RP - ROWS) * TILE; q += NT) {
       reinterpret_cast<float2*>(sm + pad + D::O_STG + ROWS * SEG)[q] = make_float2(0.f, 0.f);
@@ -413,7 +415,7 @@ __global__ void __launch_bounds__(Rs2Dims<J, TILE, PAR>::NT, Rs2Dims<J, TILE, PA
         const float2 n1 = round_update2(hi2(sv[i]), D1, cf2, rnd);
         const float4 sn = make_float4(n0.x, n0.y, n1.x, n1.y);
         if (valid(i)) *reinterpret_cast<float4*>(gsw + (long long)(RPL * NW * i) * NR) = sn;
-        sts4<D::O_TB + G0>(sm, own + sbo + NW * i * SLOT, sn);
+        if (!gr) sts4<D::O_TB + G0>(sm, own + sbo + NW * i * SLOT, sn);  // the dipole reads excited rows only
         sv[i] = sn;
         const float2 b2 = make_float2(fmaf(n0.x, n0.x, n0.y * n0.y), fmaf(n1.x, n1.x, n1.y * n1.y));
         if (gr) acc2p(pg_hi, pg_lo, b2);  // compensated from the first term on
