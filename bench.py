@@ -428,7 +428,10 @@ def main():
                 "norm_err": nerr, "path": form_path, "plans": plans}
 
     main_state = B.MS_STATE_PARITY if a.state == "parity" else 0
-    main_form = time_form(wl, path, B.MS_PREC_FP32, preroll, clocks=True, pinned=True, state_form=main_state)
+    # the three-species configuration's plans (tile shapes, molecules per CTA) come from the autotuner
+    tune_main = a.config == 3 and not a.plan
+    main_form = time_form(wl, path, B.MS_PREC_FP32, preroll, clocks=True, pinned=True, state_form=main_state,
+                          tune=tune_main)
     ms, phases, nsteps, launches = main_form["ms"], main_form["phases"], main_form["nsteps"], main_form["launches"]
     cl, P, norm_err = main_form["clocks"], main_form["P"], main_form["norm_err"]
     fused = main_form["path"] == B.MS_MOL_FUSED
@@ -503,7 +506,8 @@ def main():
         if one and sp.jmax <= 4:
             kernel, traffic_key = f"mol_rpoint_kernel<{sp.jmax},{sp.nr}>", "mol_rpoint_kernel"
         elif one and main_form["plans"][0][1] in (B.MS_KERN_PAIR, B.MS_KERN_DEFAULT) and sp.jmax >= 5:
-            tile = 8 if sp.jmax >= 9 else (main_form["plans"][0][2] or 16)    # the pair kernel's rule
+            # the pair kernel's rule: 8-point tiles, 16 for the parity-reduced rows to J = 8
+            tile = 8 if sp.jmax >= 9 else (main_form["plans"][0][2] or (16 if a.state == "parity" else 8))
             kernel, traffic_key = f"mol_rspace_pair_kernel<{sp.jmax},{tile}>", "mol_rspace_pair_kernel"
             if a.state == "parity":
                 kernel, traffic_key = f"mol_rspace_pair_kernel<{sp.jmax},{tile},parity>", "mol_rspace_pair_kernel_parity"
@@ -544,7 +548,8 @@ def main():
         # of every population (timed)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = B.Simulation(wl, mol_path=path)
+        s2 = B.Simulation(wl, mol_path=path, state_form=main_state,
+                          autotune=B.MS_TUNE_MEASURE if tune_main else B.MS_TUNE_OFF)
         pin(s2, wl)
         s2.set_batches(a.batches)
         torch.cuda.synchronize()
@@ -585,7 +590,7 @@ def main():
                                        "molecules_stage2": phases[5] / nsteps},
                 "plans": [{"layout": p[0], "kernel": p[1], "chunk": p[2], "ctas_per_sm": p[3]}
                           for p in main_form["plans"]],
-                "mol_batches": a.batches,
+                "mol_batches": a.batches, "autotuned": tune_main,
                 "roofline": roof, "roofline_kinetic": roof_kin, "roofline_molecular_step": roof_step,
                 "roofline_fdtd": roof_fdtd,
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * world,

@@ -113,8 +113,8 @@ enum { MS_GRAPHS_AUTO = 0, MS_GRAPHS_OFF = 1 };
  * radial points (4, 8, 16 or 32) of all rows (any J).  MS_KERN_PAIR: the
  * tiled kernel's schedule with two neighbouring radial points per thread and
  * packed FP32x2 arithmetic (streaming; chunk 32 or 16 for J <= 4, 16 or 8
- * for J 5..8, 8 for J 9..16; chunk 0: 8 from J = 9 on, 16 from J = 5 on,
- * else 32).  MS_KERN_DEFAULT: the
+ * for J 5..8, 8 for J 9..16; chunk 0: 8 from J = 5 on, else 32; the
+ * parity-reduced state: 16 for J 5..8).  MS_KERN_DEFAULT: the
  * static rule (the first that applies of point for J <= 4, pair from J = 5
  * on in the streaming layout, tile, chunk at the widest fitting chunk).
  * Parity-reduced and d(R) species run

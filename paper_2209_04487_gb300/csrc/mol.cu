@@ -1265,13 +1265,14 @@ static bool use_tile(const SpeciesDev& sp) {
   if (sp.path != MS_MOL_STREAMING || use_point(sp) || use_pair(sp) || !rspace_ok(sp.nr, sp.jmax)) return false;
   return sp.kern == MS_KERN_DEFAULT || sp.kern == MS_KERN_TILE;
 }
-// its tile width: 8 points from J = 9 on; else the plan's, or 16 points from
-// J = 5 on and 32 below (parity-reduced: 16 points to J = 8)
+// its tile width: 8 points from J = 9 on; else the plan's, or 8 points from
+// J = 5 on (the nanohole pass 113.7 against 118.3 ms at 16) and 32 below;
+// parity-reduced rows: 16 points to J = 8 (at 8 a CTA would hold two warps)
 static int pair_tile(const SpeciesDev& sp) {
   if (sp.jmax >= 9) return 8;
   if (sp.par) return 16;
   if (sp.ch == 8 || sp.ch == 16 || sp.ch == 32) return sp.ch;
-  return sp.jmax >= 5 ? 16 : 32;
+  return sp.jmax >= 5 ? 8 : 32;
 }
 }  // namespace ms
 
