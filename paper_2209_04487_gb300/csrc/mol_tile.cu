@@ -1,6 +1,9 @@
 // Tiled R-space pass with one radial point a thread (MS_KERN_TILE): the
-// kernels and their launch.  A translation unit of its own, so that it
-// compiles beside mol.cu.
+// kernels and their launch.  The pass is the R-space half of the
+// split-operator step of Eqs. 4-7 (the potential phases of Eqs. 6-7, the
+// exponential of the field interaction, the absorbing mask) and the
+// populations and molecular dipole it reports.  A translation unit of its
+// own, so that it compiles beside mol.cu.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
